@@ -1,0 +1,106 @@
+"""Host-side measurement formulas against the paper's printed tables, and the
+synthetic generator's determinism."""
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from paper_2104_14667_gb300 import metrics
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_streaming_tables.txt")
+
+
+def _rows():
+    rows = []
+    with open(GOLDEN) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            s, w, h, alg, n, t_us, rate, eff = line.split()
+            rows.append((s, int(w), int(h), alg, int(n), float(t_us), float(rate), float(eff)))
+    return rows
+
+
+def test_golden_has_every_printed_row():
+    assert len(_rows()) == 32
+
+
+def test_transfer_rate_reproduces_paper_tables():
+    # 1 byte per pixel: raster bytes x N / wall time gives the printed GB/s
+    for s, w, h, alg, n, t_us, rate, _ in _rows():
+        got = metrics.transfer_gbs(w * h * n, t_us * 1e-6)
+        assert abs(got - rate) <= 0.0015, (s, alg, n, got, rate)
+        assert metrics.member_pixels_per_s(n, w, h, t_us * 1e-6) == pytest.approx(rate * 1e9, rel=4e-4)
+
+
+def test_efficiency_is_rate_over_one_copy_rate_per_set():
+    # efficiency = rate / plain-copy rate; the implied copy rate is one
+    # number per raster size, whatever the algorithm or N
+    by_set = {}
+    for s, _, _, _, _, _, rate, eff in _rows():
+        by_set.setdefault(s, []).append(rate / (eff / 100.0))
+    for s, vals in by_set.items():
+        assert max(vals) / min(vals) < 1.005, (s, vals)      # the ~2k N=10 row is 0.3 % off
+    copy = {s: float(np.mean(v)) for s, v in by_set.items()}
+    assert copy["~4k"] == pytest.approx(5.285, abs=0.005)
+    for s, _, _, _, _, _, rate, eff in _rows():
+        assert metrics.efficiency(rate, copy[s]) * 100 == pytest.approx(eff, abs=0.2)
+
+
+def test_pipeline_model_closed_forms():
+    n = 10
+    # copy-bound: n copies plus the last transform and process
+    assert metrics.pipeline_wall([3.0] * n, [0.5] * n, [1.0] * n) == pytest.approx(n * 3.0 + 1.5)
+    # compute-bound: the first copy plus every transform and process
+    assert metrics.pipeline_wall([1.0] * n, [2.0] * n, [1.5] * n) == pytest.approx(1.0 + n * 3.5)
+    assert metrics.pipeline_ratio([2.0] * n, [0.0] * n, [0.0] * n) == pytest.approx(1.0)
+    assert metrics.pipeline_ratio([1.0] * n, [0.0] * n, [0.1] * n) >= 1.0
+
+
+def test_overlap_fraction():
+    assert metrics.overlap_fraction([(0, 10)], [(2, 8)]) == pytest.approx(1.0)
+    assert metrics.overlap_fraction([(0, 5)], [(5, 10)]) == pytest.approx(0.0)
+    # both busy 8 of a 10-long wall: 6 of the 8 overlap
+    assert metrics.overlap_fraction([(0, 4), (4, 8)], [(2, 6), (6, 10)]) == pytest.approx(0.75)
+    assert metrics.overlap_fraction([], [(0, 1)]) is None
+
+
+def test_percentile_nearest_rank():
+    v = list(range(1, 101))
+    assert metrics.percentile(v, 50) == 50
+    assert metrics.percentile(v, 99) == 99
+    assert metrics.percentile([7.0], 99) == 7.0
+
+
+def test_splitmix64_published_vectors():
+    # first outputs of SplitMix64 seeded with 0 (Steele, Lea & Flood 2014)
+    got = [int(x) for x in synth.splitmix64(0, 3)]
+    assert got == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_streams_are_counter_based():
+    a = synth.splitmix64(42, 100)
+    np.testing.assert_array_equal(synth.splitmix64(42, 30, start=70), a[70:])
+    u = synth.uniforms(42, 1000)
+    assert u.min() >= 0.0 and u.max() < 1.0
+
+
+def test_ensemble_is_deterministic_and_shaped():
+    e1 = synth.ensemble(5, 64, 40, 9)
+    e2 = synth.ensemble(5, 64, 40, 9)
+    np.testing.assert_array_equal(e1.terrain, e2.terrain)
+    np.testing.assert_array_equal(e1.levels, e2.levels)
+    m = synth.masks(e1)
+    assert m.dtype == np.uint8 and m.shape == (9, 40, 64) and set(np.unique(m)) <= {0, 1}
+    frac = m.reshape(9, -1).mean(axis=1)
+    assert np.all(frac >= 0.09) and np.all(frac <= 0.51)
+    np.testing.assert_array_equal(m.reshape(9, -1).sum(axis=1), e1.flooded)
+    tail = synth.ensemble(5, 64, 40, 4, member_offset=5)
+    np.testing.assert_array_equal(tail.levels, e1.levels[5:])
+
+
+def test_terrain_row_band_matches_whole():
+    whole = synth.terrain(7, 50, 30)
+    band = synth.terrain(7, 50, 30, rows=slice(10, 20))
+    np.testing.assert_array_equal(band, whole[10:20])

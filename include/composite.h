@@ -1,0 +1,178 @@
+/*
+ * composite.h -- C ABI of the GB300 iterative ensemble compositor.
+ *
+ * The operation (Johnson & Jankun-Kelly, "Efficacy of Images Versus Data
+ * Buffers", Section 2 and Fig. 1): N flood-extent rasters are combined into
+ * one composite image, the users add or remove rasters in real time, and the
+ * composite is shown as a blue saturation map of the overlap.  The
+ * accumulation streams the rasters from host memory through two or more
+ * device receiving buffers so that the upload of one overlaps the processing
+ * of another (Section 4, Figs. 2-4).
+ *
+ * Per pixel p, over the current multiset S of members, N = |S|:
+ *   count(p)  = #{m in S : mask_m(p) != 0}
+ *   bucket(p) = N == 0 ? 0 : floor(255 * count(p) / N)     (exact integers)
+ *   rgba(p)   = lut[bucket(p)]                            (256 x RGBA8 table)
+ *   mean(p)   = N == 0 ? 0 : sum_{m in S} d_m(p) / N      (mean-depth mode)
+ *
+ * Conventions for every call:
+ *   - Return value: CPT_OK (0) or a negative composite_status.  On error the
+ *     message is available from composite_last_error(ctx) until the next call
+ *     on that context.
+ *   - A raster is `height` rows of `width` elements; element type uint8 in
+ *     CPT_MODE_COUNT, float32 in CPT_MODE_MEAN_DEPTH.  Row y of member m
+ *     starts at members + m * member_stride_bytes + y * row_pitch_bytes.
+ *   - Memory kind of `members` is detected (cudaPointerGetAttributes):
+ *       pageable host  -> copied through the library's pinned ring; the
+ *                         caller may reuse the memory as soon as the call
+ *                         returns;
+ *       pinned host    -> uploaded straight from it (cudaMemcpyAsync on the
+ *       or device         copy stream) or read in place; BORROWED until the
+ *                         next composite_render/composite_sync/composite_end
+ *                         returns: do not modify or free it before then.
+ *   - Work is queued on the context's compute stream (config.cuda_stream, or
+ *     a stream the library owns) and copy stream (always library owned), and
+ *     ordered by events, never by host synchronisation.  Host waits that do
+ *     happen (ring reuse, render to host, sync, end) are bounded by
+ *     config.wait_timeout_ms and return CPT_ETIMEOUT when exceeded.
+ *   - One context per host thread; contexts are independent.
+ *   - The library never falls back to a CPU implementation: without a usable
+ *     CUDA device every compute call returns CPT_ECUDA.
+ */
+#ifndef COMPOSITE_H
+#define COMPOSITE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct composite_ctx composite_ctx;   /* opaque, owned by the library */
+
+typedef enum composite_status {
+    CPT_OK = 0,
+    CPT_EINVAL = -1,      /* bad argument; the context is unchanged            */
+    CPT_ENOMEM = -2,      /* device or pinned allocation failed                */
+    CPT_ECUDA = -3,       /* CUDA runtime/driver error (message in last_error) */
+    CPT_ESTATE = -4,      /* context poisoned by an earlier underflow          */
+    CPT_EUNDERFLOW = -5,  /* a remove took away a member that was never added  */
+    CPT_ETIMEOUT = -6     /* a bounded wait (host or device) ran out           */
+} composite_status;
+
+/* How the accumulation kernel reads a member raster (the paper's images
+ * versus buffers question, Sections 5.3 and 6.3, re-asked for sm_103a). */
+enum {
+    CPT_READ_LINEAR = 0,   /* 16-byte vector loads from linear device memory     */
+    CPT_READ_TEXTURE = 1,  /* texture object over a layered, block-tiled cudaArray
+                              filled by a buffer-to-array copy (the image path)  */
+    CPT_READ_TMA = 2       /* TMA tensor tiles staged into shared memory         */
+};
+
+enum {
+    CPT_MODE_COUNT = 0,       /* uint8 masks -> per-pixel member counts      */
+    CPT_MODE_MEAN_DEPTH = 1   /* float32 depths -> per-pixel mean (float32)   */
+};
+
+typedef struct composite_config {
+    int32_t read_path;          /* CPT_READ_*; default CPT_READ_LINEAR                    */
+    int32_t staging_buffers;    /* k device receiving buffers, 1..8; 1 is the paper's
+                                   single-buffer control ("1b"), 2 its dual buffer ("2b");
+                                   default 2                                              */
+    int32_t chunk_members;      /* C members per upload and per kernel launch, 1..255;
+                                   default 16                                             */
+    int32_t count_bits;         /* 16 (N <= 65535) or 32; default 16                      */
+    int32_t mode;               /* CPT_MODE_*; default CPT_MODE_COUNT                     */
+    int32_t trace;              /* 1 = time every copy and kernel with CUDA events
+                                   (composite_trace_read); default 0                      */
+    int64_t pinned_ring_bytes;  /* cap on the pinned ring used for pageable inputs;
+                                   0 = k * C rasters                                      */
+    void *cuda_stream;          /* compute stream (a cudaStream_t) or NULL for a stream
+                                   owned by the library                                   */
+    int64_t wait_timeout_ms;    /* bound on every wait, host and device; 0 = 10000        */
+} composite_config;
+
+/* Fills *cfg with the defaults listed above.  CPT_EINVAL if cfg is NULL. */
+int composite_default_config(composite_config *cfg);
+
+/* Creates a context for width x height rasters and clears its composite
+ * (Fig. 3, step 1: clear the accumulation buffers).  Allocates the device
+ * composite plane, the k staging buffers (and, for CPT_READ_TEXTURE, their
+ * k layered cudaArrays), the streams and events.  cfg NULL = defaults.
+ * Errors: CPT_EINVAL (out NULL, width/height <= 0, a config field out of
+ * range), CPT_ENOMEM, CPT_ECUDA.  On error *out is set to NULL. */
+int composite_begin(composite_ctx **out, int32_t width, int32_t height,
+                    const composite_config *cfg);
+
+/* Resets the composite to the empty multiset (counts and sums to zero,
+ * N = 0) and clears the underflow state, stream-ordered after every earlier
+ * call (Fig. 3, step 1; the paper's timing starts right after this). */
+int composite_clear(composite_ctx *ctx);
+
+/* Adds n_members rasters to the multiset: count(p) += [mask(p) != 0], or in
+ * mean-depth mode sum(p) += d(p) (Fig. 3, steps 3-7: upload into receiving
+ * buffer slot i mod k, accumulate, advance).
+ * member_stride_bytes >= row_pitch_bytes * height; row_pitch_bytes >=
+ * width * element size; float32 rasters need 4-byte aligned pointer, pitch
+ * and stride.  n_members == 0 is a no-op.  Errors: CPT_EINVAL (NULL members
+ * with n > 0, bad strides, N would exceed 65535 with count_bits 16),
+ * CPT_ESTATE, CPT_ECUDA, CPT_ETIMEOUT. */
+int composite_add_members(composite_ctx *ctx, const void *members, int32_t n_members,
+                          int64_t member_stride_bytes, int32_t row_pitch_bytes);
+
+/* Removes n_members rasters from the multiset (the interactive list of
+ * Fig. 1).  The state afterwards equals a recompute over what is left.
+ * CPT_EINVAL, with nothing changed, if N would become negative.  If a pixel
+ * count would go below zero (a raster removed that was never added), the
+ * device records it, the next render or sync returns CPT_EUNDERFLOW and the
+ * context is poisoned (CPT_ESTATE) until composite_clear. */
+int composite_remove_members(composite_ctx *ctx, const void *members, int32_t n_members,
+                             int64_t member_stride_bytes, int32_t row_pitch_bytes);
+
+/* Renders the composite (Fig. 1 caption: overlap classes and the blue
+ * saturation map).  Every output is dense row-major, width x height, caller
+ * owned, and may be NULL to skip it:
+ *   counts_out  uint16 or uint32 per pixel (count_bits)      COUNT mode
+ *   bucket_out  uint8 overlap class per pixel                COUNT mode
+ *   rgba_out    4 x uint8 per pixel, lut[bucket]             COUNT mode
+ *   mean_out    float32 mean depth per pixel                 MEAN_DEPTH mode
+ * lut_rgba: 256 x 4 bytes in host memory, or NULL for the default ramp
+ * b -> (255-b, 255-b, 255, 255).
+ * out_on_device = 1: the outputs are device pointers; the render is queued on
+ * the compute stream and the call returns without waiting (an underflow is
+ * then reported by composite_sync).  out_on_device = 0: host pointers; the
+ * call waits (bounded) until they are written and reports an underflow.
+ * Ends the borrow of every member passed so far when out_on_device = 0. */
+int composite_render(composite_ctx *ctx, void *counts_out, uint8_t *bucket_out,
+                     uint8_t *rgba_out, float *mean_out, int32_t out_on_device,
+                     const uint8_t *lut_rgba);
+
+/* Waits (bounded) until every queued copy and kernel of the context has
+ * finished; returns CPT_EUNDERFLOW if a remove underflowed, CPT_ETIMEOUT if
+ * the wait ran out, and ends the borrow of every member passed so far. */
+int composite_sync(composite_ctx *ctx);
+
+/* *n_out = N, the number of members in the multiset. */
+int composite_member_count(const composite_ctx *ctx, int64_t *n_out);
+
+/* With config.trace = 1: copies up to `capacity` records of 3 floats
+ * {kind, start_ms, end_ms} into `records` (host memory), kind 0 = upload,
+ * 1 = layout conversion, 2 = accumulation kernel, times relative to the
+ * first traced event since the last composite_clear.  Waits (bounded) for
+ * the traced work.  *n_out = records available (may exceed capacity). */
+int composite_trace_read(composite_ctx *ctx, float *records, int32_t capacity, int32_t *n_out);
+
+/* Waits (bounded) for the context's work and frees everything it owns.
+ * NULL is accepted.  The context pointer is invalid afterwards. */
+int composite_end(composite_ctx *ctx);
+
+/* Message of the last error on ctx (or of the last failed composite_begin
+ * on this thread when ctx is NULL).  Owned by the library; valid until the
+ * next call on the same context. */
+const char *composite_last_error(const composite_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* COMPOSITE_H */

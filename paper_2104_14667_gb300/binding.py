@@ -1,0 +1,334 @@
+"""Thin ctypes binding of include/composite.h.
+
+Argument marshalling only: every step of the composite runs in
+libcomposite.so.  Functions keep the C names; arrays may be torch tensors
+(CUDA, pinned or pageable CPU) or numpy arrays, passed by pointer with their
+strides.  There is no fallback: if the library is missing, loading fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+CPT_OK = 0
+CPT_EINVAL = -1
+CPT_ENOMEM = -2
+CPT_ECUDA = -3
+CPT_ESTATE = -4
+CPT_EUNDERFLOW = -5
+CPT_ETIMEOUT = -6
+STATUS_NAMES = {0: "CPT_OK", -1: "CPT_EINVAL", -2: "CPT_ENOMEM", -3: "CPT_ECUDA",
+                -4: "CPT_ESTATE", -5: "CPT_EUNDERFLOW", -6: "CPT_ETIMEOUT"}
+
+CPT_READ_LINEAR, CPT_READ_TEXTURE, CPT_READ_TMA = 0, 1, 2
+READ_PATHS = {"linear": CPT_READ_LINEAR, "texture": CPT_READ_TEXTURE, "tma": CPT_READ_TMA}
+CPT_MODE_COUNT, CPT_MODE_MEAN_DEPTH = 0, 1
+
+HEADER = os.path.join(_build.INCLUDE, "composite.h")
+
+
+class CompositeError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {message}")
+        self.code = code
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("read_path", ctypes.c_int32),
+        ("staging_buffers", ctypes.c_int32),
+        ("chunk_members", ctypes.c_int32),
+        ("count_bits", ctypes.c_int32),
+        ("mode", ctypes.c_int32),
+        ("trace", ctypes.c_int32),
+        ("pinned_ring_bytes", ctypes.c_int64),
+        ("cuda_stream", ctypes.c_void_p),
+        ("wait_timeout_ms", ctypes.c_int64),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(build_if_missing: bool = False) -> ctypes.CDLL:
+    """Loads libcomposite.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(_build.LIB_PATH):
+            raise RuntimeError(f"{_build.LIB_PATH} is not built; run __graft_entry__.build()")
+        lib = ctypes.CDLL(_build.LIB_PATH)
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        sig = {
+            "composite_default_config": (ctypes.c_int, [ctypes.POINTER(Config)]),
+            "composite_begin": (ctypes.c_int, [ctypes.POINTER(vp), i32, i32, ctypes.POINTER(Config)]),
+            "composite_clear": (ctypes.c_int, [vp]),
+            "composite_add_members": (ctypes.c_int, [vp, vp, i32, i64, i32]),
+            "composite_remove_members": (ctypes.c_int, [vp, vp, i32, i64, i32]),
+            "composite_render": (ctypes.c_int, [vp, vp, vp, vp, vp, i32, vp]),
+            "composite_sync": (ctypes.c_int, [vp]),
+            "composite_member_count": (ctypes.c_int, [vp, ctypes.POINTER(i64)]),
+            "composite_trace_read": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_float), i32,
+                                                    ctypes.POINTER(i32)]),
+            "composite_end": (ctypes.c_int, [vp]),
+            "composite_last_error": (ctypes.c_char_p, [vp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def declared_functions() -> list[str]:
+    """Every function the public header declares."""
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(composite_\w+)\s*\(", text, re.M)))
+
+
+# --- marshalling helpers ----------------------------------------------------
+
+def _raster_view(a):
+    """(pointer, n, height, width, member_stride_bytes, row_pitch_bytes, dtype, keepalive)."""
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(a, torch.Tensor):
+        t = a if a.dim() == 3 else a.unsqueeze(0)
+        if t.dim() != 3 or t.stride(2) != 1:
+            raise ValueError("rasters must be [n, H, W] (or [H, W]) with contiguous rows")
+        item = t.element_size()
+        dtype = {torch.uint8: np.uint8, torch.float32: np.float32}.get(t.dtype)
+        if dtype is None:
+            raise ValueError("rasters must be uint8 masks or float32 depths")
+        return (t.data_ptr(), t.shape[0], t.shape[1], t.shape[2], t.stride(0) * item,
+                t.stride(1) * item, dtype, t)
+    arr = np.asarray(a)
+    if arr.ndim == 2:
+        arr = arr[None]
+    if arr.ndim != 3 or arr.strides[2] != arr.itemsize:
+        raise ValueError("rasters must be [n, H, W] (or [H, W]) with contiguous rows")
+    if arr.dtype not in (np.uint8, np.float32):
+        raise ValueError("rasters must be uint8 masks or float32 depths")
+    return (arr.ctypes.data, arr.shape[0], arr.shape[1], arr.shape[2], arr.strides[0],
+            arr.strides[1], arr.dtype.type, arr)
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if not a.is_contiguous():
+                raise ValueError("outputs must be contiguous")
+            return a.data_ptr()
+    except ImportError:  # pragma: no cover
+        pass
+    if not a.flags.c_contiguous:
+        raise ValueError("outputs must be contiguous")
+    return a.ctypes.data
+
+
+def _on_device(*arrays) -> int:
+    dev = None
+    for a in arrays:
+        if a is None:
+            continue
+        is_dev = bool(getattr(a, "is_cuda", False))
+        if dev is None:
+            dev = is_dev
+        elif dev != is_dev:
+            raise ValueError("outputs must all be device tensors or all host arrays")
+    return 1 if dev else 0
+
+
+def _check(lib, ctx, rc):
+    if rc != CPT_OK:
+        msg = lib.composite_last_error(ctx)
+        raise CompositeError(rc, msg.decode() if msg else "")
+    return rc
+
+
+# --- the C functions, same names ---------------------------------------------
+
+def composite_default_config() -> Config:
+    cfg = Config()
+    lib = load()
+    _check(lib, None, lib.composite_default_config(ctypes.byref(cfg)))
+    return cfg
+
+
+def composite_begin(width: int, height: int, cfg: Config | None = None) -> ctypes.c_void_p:
+    lib = load()
+    ctx = ctypes.c_void_p()
+    rc = lib.composite_begin(ctypes.byref(ctx), int(width), int(height),
+                             ctypes.byref(cfg) if cfg is not None else None)
+    _check(lib, None, rc)
+    return ctx
+
+
+def composite_clear(ctx) -> None:
+    lib = load()
+    _check(lib, ctx, lib.composite_clear(ctx))
+
+
+def _apply(fn_name, ctx, members):
+    lib = load()
+    ptr, n, _, _, stride, pitch, _, _ = _raster_view(members)
+    _check(lib, ctx, getattr(lib, fn_name)(ctx, ptr, n, stride, pitch))
+
+
+def composite_add_members(ctx, members) -> None:
+    _apply("composite_add_members", ctx, members)
+
+
+def composite_remove_members(ctx, members) -> None:
+    _apply("composite_remove_members", ctx, members)
+
+
+def composite_render(ctx, counts_out=None, bucket_out=None, rgba_out=None, mean_out=None,
+                     lut=None) -> None:
+    lib = load()
+    on_dev = _on_device(counts_out, bucket_out, rgba_out, mean_out)
+    lut_arr = None
+    if lut is not None:
+        lut_arr = np.ascontiguousarray(np.asarray(lut, dtype=np.uint8).reshape(256, 4))
+    rc = lib.composite_render(ctx, _ptr(counts_out), _ptr(bucket_out), _ptr(rgba_out), _ptr(mean_out),
+                              on_dev, lut_arr.ctypes.data if lut_arr is not None else None)
+    _check(lib, ctx, rc)
+
+
+def composite_sync(ctx) -> None:
+    lib = load()
+    _check(lib, ctx, lib.composite_sync(ctx))
+
+
+def composite_member_count(ctx) -> int:
+    lib = load()
+    n = ctypes.c_int64()
+    _check(lib, ctx, lib.composite_member_count(ctx, ctypes.byref(n)))
+    return n.value
+
+
+def composite_trace_read(ctx) -> np.ndarray:
+    """float32[n, 3] records {kind, start_ms, end_ms}."""
+    lib = load()
+    n = ctypes.c_int32()
+    _check(lib, ctx, lib.composite_trace_read(ctx, None, 0, ctypes.byref(n)))
+    out = np.zeros((max(n.value, 1), 3), dtype=np.float32)
+    _check(lib, ctx, lib.composite_trace_read(ctx, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                              n.value, ctypes.byref(n)))
+    return out[: n.value]
+
+
+def composite_end(ctx) -> None:
+    lib = load()
+    _check(lib, None, lib.composite_end(ctx))
+
+
+def composite_last_error(ctx=None) -> str:
+    lib = load()
+    msg = lib.composite_last_error(ctx)
+    return msg.decode() if msg else ""
+
+
+def make_config(read_path="linear", staging_buffers=2, chunk_members=16, count_bits=16,
+                mode="count", trace=False, pinned_ring_bytes=0, stream=None,
+                wait_timeout_ms=0) -> Config:
+    cfg = composite_default_config()
+    cfg.read_path = READ_PATHS[read_path] if isinstance(read_path, str) else int(read_path)
+    cfg.staging_buffers = staging_buffers
+    cfg.chunk_members = chunk_members
+    cfg.count_bits = count_bits
+    cfg.mode = {"count": CPT_MODE_COUNT, "mean_depth": CPT_MODE_MEAN_DEPTH}[mode] if isinstance(mode, str) else int(mode)
+    cfg.trace = 1 if trace else 0
+    cfg.pinned_ring_bytes = pinned_ring_bytes
+    cfg.cuda_stream = stream
+    cfg.wait_timeout_ms = wait_timeout_ms
+    return cfg
+
+
+class Composite:
+    """A composite context as a Python object.  Keeps every borrowed raster
+    alive until the next render to host, sync or close, as the C ABI asks."""
+
+    def __init__(self, width: int, height: int, **config):
+        self.width, self.height = int(width), int(height)
+        self.config = make_config(**config)
+        self.ctx = composite_begin(width, height, self.config)
+        self._borrowed = []
+
+    def clear(self):
+        composite_clear(self.ctx)
+
+    def add(self, members):
+        composite_add_members(self.ctx, members)
+        self._borrowed.append(members)
+
+    def remove(self, members):
+        composite_remove_members(self.ctx, members)
+        self._borrowed.append(members)
+
+    @property
+    def n(self) -> int:
+        return composite_member_count(self.ctx)
+
+    def render(self, counts_out=None, bucket_out=None, rgba_out=None, mean_out=None, lut=None):
+        composite_render(self.ctx, counts_out, bucket_out, rgba_out, mean_out, lut)
+        if not _on_device(counts_out, bucket_out, rgba_out, mean_out):
+            self._borrowed.clear()
+
+    def render_host(self, lut=None) -> dict:
+        """Renders into fresh numpy arrays."""
+        h, w = self.height, self.width
+        if self.config.mode == CPT_MODE_MEAN_DEPTH:
+            mean = np.empty((h, w), np.float32)
+            self.render(mean_out=mean)
+            return {"mean": mean}
+        counts = np.empty((h, w), np.uint16 if self.config.count_bits == 16 else np.uint32)
+        bucket = np.empty((h, w), np.uint8)
+        rgba = np.empty((h, w, 4), np.uint8)
+        self.render(counts, bucket, rgba, lut=lut)
+        return {"counts": counts, "bucket": bucket, "rgba": rgba}
+
+    def sync(self):
+        composite_sync(self.ctx)
+        self._borrowed.clear()
+
+    def trace(self) -> np.ndarray:
+        return composite_trace_read(self.ctx)
+
+    def close(self):
+        if self.ctx is not None:
+            ctx, self.ctx = self.ctx, None
+            composite_end(ctx)
+            self._borrowed.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,212 @@
+// count_kernels.cu -- the accumulation step (Fig. 3, step 4: fold member i
+// into the composite) over the linear and texture read paths.
+//
+// One thread owns one 16-byte group of a composite row (16 mask pixels, or
+// 4 float32 depth pixels) and walks the members of the batch, so every
+// member byte is read once with a 16-byte load and the composite is read and
+// written once per launch instead of once per member (the paper's kernel
+// reads and writes the accumulator per member, Fig. 2 step 4).  Mask bytes
+// are turned into per-byte ones and summed four to a 32-bit word; the packed
+// byte counters are widened every 255 members.
+#include "device_common.cuh"
+
+namespace cpt {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kPackedLimit = 255;   // members a packed byte counter can hold
+
+__device__ __forceinline__ uint4 load_stream16(const uint8_t *p) {
+    return __ldcs(reinterpret_cast<const uint4 *>(p));
+}
+
+template <typename CountT>
+__global__ void __launch_bounds__(kThreads)
+count_linear_kernel(RasterBatch b, Plane p, int sign, int *flags, int64_t groups,
+                    int groups_per_row) {
+    CountT *plane = static_cast<CountT *>(p.data);
+    const int64_t stride = b.member_stride;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < groups;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int y = (int)(g / groups_per_row);
+        const int x0 = (int)(g - (int64_t)y * groups_per_row) * 16;
+        const int valid = min(16, p.width - x0);
+        const uint8_t *src = static_cast<const uint8_t *>(b.base) + y * b.row_pitch + x0;
+        uint32_t wide[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) wide[j] = 0;
+        if (valid == 16) {
+            int m = 0;
+            while (m < b.n) {
+                const int mend = min(b.n, m + kPackedLimit);
+                uint32_t k0 = 0, k1 = 0, k2 = 0, k3 = 0;
+                const uint8_t *q = src + (int64_t)m * stride;
+#pragma unroll 8
+                for (; m < mend; ++m) {
+                    const uint4 v = load_stream16(q);
+                    q += stride;
+                    k0 += nonzero_bytes(v.x);
+                    k1 += nonzero_bytes(v.y);
+                    k2 += nonzero_bytes(v.z);
+                    k3 += nonzero_bytes(v.w);
+                }
+                widen16(wide, k0, k1, k2, k3);
+            }
+        } else {
+            // ragged right edge: scalar loads, never past the row's last pixel
+            for (int m = 0; m < b.n; ++m) {
+                const uint8_t *q = src + (int64_t)m * stride;
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    if (j < valid) wide[j] += q[j] != 0;
+            }
+        }
+        apply_count_group<CountT>(plane + (int64_t)y * p.pitch + x0, valid, wide, sign, flags);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+depth_linear_kernel(RasterBatch b, Plane p, int sign, int64_t groups, int groups_per_row) {
+    float *plane = static_cast<float *>(p.data);
+    const int64_t stride = b.member_stride;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < groups;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int y = (int)(g / groups_per_row);
+        const int x0 = (int)(g - (int64_t)y * groups_per_row) * 4;
+        const int valid = min(4, p.width - x0);
+        const uint8_t *src = static_cast<const uint8_t *>(b.base) + y * b.row_pitch + x0 * 4;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        if (valid == 4) {
+            const uint8_t *q = src;
+#pragma unroll 8
+            for (int m = 0; m < b.n; ++m) {
+                const float4 v = __ldcs(reinterpret_cast<const float4 *>(q));
+                q += stride;
+                acc[0] += v.x;
+                acc[1] += v.y;
+                acc[2] += v.z;
+                acc[3] += v.w;
+            }
+        } else {
+            for (int m = 0; m < b.n; ++m) {
+                const float *q = reinterpret_cast<const float *>(src + (int64_t)m * stride);
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (j < valid) acc[j] += q[j];
+            }
+        }
+        apply_depth_group(plane + (int64_t)y * p.pitch + x0, valid, acc, sign);
+    }
+}
+
+// Texture path: member `layer` of the batch is layer `layer` of a layered
+// cudaArray whose texels are 16 bytes (16 mask pixels).  Texels past the
+// raster's right edge hold padding and are masked off.
+template <typename CountT>
+__global__ void __launch_bounds__(kThreads)
+count_texture_kernel(cudaTextureObject_t tex, int n_layers, Plane p, int sign, int *flags,
+                     int64_t groups, int groups_per_row) {
+    CountT *plane = static_cast<CountT *>(p.data);
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < groups;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int y = (int)(g / groups_per_row);
+        const int gx = (int)(g - (int64_t)y * groups_per_row);
+        const int x0 = gx * 16;
+        const int valid = min(16, p.width - x0);
+        const uint32_t m0 = valid_byte_mask(0, valid), m1 = valid_byte_mask(1, valid);
+        const uint32_t m2 = valid_byte_mask(2, valid), m3 = valid_byte_mask(3, valid);
+        const float u = gx + 0.5f, v = y + 0.5f;
+        uint32_t k0 = 0, k1 = 0, k2 = 0, k3 = 0;
+#pragma unroll 8
+        for (int layer = 0; layer < n_layers; ++layer) {
+            const uint4 t = tex2DLayered<uint4>(tex, u, v, layer);
+            k0 += nonzero_bytes(t.x) & m0;
+            k1 += nonzero_bytes(t.y) & m1;
+            k2 += nonzero_bytes(t.z) & m2;
+            k3 += nonzero_bytes(t.w) & m3;
+        }
+        uint32_t wide[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) wide[j] = 0;
+        widen16(wide, k0, k1, k2, k3);
+        apply_count_group<CountT>(plane + (int64_t)y * p.pitch + x0, valid, wide, sign, flags);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+depth_texture_kernel(cudaTextureObject_t tex, int n_layers, Plane p, int sign, int64_t groups,
+                     int groups_per_row) {
+    float *plane = static_cast<float *>(p.data);
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < groups;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int y = (int)(g / groups_per_row);
+        const int gx = (int)(g - (int64_t)y * groups_per_row);
+        const int x0 = gx * 4;
+        const int valid = min(4, p.width - x0);
+        const float u = gx + 0.5f, v = y + 0.5f;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+        for (int layer = 0; layer < n_layers; ++layer) {
+            const float4 t = tex2DLayered<float4>(tex, u, v, layer);
+            acc[0] += t.x;
+            acc[1] += valid > 1 ? t.y : 0.f;
+            acc[2] += valid > 2 ? t.z : 0.f;
+            acc[3] += valid > 3 ? t.w : 0.f;
+        }
+        apply_depth_group(plane + (int64_t)y * p.pitch + x0, valid, acc, sign);
+    }
+}
+
+inline int64_t blocks_for(int64_t groups) {
+    int64_t blocks = (groups + kThreads - 1) / kThreads;
+    return blocks < 1 ? 1 : (blocks > 0x7FFFFFFF ? 0x7FFFFFFF : blocks);
+}
+
+}  // namespace
+
+cudaError_t launch_count_linear(const RasterBatch &b, const Plane &p, int sign, int *flags,
+                                const DeviceCaps &, cudaStream_t s) {
+    const int gpr = (p.width + 15) / 16;
+    const int64_t groups = (int64_t)gpr * p.height;
+    if (b.n <= 0 || groups == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)blocks_for(groups);
+    if (p.count_bits == 16)
+        count_linear_kernel<uint16_t><<<grid, kThreads, 0, s>>>(b, p, sign, flags, groups, gpr);
+    else
+        count_linear_kernel<uint32_t><<<grid, kThreads, 0, s>>>(b, p, sign, flags, groups, gpr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_depth_linear(const RasterBatch &b, const Plane &p, int sign, int *,
+                                const DeviceCaps &, cudaStream_t s) {
+    const int gpr = (p.width + 3) / 4;
+    const int64_t groups = (int64_t)gpr * p.height;
+    if (b.n <= 0 || groups == 0) return cudaSuccess;
+    depth_linear_kernel<<<(unsigned)blocks_for(groups), kThreads, 0, s>>>(b, p, sign, groups, gpr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_texture(cudaTextureObject_t tex, int n_layers, const Plane &p, int sign,
+                                 int *flags, const DeviceCaps &, cudaStream_t s) {
+    const int gpr = (p.width + 15) / 16;
+    const int64_t groups = (int64_t)gpr * p.height;
+    if (n_layers <= 0 || groups == 0) return cudaSuccess;
+    if (n_layers > kPackedLimit) return cudaErrorInvalidValue;
+    const unsigned grid = (unsigned)blocks_for(groups);
+    if (p.count_bits == 16)
+        count_texture_kernel<uint16_t><<<grid, kThreads, 0, s>>>(tex, n_layers, p, sign, flags, groups, gpr);
+    else
+        count_texture_kernel<uint32_t><<<grid, kThreads, 0, s>>>(tex, n_layers, p, sign, flags, groups, gpr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_depth_texture(cudaTextureObject_t tex, int n_layers, const Plane &p, int sign,
+                                 int *, const DeviceCaps &, cudaStream_t s) {
+    const int gpr = (p.width + 3) / 4;
+    const int64_t groups = (int64_t)gpr * p.height;
+    if (n_layers <= 0 || groups == 0) return cudaSuccess;
+    depth_texture_kernel<<<(unsigned)blocks_for(groups), kThreads, 0, s>>>(tex, n_layers, p, sign, groups, gpr);
+    return cudaGetLastError();
+}
+
+}  // namespace cpt

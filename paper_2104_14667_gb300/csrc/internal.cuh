@@ -1,0 +1,72 @@
+// internal.cuh -- declarations shared by the library's translation units.
+// Not installed; the public interface is include/composite.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda.h>
+#include <stdint.h>
+
+namespace cpt {
+
+// Device error flags (int32 each), cleared by composite_clear.
+enum FlagIndex { kFlagUnderflow = 0, kFlagTimeout = 1, kFlagCount = 4 };
+
+// A raster batch as a kernel sees it: n rasters of height rows, row y of
+// member m at base + m * member_stride + y * row_pitch (bytes).
+struct RasterBatch {
+    const void *base;
+    int64_t member_stride;
+    int64_t row_pitch;
+    int32_t n;
+};
+
+// The composite plane: height rows of `pitch` elements (pitch is width
+// rounded up to one 16-byte vector), element uint16/uint32 counts or float32
+// depth sums.
+struct Plane {
+    void *data;
+    int64_t pitch;      // elements
+    int32_t width;
+    int32_t height;
+    int32_t count_bits; // 16, 32, or 0 for float32 sums
+};
+
+struct DeviceCaps {
+    int num_sms;
+};
+
+// Linear read path: 16-byte loads straight from the batch (device memory).
+cudaError_t launch_count_linear(const RasterBatch &b, const Plane &p, int sign, int *flags,
+                                const DeviceCaps &caps, cudaStream_t s);
+cudaError_t launch_depth_linear(const RasterBatch &b, const Plane &p, int sign, int *flags,
+                                const DeviceCaps &caps, cudaStream_t s);
+
+// Texture read path: a layered cudaArray with 16-byte texels (uint4 for
+// masks, float4 for depths); n_layers members.
+cudaError_t launch_count_texture(cudaTextureObject_t tex, int n_layers, const Plane &p, int sign,
+                                 int *flags, const DeviceCaps &caps, cudaStream_t s);
+cudaError_t launch_depth_texture(cudaTextureObject_t tex, int n_layers, const Plane &p, int sign,
+                                 int *flags, const DeviceCaps &caps, cudaStream_t s);
+
+// TMA read path: tensor map over the batch, tiles staged in shared memory.
+// The tensor map must come from encode_tma_map for the same batch.
+cudaError_t launch_count_tma(const CUtensorMap &map, const RasterBatch &b, const Plane &p, int sign,
+                             int *flags, uint64_t timeout_ns, const DeviceCaps &caps, cudaStream_t s);
+cudaError_t launch_depth_tma(const CUtensorMap &map, const RasterBatch &b, const Plane &p, int sign,
+                             int *flags, uint64_t timeout_ns, const DeviceCaps &caps, cudaStream_t s);
+// Returns 0 on success; a CUresult otherwise.  elem_bytes 1 (masks) or 4.
+int encode_tma_map(CUtensorMap *map, const RasterBatch &b, int width, int height, int elem_bytes);
+// Requirements of the TMA path for a batch (alignment of base and strides).
+bool tma_compatible(const RasterBatch &b);
+
+// Render: counts -> dense counts / bucket / rgba, or sums -> mean.
+struct Lut {
+    uint32_t rgba[256];
+};
+cudaError_t launch_render_counts(const Plane &p, uint64_t n_members, void *counts_out,
+                                 uint8_t *bucket_out, uint32_t *rgba_out, const Lut &lut,
+                                 const DeviceCaps &caps, cudaStream_t s);
+cudaError_t launch_render_mean(const Plane &p, uint64_t n_members, float *mean_out,
+                               const DeviceCaps &caps, cudaStream_t s);
+
+}  // namespace cpt

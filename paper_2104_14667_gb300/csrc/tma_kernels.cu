@@ -1,0 +1,338 @@
+// tma_kernels.cu -- the accumulation step over the TMA read path.
+//
+// The batch is described to the tensor memory accelerator as a 3-D tensor
+// (x = pixel within a row, y = row, z = member).  A persistent CTA walks its
+// composite tiles (128 bytes x 16 rows); for every tile one producer thread
+// streams boxes of 128 B x 16 rows x 8 members through a ring of shared-memory
+// stages with cp.async.bulk.tensor, and four consumer warps fold each box
+// into registers, one 16-byte group per thread.  Boxes past the raster's
+// edge or the last member are zero filled by the hardware, which counts as
+// "not flooded" and adds 0.0 to a depth sum.  Every mbarrier wait is bounded
+// in time; a wait that runs out raises the timeout flag and the CTA leaves
+// after draining its own copies in flight.
+#include <cudaTypedefs.h>
+
+#include "device_common.cuh"
+
+namespace cpt {
+namespace {
+
+constexpr int kBoxRowBytes = 128;                   // x extent of a box, bytes
+constexpr int kBoxRows = 16;                        // y extent
+constexpr int kBoxMembers = 8;                      // z extent
+constexpr int kMemberPlaneBytes = kBoxRowBytes * kBoxRows;
+constexpr int kBoxBytes = kMemberPlaneBytes * kBoxMembers;   // 16 KiB
+constexpr int kStages = 6;
+constexpr int kConsumers = 128;                      // 8 groups x 16 rows
+constexpr int kThreads = kConsumers + 32;            // + one producer warp
+constexpr int kCtasPerSm = 2;
+
+struct alignas(128) TmaShared {
+    uint8_t stage[kStages][kBoxBytes];
+    uint64_t full[kStages];
+    uint64_t empty[kStages];
+    int abort;
+};
+constexpr size_t kSmemBytes = sizeof(TmaShared) + 128;   // + alignment slack
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for the phase of `bar` with the given parity to complete, for at most
+// timeout_ns, or until another thread of the CTA has given up.
+__device__ __forceinline__ bool wait_bounded(uint64_t *bar, uint32_t parity, uint64_t timeout_ns,
+                                             volatile int *abort) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t deadline = global_ns() + timeout_ns;
+    for (uint32_t i = 1;; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 31u) == 0u && (*abort || global_ns() > deadline)) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load_box(void *dst, const CUtensorMap *map, int x, int y,
+                                             int z, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ uint4 lds16(const uint8_t *p) {
+    return *reinterpret_cast<const uint4 *>(p);
+}
+
+// The producer role: one thread issues every box of the CTA's tiles.
+__device__ void produce(TmaShared &sh, const CUtensorMap *map, int tiles, int tiles_x,
+                        int slabs, int box_x_elems, uint64_t timeout_ns, int *flags) {
+    uint32_t it = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; ok && tile < tiles; tile += gridDim.x) {
+        const int tx = tile % tiles_x, ty = tile / tiles_x;
+        for (int slab = 0; slab < slabs; ++slab, ++it) {
+            const int s = it % kStages;
+            const uint32_t phase = (it / kStages) & 1u;
+            if (!wait_bounded(&sh.empty[s], phase ^ 1u, timeout_ns, &sh.abort)) {
+                ok = false;
+                break;
+            }
+            mbar_arrive_expect_tx(&sh.full[s], kBoxBytes);
+            tma_load_box(sh.stage[s], map, tx * box_x_elems, ty * kBoxRows, slab * kBoxMembers,
+                         &sh.full[s]);
+        }
+    }
+    if (!ok) {
+        flag_set(flags, kFlagTimeout);
+        sh.abort = 1;
+        // Drain: every box still in flight lands before the CTA may exit.
+        const uint32_t first = it > (uint32_t)kStages ? it - kStages : 0u;
+        for (uint32_t j = first; j < it; ++j) {
+            int dummy = 0;
+            wait_bounded(&sh.full[j % kStages], (j / kStages) & 1u, timeout_ns, &dummy);
+        }
+    }
+}
+
+template <typename CountT>
+__global__ void __launch_bounds__(kThreads, kCtasPerSm)
+count_tma_kernel(const __grid_constant__ CUtensorMap map, Plane p, int n_members, int sign,
+                 int *flags, uint64_t timeout_ns) {
+    extern __shared__ uint8_t smem_raw[];
+    TmaShared &sh = *reinterpret_cast<TmaShared *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    const int tiles_x = (p.width + kBoxRowBytes - 1) / kBoxRowBytes;
+    const int tiles = tiles_x * ((p.height + kBoxRows - 1) / kBoxRows);
+    const int slabs = (n_members + kBoxMembers - 1) / kBoxMembers;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&sh.full[s], 1);
+            mbar_init(&sh.empty[s], kConsumers);
+        }
+        sh.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (threadIdx.x >= kConsumers) {
+        if (threadIdx.x == kConsumers)
+            produce(sh, &map, tiles, tiles_x, slabs, kBoxRowBytes, timeout_ns, flags);
+        return;
+    }
+
+    CountT *plane = static_cast<CountT *>(p.data);
+    const int row = threadIdx.x / 8, grp = threadIdx.x % 8;
+    const int offset = row * kBoxRowBytes + grp * 16;
+    uint32_t it = 0;
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int tx = tile % tiles_x, ty = tile / tiles_x;
+        uint32_t wide[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) wide[j] = 0;
+        uint32_t k0 = 0, k1 = 0, k2 = 0, k3 = 0;
+        int packed_members = 0;
+        for (int slab = 0; slab < slabs; ++slab, ++it) {
+            const int s = it % kStages;
+            if (!wait_bounded(&sh.full[s], (it / kStages) & 1u, timeout_ns, &sh.abort)) {
+                flag_set(flags, kFlagTimeout);
+                sh.abort = 1;
+                return;
+            }
+            const uint8_t *box = sh.stage[s] + offset;
+#pragma unroll
+            for (int m = 0; m < kBoxMembers; ++m) {
+                const uint4 v = lds16(box + m * kMemberPlaneBytes);
+                k0 += nonzero_bytes(v.x);
+                k1 += nonzero_bytes(v.y);
+                k2 += nonzero_bytes(v.z);
+                k3 += nonzero_bytes(v.w);
+            }
+            mbar_arrive(&sh.empty[s]);
+            packed_members += kBoxMembers;
+            if (packed_members > 255 - kBoxMembers) {
+                widen16(wide, k0, k1, k2, k3);
+                k0 = k1 = k2 = k3 = 0;
+                packed_members = 0;
+            }
+        }
+        widen16(wide, k0, k1, k2, k3);
+        const int y = ty * kBoxRows + row;
+        const int x0 = tx * kBoxRowBytes + grp * 16;
+        if (y < p.height && x0 < p.width)
+            apply_count_group<CountT>(plane + (int64_t)y * p.pitch + x0, min(16, p.width - x0),
+                                      wide, sign, flags);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, kCtasPerSm)
+depth_tma_kernel(const __grid_constant__ CUtensorMap map, Plane p, int n_members, int sign,
+                 int *flags, uint64_t timeout_ns) {
+    extern __shared__ uint8_t smem_raw[];
+    TmaShared &sh = *reinterpret_cast<TmaShared *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    constexpr int kBoxX = kBoxRowBytes / 4;   // 32 float32 pixels per box row
+    const int tiles_x = (p.width + kBoxX - 1) / kBoxX;
+    const int tiles = tiles_x * ((p.height + kBoxRows - 1) / kBoxRows);
+    const int slabs = (n_members + kBoxMembers - 1) / kBoxMembers;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&sh.full[s], 1);
+            mbar_init(&sh.empty[s], kConsumers);
+        }
+        sh.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (threadIdx.x >= kConsumers) {
+        if (threadIdx.x == kConsumers)
+            produce(sh, &map, tiles, tiles_x, slabs, kBoxX, timeout_ns, flags);
+        return;
+    }
+
+    float *plane = static_cast<float *>(p.data);
+    const int row = threadIdx.x / 8, grp = threadIdx.x % 8;
+    const int offset = row * kBoxRowBytes + grp * 16;
+    uint32_t it = 0;
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int tx = tile % tiles_x, ty = tile / tiles_x;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int slab = 0; slab < slabs; ++slab, ++it) {
+            const int s = it % kStages;
+            if (!wait_bounded(&sh.full[s], (it / kStages) & 1u, timeout_ns, &sh.abort)) {
+                flag_set(flags, kFlagTimeout);
+                sh.abort = 1;
+                return;
+            }
+            const uint8_t *box = sh.stage[s] + offset;
+#pragma unroll
+            for (int m = 0; m < kBoxMembers; ++m) {
+                const float4 v = *reinterpret_cast<const float4 *>(box + m * kMemberPlaneBytes);
+                acc[0] += v.x;
+                acc[1] += v.y;
+                acc[2] += v.z;
+                acc[3] += v.w;
+            }
+            mbar_arrive(&sh.empty[s]);
+        }
+        const int y = ty * kBoxRows + row;
+        const int x0 = tx * kBoxX + grp * 4;
+        if (y < p.height && x0 < p.width)
+            apply_depth_group(plane + (int64_t)y * p.pitch + x0, min(4, p.width - x0), acc, sign);
+    }
+}
+
+template <typename Kernel>
+cudaError_t prepare(Kernel k) {
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        cudaDriverEntryPointQueryResult q;
+        void *ptr = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+    }
+    return fn;
+}
+
+unsigned grid_for(int tiles, const DeviceCaps &caps) {
+    const int cap = caps.num_sms * kCtasPerSm;
+    return (unsigned)(tiles < cap ? tiles : cap);
+}
+
+}  // namespace
+
+bool tma_compatible(const RasterBatch &b) {
+    return (reinterpret_cast<uintptr_t>(b.base) % 16 == 0) && (b.row_pitch % 16 == 0) &&
+           (b.member_stride % 16 == 0) && b.row_pitch < (int64_t(1) << 40) &&
+           b.member_stride < (int64_t(1) << 40);
+}
+
+int encode_tma_map(CUtensorMap *map, const RasterBatch &b, int width, int height, int elem_bytes) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = get_encoder();
+    if (!enc) return CUDA_ERROR_NOT_FOUND;
+    cuuint64_t dims[3] = {(cuuint64_t)width, (cuuint64_t)height, (cuuint64_t)b.n};
+    cuuint64_t strides[2] = {(cuuint64_t)b.row_pitch, (cuuint64_t)b.member_stride};
+    cuuint32_t box[3] = {(cuuint32_t)(kBoxRowBytes / elem_bytes), kBoxRows, kBoxMembers};
+    cuuint32_t estrides[3] = {1, 1, 1};
+    CUresult r = enc(map,
+                     elem_bytes == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                     3, const_cast<void *>(b.base), dims, strides, box, estrides,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return (int)r;
+}
+
+cudaError_t launch_count_tma(const CUtensorMap &map, const RasterBatch &b, const Plane &p, int sign,
+                             int *flags, uint64_t timeout_ns, const DeviceCaps &caps, cudaStream_t s) {
+    if (b.n <= 0) return cudaSuccess;
+    const int tiles = ((p.width + kBoxRowBytes - 1) / kBoxRowBytes) * ((p.height + kBoxRows - 1) / kBoxRows);
+    cudaError_t e;
+    if (p.count_bits == 16) {
+        static cudaError_t prep = prepare(count_tma_kernel<uint16_t>);
+        if (prep != cudaSuccess) return prep;
+        count_tma_kernel<uint16_t><<<grid_for(tiles, caps), kThreads, kSmemBytes, s>>>(
+            map, p, b.n, sign, flags, timeout_ns);
+    } else {
+        static cudaError_t prep = prepare(count_tma_kernel<uint32_t>);
+        if (prep != cudaSuccess) return prep;
+        count_tma_kernel<uint32_t><<<grid_for(tiles, caps), kThreads, kSmemBytes, s>>>(
+            map, p, b.n, sign, flags, timeout_ns);
+    }
+    e = cudaGetLastError();
+    return e;
+}
+
+cudaError_t launch_depth_tma(const CUtensorMap &map, const RasterBatch &b, const Plane &p, int sign,
+                             int *flags, uint64_t timeout_ns, const DeviceCaps &caps, cudaStream_t s) {
+    if (b.n <= 0) return cudaSuccess;
+    const int tiles = ((p.width + 31) / 32) * ((p.height + kBoxRows - 1) / kBoxRows);
+    static cudaError_t prep = prepare(depth_tma_kernel);
+    if (prep != cudaSuccess) return prep;
+    depth_tma_kernel<<<grid_for(tiles, caps), kThreads, kSmemBytes, s>>>(map, p, b.n, sign, flags,
+                                                                          timeout_ns);
+    return cudaGetLastError();
+}
+
+}  // namespace cpt

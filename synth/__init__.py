@@ -144,6 +144,19 @@ def fill_masks(ens: Ensemble, out: np.ndarray, members: range | None = None) -> 
     return out
 
 
+def fill_masks_torch(ens: Ensemble, out, members: range | None = None, terrain_t=None):
+    """As fill_masks, into a torch uint8[n, H, W] tensor on any device: the
+    same float32 comparison terrain < w_m, so the bytes are identical."""
+    import torch
+    idx = range(ens.n) if members is None else members
+    if out.dtype != torch.uint8 or tuple(out.shape[1:]) != (ens.height, ens.width) or out.shape[0] < len(idx):
+        raise ValueError("out must be uint8[n, H, W] with room for every member")
+    t = terrain_t if terrain_t is not None else torch.from_numpy(ens.terrain).to(out.device)
+    for j, m in enumerate(idx):
+        torch.lt(t, float(ens.levels[m]), out=out[j].view(torch.bool))
+    return out
+
+
 def masks(ens: Ensemble) -> np.ndarray:
     """uint8[N, H, W] masks with values in {0, 1}."""
     return fill_masks(ens, np.empty((ens.n, ens.height, ens.width), dtype=np.uint8))

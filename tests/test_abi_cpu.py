@@ -1,0 +1,69 @@
+"""The C ABI without a GPU: the library loads, exports every function the
+header declares, and rejects bad arguments before touching CUDA."""
+import ctypes
+
+import pytest
+
+from paper_2104_14667_gb300 import binding, build
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return binding.load()
+
+
+def test_header_declares_the_boundary():
+    names = binding.declared_functions()
+    for required in ("composite_begin", "composite_add_members", "composite_remove_members",
+                     "composite_render", "composite_end", "composite_clear", "composite_sync",
+                     "composite_member_count", "composite_trace_read", "composite_last_error",
+                     "composite_default_config"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in binding.declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_default_config(lib):
+    cfg = binding.composite_default_config()
+    assert (cfg.read_path, cfg.staging_buffers, cfg.chunk_members, cfg.count_bits, cfg.mode) == (0, 2, 16, 16, 0)
+    assert ctypes.sizeof(binding.Config) == 48
+
+
+@pytest.mark.parametrize("w,h", [(0, 5), (5, 0), (-1, 3)])
+def test_begin_rejects_empty_raster(lib, w, h):
+    with pytest.raises(binding.CompositeError) as e:
+        binding.composite_begin(w, h)
+    assert e.value.code == binding.CPT_EINVAL
+
+
+@pytest.mark.parametrize("field,value", [("read_path", 3), ("staging_buffers", 0), ("staging_buffers", 9),
+                                         ("chunk_members", 0), ("chunk_members", 256), ("count_bits", 8),
+                                         ("mode", 2), ("trace", 2), ("wait_timeout_ms", -1)])
+def test_begin_rejects_bad_config(lib, field, value):
+    cfg = binding.composite_default_config()
+    setattr(cfg, field, value)
+    with pytest.raises(binding.CompositeError) as e:
+        binding.composite_begin(8, 8, cfg)
+    assert e.value.code == binding.CPT_EINVAL
+    assert binding.composite_last_error(None)
+
+
+def test_null_context_is_einval(lib):
+    assert lib.composite_clear(None) == binding.CPT_EINVAL
+    assert lib.composite_add_members(None, None, 1, 64, 8) == binding.CPT_EINVAL
+    assert lib.composite_render(None, None, None, None, None, 0, None) == binding.CPT_EINVAL
+    assert lib.composite_sync(None) == binding.CPT_EINVAL
+    assert lib.composite_end(None) == binding.CPT_OK
+
+
+def test_begin_without_gpu_fails_loudly(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(binding.CompositeError) as e:
+        binding.composite_begin(16, 16)
+    assert e.value.code in (binding.CPT_ECUDA, binding.CPT_ENOMEM)

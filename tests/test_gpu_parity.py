@@ -1,0 +1,254 @@
+"""Parity of the CUDA composite (through the C ABI) with the CPU oracle.
+
+Counts, overlap classes and colours must match bit for bit; the float32 mean
+depth must lie within 1e-5 * N of the FP64 oracle (max abs error).  Every read
+path (linear, texture, TMA) and every input memory kind (device, pinned host,
+pageable host) is covered, with ragged shapes, several staging-buffer counts
+and chunk depths, incremental add/remove, underflow, N = 0 and custom tables.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+from paper_2104_14667_gb300 import binding  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+PATHS = ["linear", "texture", "tma"]
+KINDS = ["device", "pinned", "pageable"]
+
+
+def as_kind(a: np.ndarray, kind: str):
+    if kind == "pageable":
+        return a
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    return t.pin_memory() if kind == "pinned" else t.cuda()
+
+
+def expected(masks_np, lut=None, n=None):
+    c = oracle.count(masks_np)
+    n = masks_np.shape[0] if n is None else n
+    b = oracle.bucket(c, n)
+    return c, b, oracle.rgba(b, lut)
+
+
+def check_counts(comp, masks_np, lut=None, n=None):
+    got = comp.render_host(lut=lut)
+    c, b, rgba = expected(masks_np, lut, n)
+    np.testing.assert_array_equal(got["counts"].astype(np.int64), c)
+    np.testing.assert_array_equal(got["bucket"], b)
+    np.testing.assert_array_equal(got["rgba"], rgba)
+
+
+SHAPES = [(1024, 1024, 16), (13, 7, 5), (1, 1, 3), (4097, 3, 9), (100, 37, 40), (48, 33, 300)]
+
+
+@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("w,h,n", SHAPES)
+def test_count_parity(path, kind, w, h, n):
+    m = synth.masks(synth.ensemble(100 + w + h + n, w, h, n)) if w * h > 64 else synth.random_masks(7, n, h, w)
+    with binding.Composite(w, h, read_path=path, staging_buffers=2, chunk_members=16) as comp:
+        comp.add(as_kind(m, kind))
+        assert comp.n == n
+        check_counts(comp, m)
+
+
+@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("k,c", [(1, 1), (1, 16), (2, 7), (3, 5), (4, 255), (8, 64)])
+def test_staging_and_chunk_depths(path, k, c):
+    w, h, n = 77, 45, 131
+    m = synth.scramble_nonzero(synth.masks(synth.ensemble(9, w, h, n)), 9)
+    with binding.Composite(w, h, read_path=path, staging_buffers=k, chunk_members=c) as comp:
+        comp.add(as_kind(m, "pinned"))
+        check_counts(comp, m)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_device_rasters_read_in_place_with_padded_rows(path):
+    # rows padded to 64 bytes, members padded by one extra row: aligned, so
+    # the linear and TMA paths read the caller's memory directly
+    w, h, n = 50, 29, 21
+    m = synth.random_masks(21, n, h, w, density=0.4)
+    big = torch.zeros((n, h + 1, 64), dtype=torch.uint8, device="cuda")
+    big[:, :h, :w] = torch.from_numpy(m).cuda()
+    view = big[:, :h, :w]
+    with binding.Composite(w, h, read_path=path) as comp:
+        comp.add(view)
+        check_counts(comp, m)
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_strided_host_rasters(kind):
+    w, h, n = 31, 17, 12
+    m = synth.random_masks(22, n, h, w)
+    big = np.full((n, h + 2, 40), 255, np.uint8)   # padding bytes are nonzero on purpose
+    big[:, :h, :w] = m
+    if kind == "pageable":
+        src = big[:, :h, :w]
+    else:
+        t = torch.from_numpy(big)
+        t = t.pin_memory() if kind == "pinned" else t.cuda()
+        src = t[:, :h, :w]
+    with binding.Composite(w, h, read_path="linear") as comp:
+        comp.add(src)
+        check_counts(comp, m)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_nonzero_bytes_and_32bit_counts(path):
+    w, h, n = 96, 40, 70
+    m = synth.scramble_nonzero(synth.random_masks(23, n, h, w), 23)
+    with binding.Composite(w, h, read_path=path, count_bits=32) as comp:
+        comp.add(as_kind(m, "device"))
+        got = comp.render_host()
+        assert got["counts"].dtype == np.uint32
+        check_counts(comp, m)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_add_remove_sequence_equals_recompute(path):
+    w, h = 70, 33
+    a = synth.random_masks(24, 20, h, w)
+    b = synth.random_masks(25, 11, h, w)
+    with binding.Composite(w, h, read_path=path, chunk_members=8) as comp:
+        comp.add(as_kind(a, "device"))
+        comp.add(as_kind(b, "pinned"))
+        comp.remove(as_kind(a[:10], "pageable"))
+        comp.remove(as_kind(a[10:], "device"))
+        assert comp.n == 11
+        check_counts(comp, b)
+
+
+def test_empty_composite_renders_white():
+    with binding.Composite(20, 10) as comp:
+        got = comp.render_host()
+        assert not got["counts"].any() and not got["bucket"].any()
+        assert (got["rgba"] == 255).all()
+        comp.add(as_kind(synth.random_masks(1, 3, 10, 20), "device"))
+        comp.remove(as_kind(synth.random_masks(1, 3, 10, 20), "pinned"))
+        assert comp.n == 0
+        got = comp.render_host()
+        assert not got["counts"].any() and (got["rgba"] == 255).all()
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_underflow_poisons_until_clear(path):
+    w, h = 40, 20
+    a = synth.random_masks(26, 2, h, w, density=0.5)
+    with binding.Composite(w, h, read_path=path) as comp:
+        comp.add(as_kind(a[:1], "device"))
+        comp.remove(as_kind(a[1:], "device"))
+        with pytest.raises(binding.CompositeError) as e:
+            comp.render_host()
+        assert e.value.code == binding.CPT_EUNDERFLOW
+        with pytest.raises(binding.CompositeError) as e:
+            comp.add(as_kind(a, "device"))
+        assert e.value.code == binding.CPT_ESTATE
+        comp.clear()
+        comp.add(as_kind(a, "device"))
+        check_counts(comp, a)
+
+
+def test_member_limits_rejected_on_host():
+    with binding.Composite(16, 1) as comp:
+        with pytest.raises(binding.CompositeError) as e:
+            comp.remove(np.zeros((1, 1, 16), np.uint8))
+        assert e.value.code == binding.CPT_EINVAL
+        ones = torch.ones((65535, 1, 16), dtype=torch.uint8, device="cuda")
+        comp.add(ones)
+        with pytest.raises(binding.CompositeError) as e:
+            comp.add(ones[:1])
+        assert e.value.code == binding.CPT_EINVAL
+        assert comp.n == 65535
+        got = comp.render_host()
+        assert (got["counts"] == 65535).all() and (got["bucket"] == 255).all()
+
+
+def test_custom_lut():
+    w, h, n = 33, 9, 6
+    m = synth.random_masks(27, n, h, w)
+    lut = np.random.default_rng(5).integers(0, 256, (256, 4), dtype=np.uint8)
+    with binding.Composite(w, h) as comp:
+        comp.add(as_kind(m, "device"))
+        check_counts(comp, m, lut=lut)
+
+
+def test_render_to_device_outputs_matches_host():
+    w, h, n = 64, 48, 25
+    m = synth.random_masks(28, n, h, w)
+    with binding.Composite(w, h) as comp:
+        comp.add(as_kind(m, "pinned"))
+        counts = torch.empty((h, w), dtype=torch.int16, device="cuda")
+        bucket = torch.empty((h, w), dtype=torch.uint8, device="cuda")
+        rgba = torch.empty((h, w, 4), dtype=torch.uint8, device="cuda")
+        comp.render(counts, bucket, rgba)
+        comp.sync()
+        c, b, col = expected(m)
+        np.testing.assert_array_equal(counts.cpu().numpy().view(np.uint16).astype(np.int64), c)
+        np.testing.assert_array_equal(bucket.cpu().numpy(), b)
+        np.testing.assert_array_equal(rgba.cpu().numpy(), col)
+
+
+@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("w,h,n", [(256, 256, 256), (13, 7, 5), (37, 129, 19)])
+def test_mean_depth_parity(path, kind, w, h, n):
+    d = synth.depths(synth.ensemble(200 + w + n, w, h, n)) if w * h > 100 else synth.random_depths(3, n, h, w)
+    with binding.Composite(w, h, read_path=path, mode="mean_depth", chunk_members=16) as comp:
+        comp.add(as_kind(d, kind))
+        got = comp.render_host()["mean"]
+    ref = oracle.mean_depth(d)
+    assert np.abs(got.astype(np.float64) - ref).max() <= 1e-5 * n
+
+
+def test_mean_depth_single_member_exact_and_remove():
+    w, h = 45, 21
+    d = synth.random_depths(4, 6, h, w)
+    with binding.Composite(w, h, mode="mean_depth") as comp:
+        comp.add(as_kind(d[:1], "device"))
+        np.testing.assert_array_equal(comp.render_host()["mean"], d[0])
+        comp.add(as_kind(d[1:], "pinned"))
+        comp.remove(as_kind(d[:3], "pageable"))
+        got = comp.render_host()["mean"]
+    ref = oracle.mean_depth(d[3:])
+    assert np.abs(got.astype(np.float64) - ref).max() <= 1e-5 * 6
+
+
+def test_trace_records_upload_and_kernel_intervals():
+    w, h, n = 256, 128, 64
+    m = synth.random_masks(29, n, h, w)
+    with binding.Composite(w, h, chunk_members=8, staging_buffers=2, trace=True) as comp:
+        comp.add(as_kind(m, "pinned"))
+        rec = comp.trace()
+        check_counts(comp, m)
+    kinds = rec[:, 0].astype(int)
+    assert (kinds == 0).sum() == 8 and (kinds == 2).sum() == 8
+    assert np.all(rec[:, 2] >= rec[:, 1]) and rec[:, 1].min() >= 0.0
+
+
+def test_nested_threshold_identity_at_streaming_size():
+    # 4096 x 4096, 64 members streamed from pinned host memory through two
+    # staging buffers of 32 members: every pixel against the independent
+    # binary-search count, sampled rows against the oracle
+    w = h = 4096
+    n = 64
+    ens = synth.ensemble(2, w, h, n)
+    host = torch.empty((n, h, w), dtype=torch.uint8).pin_memory()
+    synth.fill_masks(ens, host.numpy())
+    with binding.Composite(w, h, chunk_members=32, staging_buffers=2) as comp:
+        comp.add(host)
+        got = comp.render_host()
+    sorted_w = np.sort(ens.levels)
+    ident = n - np.searchsorted(sorted_w, ens.terrain.ravel(), side="right").reshape(h, w)
+    np.testing.assert_array_equal(got["counts"].astype(np.int64), ident)
+    rows = [0, 1, 2047, 4095]
+    sample = host.numpy()[:, rows, :]
+    c = oracle.count(sample)
+    b = oracle.bucket(c, n)
+    np.testing.assert_array_equal(got["counts"][rows].astype(np.int64), c)
+    np.testing.assert_array_equal(got["bucket"][rows], b)
+    np.testing.assert_array_equal(got["rgba"][rows], oracle.rgba(b))

@@ -1,0 +1,427 @@
+"""Benchmark of the iterative ensemble composite on one GB300 (or N replicas).
+
+Workload (the streaming-sweep point this line is quoted on): 1024 flood masks
+of 4096 x 4096 uint8 from the seeded terrain generator (synth), composited
+into uint16 counts, overlap classes and RGBA colours.  One step is one pass
+of the hot path over the whole ensemble: clear, accumulate every member,
+render.
+
+* ``value``: member-pixels/s with the ensemble resident in HBM (the kernel
+  reads the members in place); timed with CUDA events on the compute stream.
+* ``e2e``: the same metric through the C ABI from pinned HOST memory: every
+  step uploads all members through two staging buffers (copy stream,
+  events) and reads the rendered buckets and colours back to the host.
+* ``roofline``: the accumulation kernel against the measured HBM copy peak,
+  its launches timed with CUDA events inside the timed region.
+* ``cpu_baseline``: the CPU oracle, single threaded, on a bounded sample of
+  the same workload.
+
+``--impl reference`` times the CPU oracle itself on the same workload (each
+step a bounded sample of members) and prints its own line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "composited member-pixels/s"
+UNIT = "member-px/s"
+L2_BYTES = 129 * 2 ** 20
+HBM_FALLBACK_GBS = 6800.0
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--width", type=int, default=4096)
+    p.add_argument("--height", type=int, default=4096)
+    p.add_argument("--members", type=int, default=1024)
+    p.add_argument("--chunk", type=int, default=32)
+    p.add_argument("--staging", type=int, default=2)
+    p.add_argument("--read-path", default="linear", choices=["linear", "texture", "tma"])
+    p.add_argument("--seed", type=int, default=2)
+    p.add_argument("--cpu-seconds", type=float, default=10.0,
+                   help="target CPU time of the oracle baseline sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the run."""
+
+    QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.rows = []
+        self.windows = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append((time.time(), [x.strip() for x in line.split(",")]))
+
+    def window(self, t0, t1):
+        self.windows.append((t0, t1))
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        inside = [r for t, r in self.rows if any(a - 0.15 <= t <= b + 0.15 for a, b in self.windows)]
+        rows = inside or [r for _, r in self.rows]
+        if not rows:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[2]) for r in rows if len(r) > 9 and num(r[2]) is not None]
+        mx = [num(r[3]) for r in rows if len(r) > 9 and num(r[3]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows if len(r) > 9 for i in range(4)
+                          if r[6 + i].lower() in ("active", "1")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows), "samples_in_timed_region": len(inside)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": HBM_FALLBACK_GBS}, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in ("count_kernels.cu", "device_common.cuh"):
+        with open(os.path.join(ROOT, "paper_2104_14667_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload_key: str):
+    """DRAM bytes per launch of the accumulation kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "count_linear_4096x4096x1024.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    src = cnt = None
+    for line in text.splitlines():
+        if line.startswith("kernel_source_sha256_16:"):
+            src = line.split(":", 1)[1].strip()
+        if line.startswith(f"dram_bytes_per_launch[{workload_key}]:"):
+            cnt = float(line.split(":", 1)[1].split()[0])
+    if src != kernel_source_hash() or cnt is None:
+        return None
+    return cnt
+
+
+def make_ensemble(args, torch, device):
+    import synth
+    ens = synth.ensemble(args.seed, args.width, args.height, args.members)
+    terrain_dev = torch.from_numpy(ens.terrain).to(device)
+    dev = torch.empty((args.members, args.height, args.width), dtype=torch.uint8, device=device)
+    synth.fill_masks_torch(ens, dev, terrain_t=terrain_dev)
+    del terrain_dev
+    return ens, dev
+
+
+def cpu_oracle_rate(ens, members: int, target_s: float, batch: int = 4):
+    """The oracle (plain C, one thread) over batches of members of the same
+    workload until about target_s seconds of CPU work; member-px/s."""
+    import oracle
+    import synth
+    h, w = ens.height, ens.width
+    buf = np.empty((batch, h, w), dtype=np.uint8)
+    counts = np.zeros((h, w), dtype=np.int64)
+    done, spent = 0, 0.0
+    while done == 0 or (spent < target_s and done < members):
+        b = min(batch, members - done)
+        synth.fill_masks(ens, buf[:b], range(done, done + b))
+        t0 = time.perf_counter()
+        oracle.count_apply(counts, buf[:b], 1)
+        spent += time.perf_counter() - t0
+        done += b
+    return done * w * h / spent, done, spent
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import synth
+    ens = synth.ensemble(args.seed, args.width, args.height, args.members)
+    per_step = max(1, min(args.members, 4))
+    rates = []
+    for i in range(args.warmup + args.steps):
+        rate, done, spent = cpu_oracle_rate(ens, per_step, 0.0, batch=per_step)
+        if i >= args.warmup:
+            rates.append((done, spent))
+    total_px = sum(d for d, _ in rates) * args.width * args.height
+    total_s = sum(s for _, s in rates)
+    value = total_px / total_s
+    sample = f"{per_step} of {args.members} members of the {args.width}x{args.height} workload per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic",
+        "config": workload_config(args),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args):
+    return {"workload": f"streaming sweep point: {args.members} flood masks of {args.width}x{args.height} "
+                        f"uint8, uint16 counts, bucket + RGBA render",
+            "width": args.width, "height": args.height, "members": args.members,
+            "read_path": args.read_path, "chunk_members": args.chunk, "staging_buffers": args.staging,
+            "seed": args.seed, "l2": "inputs larger than L2 (no flush needed)"}
+
+
+def link_peak_gbs(torch, device, nbytes=1 << 30, reps=5):
+    """Pinned host -> device cudaMemcpyAsync rate, best of reps (GB/s)."""
+    src = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    dst = torch.empty(nbytes, dtype=torch.uint8, device=device)
+    s = torch.cuda.Stream(device)
+    best = 0.0
+    for _ in range(reps + 1):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(s):
+            a.record()
+            dst.copy_(src, non_blocking=True)
+            b.record()
+        b.synchronize()
+        best = max(best, nbytes / (a.elapsed_time(b) * 1e-3) / 1e9)
+    del src, dst
+    return best
+
+
+def run_ours(args):
+    import torch
+    from paper_2104_14667_gb300 import binding, metrics
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    binding.load()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    W, H, N = args.width, args.height, args.members
+    P = W * H
+    ens, dev_masks = make_ensemble(args, torch, device)
+    # a real (non-NULL) stream: the library runs its kernels on it, and the
+    # CUDA events below are recorded on the same stream
+    stream = torch.cuda.Stream(device)
+    torch.cuda.set_stream(stream)
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+
+    # ---- value: device-resident ensemble ---------------------------------
+    comp = binding.Composite(W, H, read_path=args.read_path, staging_buffers=args.staging,
+                             chunk_members=args.chunk, stream=stream.cuda_stream)
+    bucket = torch.empty((H, W), dtype=torch.uint8, device=device)
+    rgba = torch.empty((H, W, 4), dtype=torch.uint8, device=device)
+    k_events = []
+
+    def device_step(timed: bool):
+        comp.clear()
+        if timed:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+        comp.add(dev_masks)
+        if timed:
+            b.record(stream)
+            k_events.append((a, b))
+        comp.render(bucket_out=bucket, rgba_out=rgba)
+
+    for _ in range(args.warmup):
+        device_step(False)
+    comp.sync()
+    barrier()
+    t_start, t_stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    w0 = time.time()
+    t_start.record(stream)
+    for _ in range(args.steps):
+        device_step(True)
+    t_stop.record(stream)
+    barrier()
+    w1 = time.time()
+    if sampler:
+        sampler.window(w0, w1)
+    comp.sync()
+    dev_ms = t_start.elapsed_time(t_stop)
+    dev_ms = max_over_ranks(dev_ms)
+    kernel_ms = [a.elapsed_time(b) for a, b in k_events]
+    kernel_avg_ms = sum(kernel_ms) / len(kernel_ms)
+    value = world * args.steps * N * P / (dev_ms * 1e-3)
+    comp.close()
+
+    # roofline of the accumulation kernel (one launch per step on this path)
+    peaks, peak_src = measured_peaks()
+    alg_bytes = N * P + 2 * 2 * P     # every mask byte once + uint16 count read and write
+    achieved = alg_bytes / (kernel_avg_ms * 1e-3) / 1e9
+    traffic = profiled_traffic(f"{W}x{H}x{N}") if args.read_path == "linear" else None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                "kernel": f"count_linear_kernel<uint16_t> ({args.read_path} read path)",
+                "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": kernel_avg_ms,
+                "peak_source": f"{peak_src} hbm_gbs (copy test)"}
+
+    # ---- e2e: pinned host ensemble through the C ABI -----------------------
+    e2e = None
+    link = None
+    if not args.no_e2e:
+        host = torch.empty((N, H, W), dtype=torch.uint8, pin_memory=True)
+        host.copy_(dev_masks)
+        del dev_masks
+        torch.cuda.empty_cache()
+        peak_link = link_peak_gbs(torch, device)
+        comp = binding.Composite(W, H, read_path=args.read_path, staging_buffers=args.staging,
+                                 chunk_members=args.chunk, stream=stream.cuda_stream)
+        h_bucket = torch.empty((H, W), dtype=torch.uint8, pin_memory=True)
+        h_rgba = torch.empty((H, W, 4), dtype=torch.uint8, pin_memory=True)
+
+        def host_step():
+            comp.clear()
+            comp.add(host)
+            comp.render(bucket_out=h_bucket.numpy(), rgba_out=h_rgba.numpy())
+
+        for _ in range(args.warmup):
+            host_step()
+        barrier()
+        w0 = time.time()
+        t0 = time.perf_counter()
+        t_start.record(stream)
+        for _ in range(args.steps):
+            host_step()
+        t_stop.record(stream)
+        barrier()
+        host_s = time.perf_counter() - t0
+        w1 = time.time()
+        if sampler:
+            sampler.window(w0, w1)
+        e2e_ms = max_over_ranks(1e3 * host_s)
+        e2e_value = world * args.steps * N * P / (e2e_ms * 1e-3)
+        h2d_gbs = N * P / (e2e_ms * 1e-3 / args.steps) / 1e9
+        comp.close()
+        # one traced step (outside the timed region) for the overlap fraction
+        traced = binding.Composite(W, H, read_path=args.read_path, staging_buffers=args.staging,
+                                   chunk_members=args.chunk, stream=stream.cuda_stream, trace=True)
+        traced.add(host)
+        rec = traced.trace()
+        traced.close()
+        copies = [(float(a), float(b)) for k, a, b in rec if int(k) == 0]
+        kernels = [(float(a), float(b)) for k, a, b in rec if int(k) != 0]
+        overlap = metrics.overlap_fraction(copies, kernels)
+        copy_busy = sum(b - a for a, b in copies)
+        e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": N * P,
+               "d2h_bytes_per_step": 5 * P, "ms_per_step": e2e_ms / args.steps}
+        link = {"h2d_gbs": h2d_gbs, "link_peak_gbs": peak_link, "link_frac": h2d_gbs / peak_link,
+                "link_peak_how": "best of 5 pinned 1 GiB cudaMemcpyAsync host->device",
+                "overlap_fraction": overlap,
+                "upload_busy_ms": copy_busy, "chunks": len(copies)}
+        del host
+
+    clocks = sampler.stop() if sampler else None
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, done, spent = cpu_oracle_rate(ens, N, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{done} of {N} members of the {W}x{H} workload ({spent:.1f} s, one thread)"}
+
+    if rank == 0:
+        launches_per_step = 2
+        launches_e2e = -(-N // args.chunk) + 1
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": workload_config(args), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": args.steps * (launches_per_step + (launches_e2e if e2e else 0)),
+            "clocks": clocks, "link": link,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

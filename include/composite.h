@@ -167,9 +167,41 @@ int composite_trace_read(composite_ctx *ctx, float *records, int32_t capacity, i
 int composite_end(composite_ctx *ctx);
 
 /* Message of the last error on ctx (or of the last failed composite_begin
- * on this thread when ctx is NULL).  Owned by the library; valid until the
- * next call on the same context. */
+ * or composite_oneshot_static on this thread when ctx is NULL).  Owned by
+ * the library; valid until the next call on the same context. */
 const char *composite_last_error(const composite_ctx *ctx);
+
+/* Largest composite plane of composite_oneshot_static, in padded pixels:
+ * roundup(width, 16) * height must not exceed it (2048 x 2048). */
+#define CPT_ONESHOT_MAX_PIXELS 4194304
+
+/* One-shot composite that allocates nothing.  The paper has no counterpart:
+ * it exists for callers that cannot call cudaMalloc, such as a per-frame
+ * render callback that must not risk the implicit device synchronisation an
+ * allocation can bring, or a host application that owns all device memory
+ * through its own pool and forbids libraries from allocating.
+ * Computes, over the n_members device-resident uint8 masks, uint32 counts,
+ * overlap classes and colours exactly as composite_begin + add_members +
+ * render would (same kernels), writing every non-NULL output (dense
+ * row-major, device memory, counts_out and rgba_out 4-byte aligned).
+ * members, row_pitch_bytes and member_stride_bytes must be 16-byte aligned
+ * and in device memory; lut_rgba is a host table or NULL for the default.
+ * The work is queued on cuda_stream (a cudaStream_t, NULL = legacy default
+ * stream) and the call returns without waiting.
+ * Scratch: a file-scope __device__ array of CPT_ONESHOT_MAX_PIXELS uint32
+ * counts (16 MiB, plus 16 bytes of flags) that every GPU loading the library
+ * holds until the process exits.  The first call on a device looks up its
+ * address (cudaGetSymbolAddress) and should come before any stream capture.
+ * Every call on a device shares that array and clears the part it uses, so
+ * calls whose work overlaps on the GPU (different streams, or host threads)
+ * race and must be serialised by the caller.
+ * Errors: CPT_EINVAL (empty raster, raster larger than the scratch,
+ * unaligned or non-device members, bad strides), CPT_ECUDA; the message is
+ * in composite_last_error(NULL). */
+int composite_oneshot_static(const void *members, int32_t n_members, int64_t member_stride_bytes,
+                             int32_t row_pitch_bytes, int32_t width, int32_t height,
+                             uint32_t *counts_out, uint8_t *bucket_out, uint8_t *rgba_out,
+                             const uint8_t *lut_rgba, void *cuda_stream);
 
 #ifdef __cplusplus
 }

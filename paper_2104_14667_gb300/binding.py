@@ -86,6 +86,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
                                                     ctypes.POINTER(i32)]),
             "composite_end": (ctypes.c_int, [vp]),
             "composite_last_error": (ctypes.c_char_p, [vp]),
+            "composite_oneshot_static": (ctypes.c_int, [vp, i32, i64, i32, i32, i32, vp, vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -247,6 +248,21 @@ def composite_last_error(ctx=None) -> str:
     lib = load()
     msg = lib.composite_last_error(ctx)
     return msg.decode() if msg else ""
+
+
+def composite_oneshot_static(members, counts_out=None, bucket_out=None, rgba_out=None, lut=None,
+                             stream=None) -> None:
+    """One-shot composite of device-resident masks with no allocation in the
+    library (scratch in a fixed device array); queued on ``stream``."""
+    lib = load()
+    ptr, n, h, w, stride, pitch, _, _ = _raster_view(members)
+    lut_arr = None
+    if lut is not None:
+        lut_arr = np.ascontiguousarray(np.asarray(lut, dtype=np.uint8).reshape(256, 4))
+    rc = lib.composite_oneshot_static(ptr, n, stride, pitch, w, h, _ptr(counts_out), _ptr(bucket_out),
+                                      _ptr(rgba_out), lut_arr.ctypes.data if lut_arr is not None else None,
+                                      stream)
+    _check(lib, None, rc)
 
 
 def make_config(read_path="linear", staging_buffers=2, chunk_members=16, count_bits=16,

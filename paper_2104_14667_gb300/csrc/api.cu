@@ -528,6 +528,8 @@ int wait_all(composite_ctx *ctx) {
 
 }  // namespace
 
+void cpt::set_thread_error(const char *message) { g_begin_error = message; }
+
 extern "C" {
 
 int composite_default_config(composite_config *cfg) {

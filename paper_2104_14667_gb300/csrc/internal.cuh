@@ -69,4 +69,8 @@ cudaError_t launch_render_counts(const Plane &p, uint64_t n_members, void *count
 cudaError_t launch_render_mean(const Plane &p, uint64_t n_members, float *mean_out,
                                const DeviceCaps &caps, cudaStream_t s);
 
+// Sets the calling thread's context-free error message (the one that
+// composite_last_error(NULL) returns).
+void set_thread_error(const char *message);
+
 }  // namespace cpt

@@ -59,6 +59,10 @@ def parse_args():
                    help="target CPU time of the oracle baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--sweep", choices=["readpath", "layout", "streaming", "tiny"], default=None,
+                   help="print one JSON line per point of a workload sweep instead of the bench line")
+    p.add_argument("--e2e-mode", choices=["staged", "host_read"], default="staged",
+                   help="which host-to-device path the e2e value reports (both are measured)")
     return p.parse_args()
 
 
@@ -345,35 +349,40 @@ def run_ours(args):
         del dev_masks
         torch.cuda.empty_cache()
         peak_link = link_peak_gbs(torch, device)
-        comp = binding.Composite(W, H, read_path=args.read_path, staging_buffers=args.staging,
-                                 chunk_members=args.chunk, stream=stream.cuda_stream)
         h_bucket = torch.empty((H, W), dtype=torch.uint8, pin_memory=True)
         h_rgba = torch.empty((H, W, 4), dtype=torch.uint8, pin_memory=True)
 
-        def host_step():
-            comp.clear()
-            comp.add(host)
-            comp.render(bucket_out=h_bucket.numpy(), rgba_out=h_rgba.numpy())
+        def e2e_run(host_read: bool) -> float:
+            comp = binding.Composite(W, H, read_path=args.read_path, staging_buffers=args.staging,
+                                     chunk_members=args.chunk, stream=stream.cuda_stream,
+                                     host_read=host_read)
 
-        for _ in range(args.warmup):
-            host_step()
-        barrier()
-        w0 = time.time()
-        t0 = time.perf_counter()
-        t_start.record(stream)
-        for _ in range(args.steps):
-            host_step()
-        t_stop.record(stream)
-        barrier()
-        host_s = time.perf_counter() - t0
-        w1 = time.time()
-        if sampler:
-            sampler.window(w0, w1)
-        e2e_ms = max_over_ranks(1e3 * host_s)
+            def host_step():
+                comp.clear()
+                comp.add(host)
+                comp.render(bucket_out=h_bucket.numpy(), rgba_out=h_rgba.numpy())
+
+            for _ in range(args.warmup):
+                host_step()
+            barrier()
+            w0 = time.time()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                host_step()
+            barrier()
+            host_s = time.perf_counter() - t0
+            if sampler:
+                sampler.window(w0, time.time())
+            comp.close()
+            return max_over_ranks(1e3 * host_s)
+
+        staged_ms = e2e_run(False)
+        direct_ms = e2e_run(True) if args.read_path == "linear" else None
+        use_direct = args.e2e_mode == "host_read" and direct_ms is not None
+        e2e_ms = direct_ms if use_direct else staged_ms
         e2e_value = world * args.steps * N * P / (e2e_ms * 1e-3)
         h2d_gbs = N * P / (e2e_ms * 1e-3 / args.steps) / 1e9
-        comp.close()
-        # one traced step (outside the timed region) for the overlap fraction
+        # one traced staged step (outside the timed region) for the overlap fraction
         traced = binding.Composite(W, H, read_path=args.read_path, staging_buffers=args.staging,
                                    chunk_members=args.chunk, stream=stream.cuda_stream, trace=True)
         traced.add(host)
@@ -384,11 +393,14 @@ def run_ours(args):
         overlap = metrics.overlap_fraction(copies, kernels)
         copy_busy = sum(b - a for a, b in copies)
         e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": N * P,
-               "d2h_bytes_per_step": 5 * P, "ms_per_step": e2e_ms / args.steps}
+               "d2h_bytes_per_step": 5 * P, "ms_per_step": e2e_ms / args.steps,
+               "mode": "host_read (kernel loads pinned host memory over the link)" if use_direct
+               else f"staged ({args.staging} staging buffers of {args.chunk} members, copy stream + events)"}
         link = {"h2d_gbs": h2d_gbs, "link_peak_gbs": peak_link, "link_frac": h2d_gbs / peak_link,
                 "link_peak_how": "best of 5 pinned 1 GiB cudaMemcpyAsync host->device",
-                "overlap_fraction": overlap,
-                "upload_busy_ms": copy_busy, "chunks": len(copies)}
+                "staged_h2d_gbs": N * P / (staged_ms * 1e-3 / args.steps) / 1e9,
+                "host_read_h2d_gbs": (N * P / (direct_ms * 1e-3 / args.steps) / 1e9) if direct_ms else None,
+                "overlap_fraction": overlap, "upload_busy_ms": copy_busy, "chunks": len(copies)}
         del host
 
     clocks = sampler.stop() if sampler else None
@@ -415,9 +427,190 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+# ---- sweeps: the workload configs' other measurements (one JSON line each) ----
+
+def _timed(torch, stream, fn, steps: int, warmup: int) -> float:
+    """Average ms of fn() over `steps` runs (CUDA events on `stream`)."""
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def _busy(rec, kinds):
+    return sum(float(e) - float(s) for k, s, e in rec if int(k) in kinds)
+
+
+def sweep_readpath(args, torch, binding, device, stream):
+    """Kernel over 256 device-resident members at 4096x4096 through the
+    linear, texture and TMA read paths, uint8 masks and float32 depths."""
+    import synth
+    W = H = 4096
+    N = 256
+    P = W * H
+    ens = synth.ensemble(3, W, H, N)
+    terrain_t = torch.from_numpy(ens.terrain).to(device)
+    peaks, _ = measured_peaks()
+    for mode in ("count", "mean_depth"):
+        elem = 1 if mode == "count" else 4
+        if mode == "count":
+            data = torch.empty((N, H, W), dtype=torch.uint8, device=device)
+            synth.fill_masks_torch(ens, data, terrain_t=terrain_t)
+        else:
+            data = torch.empty((N, H, W), dtype=torch.float32, device=device)
+            synth.fill_depths_torch(ens, data, terrain_t=terrain_t)
+        for path in ("linear", "texture", "tma"):
+            cfg = dict(read_path=path, chunk_members=args.chunk, staging_buffers=args.staging,
+                       mode=mode, stream=stream.cuda_stream)
+            with binding.Composite(W, H, **cfg) as comp:
+                def step():
+                    comp.clear()
+                    comp.add(data)
+                ms = _timed(torch, stream, step, args.steps, args.warmup)
+                comp.sync()
+            with binding.Composite(W, H, trace=True, **cfg) as comp:
+                comp.add(data)
+                rec = comp.trace()
+            launches = int(sum(1 for k, _, _ in rec if int(k) == 2))
+            kernel_ms = _busy(rec, (2,))
+            convert_ms = _busy(rec, (1,))
+            plane_rmw = (4 if mode == "count" else 8) * P * launches
+            kernel_bytes = N * P * elem + plane_rmw
+            line = {"sweep": "readpath", "mode": mode, "read_path": path, "width": W, "height": H,
+                    "members": N, "chunk_members": args.chunk, "ms_per_pass": ms,
+                    "member_px_per_s": N * P / (ms * 1e-3), "kernel_launches": launches,
+                    "kernel_busy_ms": kernel_ms, "conversion_busy_ms": convert_ms,
+                    "kernel_alg_gbs": kernel_bytes / (kernel_ms * 1e-3) / 1e9,
+                    "kernel_frac_of_hbm": kernel_bytes / (kernel_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                    "conversion_gbs": (N * P * elem / (convert_ms * 1e-3) / 1e9) if convert_ms else None}
+            print(json.dumps(line), flush=True)
+        del data
+        torch.cuda.empty_cache()
+
+
+def sweep_layout(args, torch, binding, device, stream):
+    """Linear buffer -> layered cudaArray conversion rate for every power-of-two
+    width and height in 64..16384 (the buffer-to-image transform study)."""
+    sides = [64 << i for i in range(9)]
+    reps = 4
+    for h in sides:
+        for w in sides:
+            data = torch.randint(0, 2, (reps, h, w), dtype=torch.uint8, device=device)
+            with binding.Composite(w, h, read_path="texture", chunk_members=1, staging_buffers=2,
+                                   trace=True, stream=stream.cuda_stream) as comp:
+                comp.add(data)
+                comp.sync()
+                comp.clear()
+                comp.add(data)
+                rec = comp.trace()
+            conv = sorted(float(e) - float(s) for k, s, e in rec if int(k) == 1)
+            med = conv[len(conv) // 2]
+            print(json.dumps({"sweep": "layout", "width": w, "height": h, "bytes": w * h,
+                              "conversion_ms": med, "conversion_gbs": w * h / (med * 1e-3) / 1e9}),
+                  flush=True)
+            del data
+
+
+def sweep_streaming(args, torch, binding, device, stream, sides=None, counts=None, chunks=None,
+                    stagings=None, pool_bytes=16 << 30, plan=None):
+    """Members streamed from pinned host memory: member-px/s, H2D GB/s against
+    the measured pinned copy rate, copy/compute overlap, MB per 100 ms."""
+    import synth
+    from paper_2104_14667_gb300 import metrics
+    peak = link_peak_gbs(torch, device)
+    sides = sides or [512, 1024, 2048, 4096, 8192]
+    counts = counts or [16, 64, 256, 1024, 4096]
+    if plan is None:
+        plan = [(s, n, args.chunk, args.staging) for s in sides for n in counts]
+        for c in (chunks or []):
+            plan.append((4096, 1024, c, args.staging))
+        for k in (stagings or []):
+            plan.append((4096, 1024, args.chunk, k))
+    counts = sorted({n for _, n, _, _ in plan})
+    pools = {}
+    for side, n, chunk, k in plan:
+        P = side * side
+        if side not in pools:
+            pools.clear()
+            torch.cuda.empty_cache()
+            pool_n = max(1, min(max(counts), pool_bytes // P))
+            ens = synth.ensemble(2, side, side, pool_n)
+            dev = torch.empty((pool_n, side, side), dtype=torch.uint8, device=device)
+            synth.fill_masks_torch(ens, dev)
+            host = torch.empty((pool_n, side, side), dtype=torch.uint8, pin_memory=True)
+            host.copy_(dev)
+            del dev
+            pools[side] = host
+        host = pools[side]
+        pool_n = host.shape[0]
+
+        def add_all(comp):
+            done = 0
+            while done < n:
+                take = min(pool_n, n - done)
+                comp.add(host[:take])
+                done += take
+
+        cfg = dict(chunk_members=chunk, staging_buffers=k, stream=stream.cuda_stream)
+        with binding.Composite(side, side, **cfg) as comp:
+            for _ in range(args.warmup):
+                comp.clear()
+                add_all(comp)
+                comp.sync()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                comp.clear()
+                add_all(comp)
+                comp.sync()
+            ms = 1e3 * (time.perf_counter() - t0) / args.steps
+        with binding.Composite(side, side, trace=True, **cfg) as comp:
+            add_all(comp)
+            rec = comp.trace()
+        copies = [(float(a), float(b)) for kk, a, b in rec if int(kk) == 0]
+        kernels = [(float(a), float(b)) for kk, a, b in rec if int(kk) != 0]
+        gbs = n * P / (ms * 1e-3) / 1e9
+        print(json.dumps({"sweep": "streaming", "side": side, "members": n, "chunk_members": chunk,
+                          "staging_buffers": k, "pool_members": pool_n, "ms_per_pass": ms,
+                          "member_px_per_s": n * P / (ms * 1e-3), "h2d_gbs": gbs,
+                          "link_peak_gbs": peak, "link_frac": gbs / peak,
+                          "overlap_fraction": metrics.overlap_fraction(copies, kernels),
+                          "mb_per_100ms": gbs * 100.0}), flush=True)
+    pools.clear()
+
+
+def run_sweep(args):
+    import torch
+    from paper_2104_14667_gb300 import binding
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py --sweep needs a CUDA device")
+    device = torch.device("cuda", 0)
+    torch.cuda.set_device(device)
+    stream = torch.cuda.Stream(device)
+    torch.cuda.set_stream(stream)
+    binding.load()
+    if args.sweep == "readpath":
+        sweep_readpath(args, torch, binding, device, stream)
+    elif args.sweep == "layout":
+        sweep_layout(args, torch, binding, device, stream)
+    elif args.sweep == "streaming":
+        sweep_streaming(args, torch, binding, device, stream, chunks=[1, 2, 4, 8, 16, 64, 128],
+                        stagings=[1, 3, 4])
+    elif args.sweep == "tiny":
+        sweep_streaming(args, torch, binding, device, stream,
+                        plan=[(1024, 16, c, k) for c in (16, 1, 2, 4, 8) for k in (2, 1)])
+
+
 def main():
     args = parse_args()
-    if args.impl == "reference":
+    if args.sweep:
+        run_sweep(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

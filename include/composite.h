@@ -90,6 +90,11 @@ typedef struct composite_config {
     void *cuda_stream;          /* compute stream (a cudaStream_t) or NULL for a stream
                                    owned by the library                                   */
     int64_t wait_timeout_ms;    /* bound on every wait, host and device; 0 = 10000        */
+    int32_t host_read;          /* 1 = with CPT_READ_LINEAR, pinned host rasters with 16-byte
+                                   aligned base, pitch and stride are read in place by the
+                                   accumulation kernel over the host link (no copy engine,
+                                   no staging); 0 = upload through the staging buffers
+                                   (the paper's pipeline); default 0                      */
 } composite_config;
 
 /* Fills *cfg with the defaults listed above.  CPT_EINVAL if cfg is NULL. */

@@ -50,6 +50,7 @@ class Config(ctypes.Structure):
         ("pinned_ring_bytes", ctypes.c_int64),
         ("cuda_stream", ctypes.c_void_p),
         ("wait_timeout_ms", ctypes.c_int64),
+        ("host_read", ctypes.c_int32),
     ]
 
 
@@ -267,7 +268,7 @@ def composite_oneshot_static(members, counts_out=None, bucket_out=None, rgba_out
 
 def make_config(read_path="linear", staging_buffers=2, chunk_members=16, count_bits=16,
                 mode="count", trace=False, pinned_ring_bytes=0, stream=None,
-                wait_timeout_ms=0) -> Config:
+                wait_timeout_ms=0, host_read=False) -> Config:
     cfg = composite_default_config()
     cfg.read_path = READ_PATHS[read_path] if isinstance(read_path, str) else int(read_path)
     cfg.staging_buffers = staging_buffers
@@ -278,6 +279,7 @@ def make_config(read_path="linear", staging_buffers=2, chunk_members=16, count_b
     cfg.pinned_ring_bytes = pinned_ring_bytes
     cfg.cuda_stream = stream
     cfg.wait_timeout_ms = wait_timeout_ms
+    cfg.host_read = 1 if host_read else 0
     return cfg
 
 

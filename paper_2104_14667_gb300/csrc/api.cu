@@ -187,6 +187,7 @@ int check_config(const composite_config &c) {
     if (c.mode != CPT_MODE_COUNT && c.mode != CPT_MODE_MEAN_DEPTH) return fail(nullptr, CPT_EINVAL, "mode %d out of range", c.mode);
     if (c.trace != 0 && c.trace != 1) return fail(nullptr, CPT_EINVAL, "trace must be 0 or 1");
     if (c.pinned_ring_bytes < 0 || c.wait_timeout_ms < 0) return fail(nullptr, CPT_EINVAL, "negative ring budget or timeout");
+    if (c.host_read != 0 && c.host_read != 1) return fail(nullptr, CPT_EINVAL, "host_read must be 0 or 1");
     return CPT_OK;
 }
 
@@ -498,7 +499,16 @@ int apply(composite_ctx *ctx, const void *members, int32_t n, int64_t stride, in
             rc = run_staged(ctx, src, n, stride, pitch, sign);
         }
     } else if (kind == kPinned) {
-        rc = run_staged(ctx, src, n, stride, pitch, sign);
+        const bool aligned = (reinterpret_cast<uintptr_t>(members) % 16 == 0) && (pitch % 16 == 0) && (stride % 16 == 0);
+        if (ctx->cfg.host_read && ctx->cfg.read_path == CPT_READ_LINEAR && aligned) {
+            // the kernel loads the pinned rasters over the host link itself
+            void *dptr = nullptr;
+            CK(ctx, cudaHostGetDevicePointer(&dptr, const_cast<void *>(members), 0));
+            RasterBatch b{dptr, stride, pitch, n};
+            rc = accumulate(ctx, b, sign);
+        } else {
+            rc = run_staged(ctx, src, n, stride, pitch, sign);
+        }
     } else {
         rc = run_ring(ctx, src, n, stride, pitch, sign);
     }
@@ -544,6 +554,7 @@ int composite_default_config(composite_config *cfg) {
     cfg->pinned_ring_bytes = 0;
     cfg->cuda_stream = nullptr;
     cfg->wait_timeout_ms = 0;
+    cfg->host_read = 0;
     return CPT_OK;
 }
 

@@ -157,6 +157,20 @@ def fill_masks_torch(ens: Ensemble, out, members: range | None = None, terrain_t
     return out
 
 
+def fill_depths_torch(ens: Ensemble, out, members: range | None = None, terrain_t=None):
+    """As depths, into a torch float32[n, H, W] tensor on any device: the same
+    float32 subtraction w_m - terrain, clipped at 0, so the values are identical."""
+    import torch
+    idx = range(ens.n) if members is None else members
+    if out.dtype != torch.float32 or tuple(out.shape[1:]) != (ens.height, ens.width) or out.shape[0] < len(idx):
+        raise ValueError("out must be float32[n, H, W] with room for every member")
+    t = terrain_t if terrain_t is not None else torch.from_numpy(ens.terrain).to(out.device)
+    for j, m in enumerate(idx):
+        torch.sub(torch.tensor(float(ens.levels[m]), dtype=torch.float32, device=t.device), t, out=out[j])
+        out[j].clamp_(min=0.0)
+    return out
+
+
 def masks(ens: Ensemble) -> np.ndarray:
     """uint8[N, H, W] masks with values in {0, 1}."""
     return fill_masks(ens, np.empty((ens.n, ens.height, ens.width), dtype=np.uint8))

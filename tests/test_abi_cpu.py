@@ -30,7 +30,7 @@ def test_library_exports_every_declared_symbol(lib):
 def test_default_config(lib):
     cfg = binding.composite_default_config()
     assert (cfg.read_path, cfg.staging_buffers, cfg.chunk_members, cfg.count_bits, cfg.mode) == (0, 2, 16, 16, 0)
-    assert ctypes.sizeof(binding.Config) == 48
+    assert ctypes.sizeof(binding.Config) == 56
 
 
 @pytest.mark.parametrize("w,h", [(0, 5), (5, 0), (-1, 3)])
@@ -42,7 +42,8 @@ def test_begin_rejects_empty_raster(lib, w, h):
 
 @pytest.mark.parametrize("field,value", [("read_path", 3), ("staging_buffers", 0), ("staging_buffers", 9),
                                          ("chunk_members", 0), ("chunk_members", 256), ("count_bits", 8),
-                                         ("mode", 2), ("trace", 2), ("wait_timeout_ms", -1)])
+                                         ("mode", 2), ("trace", 2), ("wait_timeout_ms", -1),
+                                         ("host_read", 2)])
 def test_begin_rejects_bad_config(lib, field, value):
     cfg = binding.composite_default_config()
     setattr(cfg, field, value)

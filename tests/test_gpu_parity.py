@@ -252,3 +252,14 @@ def test_nested_threshold_identity_at_streaming_size():
     np.testing.assert_array_equal(got["counts"][rows].astype(np.int64), c)
     np.testing.assert_array_equal(got["bucket"][rows], b)
     np.testing.assert_array_equal(got["rgba"][rows], oracle.rgba(b))
+
+
+@pytest.mark.parametrize("w,h,n", [(1024, 1024, 16), (48, 33, 300), (13, 7, 5), (4097, 3, 9)])
+def test_host_read_in_place(w, h, n):
+    # pinned rasters read by the kernel over the host link; unaligned
+    # layouts fall back to the staging pipeline
+    m = synth.scramble_nonzero(synth.random_masks(30 + w, n, h, w), 30)
+    with binding.Composite(w, h, host_read=True) as comp:
+        comp.add(as_kind(m, "pinned"))
+        comp.remove(as_kind(m[: n // 2], "pinned"))
+        check_counts(comp, m[n // 2:])

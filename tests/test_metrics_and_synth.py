@@ -104,3 +104,14 @@ def test_terrain_row_band_matches_whole():
     whole = synth.terrain(7, 50, 30)
     band = synth.terrain(7, 50, 30, rows=slice(10, 20))
     np.testing.assert_array_equal(band, whole[10:20])
+
+
+def test_torch_fills_match_numpy_generator():
+    torch = __import__("pytest").importorskip("torch")
+    ens = synth.ensemble(6, 70, 50, 5)
+    m = torch.empty((5, 50, 70), dtype=torch.uint8)
+    synth.fill_masks_torch(ens, m)
+    np.testing.assert_array_equal(m.numpy(), synth.masks(ens))
+    d = torch.empty((5, 50, 70), dtype=torch.float32)
+    synth.fill_depths_torch(ens, d)
+    np.testing.assert_array_equal(d.numpy(), synth.depths(ens))

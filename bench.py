@@ -465,9 +465,9 @@ def sweep_readpath(args, torch, binding, device, stream):
         else:
             data = torch.empty((N, H, W), dtype=torch.float32, device=device)
             synth.fill_depths_torch(ens, data, terrain_t=terrain_t)
-        for path in ("linear", "texture", "tma"):
+        for path, box in (("linear", 0), ("texture", 0), ("tma", 64), ("tma", 128), ("tma", 256)):
             cfg = dict(read_path=path, chunk_members=args.chunk, staging_buffers=args.staging,
-                       mode=mode, stream=stream.cuda_stream)
+                       mode=mode, stream=stream.cuda_stream, tma_box_bytes=box)
             with binding.Composite(W, H, **cfg) as comp:
                 def step():
                     comp.clear()
@@ -482,7 +482,8 @@ def sweep_readpath(args, torch, binding, device, stream):
             convert_ms = _busy(rec, (1,))
             plane_rmw = (4 if mode == "count" else 8) * P * launches
             kernel_bytes = N * P * elem + plane_rmw
-            line = {"sweep": "readpath", "mode": mode, "read_path": path, "width": W, "height": H,
+            line = {"sweep": "readpath", "mode": mode, "read_path": path, "tma_box_bytes": box or None,
+                    "width": W, "height": H,
                     "members": N, "chunk_members": args.chunk, "ms_per_pass": ms,
                     "member_px_per_s": N * P / (ms * 1e-3), "kernel_launches": launches,
                     "kernel_busy_ms": kernel_ms, "conversion_busy_ms": convert_ms,

@@ -95,6 +95,9 @@ typedef struct composite_config {
                                    accumulation kernel over the host link (no copy engine,
                                    no staging); 0 = upload through the staging buffers
                                    (the paper's pipeline); default 0                      */
+    int32_t tma_box_bytes;      /* CPT_READ_TMA box width in bytes: 64, 128 or 256 (a box is
+                                   2 KiB per member: width x 2048/width rows, x 8 members);
+                                   0 = 256                                                */
 } composite_config;
 
 /* Fills *cfg with the defaults listed above.  CPT_EINVAL if cfg is NULL. */

@@ -51,6 +51,7 @@ class Config(ctypes.Structure):
         ("cuda_stream", ctypes.c_void_p),
         ("wait_timeout_ms", ctypes.c_int64),
         ("host_read", ctypes.c_int32),
+        ("tma_box_bytes", ctypes.c_int32),
     ]
 
 
@@ -268,7 +269,7 @@ def composite_oneshot_static(members, counts_out=None, bucket_out=None, rgba_out
 
 def make_config(read_path="linear", staging_buffers=2, chunk_members=16, count_bits=16,
                 mode="count", trace=False, pinned_ring_bytes=0, stream=None,
-                wait_timeout_ms=0, host_read=False) -> Config:
+                wait_timeout_ms=0, host_read=False, tma_box_bytes=0) -> Config:
     cfg = composite_default_config()
     cfg.read_path = READ_PATHS[read_path] if isinstance(read_path, str) else int(read_path)
     cfg.staging_buffers = staging_buffers
@@ -280,6 +281,7 @@ def make_config(read_path="linear", staging_buffers=2, chunk_members=16, count_b
     cfg.cuda_stream = stream
     cfg.wait_timeout_ms = wait_timeout_ms
     cfg.host_read = 1 if host_read else 0
+    cfg.tma_box_bytes = tma_box_bytes
     return cfg
 
 

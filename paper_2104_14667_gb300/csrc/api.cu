@@ -30,6 +30,7 @@ namespace {
 thread_local std::string g_begin_error;
 
 enum MemKind { kPageable = 0, kPinned = 1, kDevice = 2 };
+constexpr int kDefaultTmaBoxBytes = 256;
 enum TraceKind { kTraceUpload = 0, kTraceConvert = 1, kTraceKernel = 2 };
 
 struct Slot {
@@ -188,6 +189,8 @@ int check_config(const composite_config &c) {
     if (c.trace != 0 && c.trace != 1) return fail(nullptr, CPT_EINVAL, "trace must be 0 or 1");
     if (c.pinned_ring_bytes < 0 || c.wait_timeout_ms < 0) return fail(nullptr, CPT_EINVAL, "negative ring budget or timeout");
     if (c.host_read != 0 && c.host_read != 1) return fail(nullptr, CPT_EINVAL, "host_read must be 0 or 1");
+    if (c.tma_box_bytes != 0 && !cpt::tma_box_supported(c.tma_box_bytes))
+        return fail(nullptr, CPT_EINVAL, "tma_box_bytes %d is not 0, 64, 128 or 256", c.tma_box_bytes);
     return CPT_OK;
 }
 
@@ -297,10 +300,11 @@ int accumulate(composite_ctx *ctx, const RasterBatch &b, int sign) {
     cudaError_t e;
     if (ctx->cfg.read_path == CPT_READ_TMA) {
         CUtensorMap map;
-        const int r = cpt::encode_tma_map(&map, b, ctx->width, ctx->height, ctx->elem);
+        const int box = ctx->cfg.tma_box_bytes;
+        const int r = cpt::encode_tma_map(&map, b, ctx->width, ctx->height, ctx->elem, box);
         if (r != 0) return fail(ctx, CPT_ECUDA, "cuTensorMapEncodeTiled failed (CUresult %d)", r);
-        e = count ? cpt::launch_count_tma(map, b, ctx->plane, sign, ctx->flags, tns, ctx->caps, ctx->compute)
-                  : cpt::launch_depth_tma(map, b, ctx->plane, sign, ctx->flags, tns, ctx->caps, ctx->compute);
+        e = count ? cpt::launch_count_tma(map, b, ctx->plane, sign, ctx->flags, tns, box, ctx->caps, ctx->compute)
+                  : cpt::launch_depth_tma(map, b, ctx->plane, sign, ctx->flags, tns, box, ctx->caps, ctx->compute);
     } else {
         e = count ? cpt::launch_count_linear(b, ctx->plane, sign, ctx->flags, ctx->caps, ctx->compute)
                   : cpt::launch_depth_linear(b, ctx->plane, sign, ctx->flags, ctx->caps, ctx->compute);
@@ -555,6 +559,7 @@ int composite_default_config(composite_config *cfg) {
     cfg->cuda_stream = nullptr;
     cfg->wait_timeout_ms = 0;
     cfg->host_read = 0;
+    cfg->tma_box_bytes = 0;
     return CPT_OK;
 }
 
@@ -570,6 +575,7 @@ int composite_begin(composite_ctx **out, int32_t width, int32_t height, const co
         composite_default_config(&c);
     int rc = check_config(c);
     if (rc) return rc;
+    if (c.tma_box_bytes == 0) c.tma_box_bytes = kDefaultTmaBoxBytes;
     composite_ctx *ctx = new composite_ctx();
     ctx->width = width;
     ctx->height = height;

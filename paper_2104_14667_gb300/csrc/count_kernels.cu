@@ -6,8 +6,10 @@
 // member byte is read once with a 16-byte load and the composite is read and
 // written once per launch instead of once per member (the paper's kernel
 // reads and writes the accumulator per member, Fig. 2 step 4).  Mask bytes
-// are turned into per-byte ones and summed four to a 32-bit word; the packed
-// byte counters are widened every 255 members.
+// are turned into per-byte ones and summed four to a 32-bit word, in slabs of
+// at most 255 members so the packed byte counters cannot overflow.
+#include <algorithm>
+
 #include "device_common.cuh"
 
 namespace cpt {
@@ -20,48 +22,56 @@ __device__ __forceinline__ uint4 load_stream16(const uint8_t *p) {
     return __ldcs(reinterpret_cast<const uint4 *>(p));
 }
 
+// Work unit = (member slab, 16-byte group).  A slab holds at most 255
+// members, so four packed byte counters never overflow inside a unit; with
+// more than one slab the unit's counts go into the composite by atomics.
+// Splitting the members gives many small units, so the last wave of a large
+// launch is as full as the others.
 template <typename CountT>
 __global__ void __launch_bounds__(kThreads)
 count_linear_kernel(RasterBatch b, Plane p, int sign, int *flags, int64_t groups,
-                    int groups_per_row) {
+                    int groups_per_row, int slab, int slabs) {
     CountT *plane = static_cast<CountT *>(p.data);
     const int64_t stride = b.member_stride;
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < groups;
-         g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t units = groups * slabs;
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < units;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        const int sl = (int)(u / groups);
+        const int64_t g = u - (int64_t)sl * groups;
         const int y = (int)(g / groups_per_row);
         const int x0 = (int)(g - (int64_t)y * groups_per_row) * 16;
         const int valid = min(16, p.width - x0);
-        const uint8_t *src = static_cast<const uint8_t *>(b.base) + y * b.row_pitch + x0;
-        uint32_t wide[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) wide[j] = 0;
+        const int m0 = sl * slab;
+        const int m1 = min(b.n, m0 + slab);
+        const uint8_t *q = static_cast<const uint8_t *>(b.base) + y * b.row_pitch + x0 + (int64_t)m0 * stride;
+        uint32_t k[4] = {0u, 0u, 0u, 0u};
         if (valid == 16) {
-            int m = 0;
-            while (m < b.n) {
-                const int mend = min(b.n, m + kPackedLimit);
-                uint32_t k0 = 0, k1 = 0, k2 = 0, k3 = 0;
-                const uint8_t *q = src + (int64_t)m * stride;
 #pragma unroll 8
-                for (; m < mend; ++m) {
-                    const uint4 v = load_stream16(q);
-                    q += stride;
-                    k0 += nonzero_bytes(v.x);
-                    k1 += nonzero_bytes(v.y);
-                    k2 += nonzero_bytes(v.z);
-                    k3 += nonzero_bytes(v.w);
-                }
-                widen16(wide, k0, k1, k2, k3);
+            for (int m = m0; m < m1; ++m) {
+                const uint4 v = load_stream16(q);
+                q += stride;
+                k[0] += nonzero_bytes(v.x);
+                k[1] += nonzero_bytes(v.y);
+                k[2] += nonzero_bytes(v.z);
+                k[3] += nonzero_bytes(v.w);
             }
         } else {
             // ragged right edge: scalar loads, never past the row's last pixel
-            for (int m = 0; m < b.n; ++m) {
-                const uint8_t *q = src + (int64_t)m * stride;
+            for (int m = m0; m < m1; ++m, q += stride) {
 #pragma unroll
                 for (int j = 0; j < 16; ++j)
-                    if (j < valid) wide[j] += q[j] != 0;
+                    if (j < valid) k[j / 4] += (uint32_t)(q[j] != 0) << (8 * (j % 4));
             }
         }
-        apply_count_group<CountT>(plane + (int64_t)y * p.pitch + x0, valid, wide, sign, flags);
+        uint32_t wide[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) wide[j] = 0;
+        widen16(wide, k[0], k[1], k[2], k[3]);
+        CountT *dst = plane + (int64_t)y * p.pitch + x0;
+        if (slabs == 1)
+            apply_count_group<CountT>(dst, valid, wide, sign, flags);
+        else
+            atomic_count_group<CountT>(dst, wide, sign, flags);
     }
 }
 
@@ -165,15 +175,23 @@ inline int64_t blocks_for(int64_t groups) {
 }  // namespace
 
 cudaError_t launch_count_linear(const RasterBatch &b, const Plane &p, int sign, int *flags,
-                                const DeviceCaps &, cudaStream_t s) {
+                                const DeviceCaps &caps, cudaStream_t s) {
     const int gpr = (p.width + 15) / 16;
     const int64_t groups = (int64_t)gpr * p.height;
     if (b.n <= 0 || groups == 0) return cudaSuccess;
-    const unsigned grid = (unsigned)blocks_for(groups);
+    // Member slabs: at most kPackedLimit members each; more slabs (down to 32
+    // members each) when the groups alone fill fewer than eight waves.
+    const int64_t target_units = 8ll * caps.num_sms * 2048;
+    int64_t slabs = (b.n + kPackedLimit - 1) / kPackedLimit;
+    const int64_t want = std::min<int64_t>((target_units + groups - 1) / groups, (b.n + 31) / 32);
+    slabs = std::max<int64_t>(std::max<int64_t>(slabs, want), 1);
+    const int slab = (int)((b.n + slabs - 1) / slabs);
+    slabs = (b.n + slab - 1) / slab;
+    const unsigned grid = (unsigned)blocks_for(groups * slabs);
     if (p.count_bits == 16)
-        count_linear_kernel<uint16_t><<<grid, kThreads, 0, s>>>(b, p, sign, flags, groups, gpr);
+        count_linear_kernel<uint16_t><<<grid, kThreads, 0, s>>>(b, p, sign, flags, groups, gpr, slab, (int)slabs);
     else
-        count_linear_kernel<uint32_t><<<grid, kThreads, 0, s>>>(b, p, sign, flags, groups, gpr);
+        count_linear_kernel<uint32_t><<<grid, kThreads, 0, s>>>(b, p, sign, flags, groups, gpr, slab, (int)slabs);
     return cudaGetLastError();
 }
 

@@ -108,6 +108,47 @@ __device__ __forceinline__ void apply_count_group(CountT *dst, int valid,
     if (under) flag_set(flags, kFlagUnderflow);
 }
 
+// The same update as apply_count_group, by atomic adds (or subtractions) on
+// the 32-bit words of the group, for launches where several threads fold
+// different member slabs into the same pixels.  Pixels past the raster's edge
+// carry a zero delta.  uint16 counts are updated two to a word: an add cannot
+// carry into the upper half because no count exceeds N <= 65535, and a
+// subtraction that would borrow is itself an underflow, caught from the
+// returned old value (subtractions only decrease a count, so a count that
+// ends below zero makes some subtraction see an old value below its delta).
+template <typename CountT>
+__device__ __forceinline__ void atomic_count_group(CountT *dst, const uint32_t (&wide)[16], int sign,
+                                                   int *flags) {
+    bool under = false;
+    uint32_t *w = reinterpret_cast<uint32_t *>(dst);
+    if constexpr (sizeof(CountT) == 2) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const uint32_t dl = wide[2 * k], dh = wide[2 * k + 1];
+            const uint32_t d = dl | (dh << 16);
+            if (d == 0) continue;
+            if (sign > 0) {
+                atomicAdd(w + k, d);
+            } else {
+                const uint32_t old = atomicSub(w + k, d);
+                under |= (dl > (old & 0xFFFFu)) | (dh > (old >> 16));
+            }
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            if (wide[j] == 0) continue;
+            if (sign > 0) {
+                atomicAdd(w + j, wide[j]);
+            } else {
+                const uint32_t old = atomicSub(w + j, wide[j]);
+                under |= wide[j] > old;
+            }
+        }
+    }
+    if (under) flag_set(flags, kFlagUnderflow);
+}
+
 // dst[j] (+|-)= acc[j] for the first `valid` of four float32 sums.
 __device__ __forceinline__ void apply_depth_group(float *dst, int valid, const float (&acc)[4],
                                                   int sign) {

@@ -50,12 +50,18 @@ cudaError_t launch_depth_texture(cudaTextureObject_t tex, int n_layers, const Pl
 
 // TMA read path: tensor map over the batch, tiles staged in shared memory.
 // The tensor map must come from encode_tma_map for the same batch.
+// box_bytes: the x extent of a box in bytes (64, 128 or 256); a box is always
+// 2 KiB per member (box_bytes x 2048/box_bytes rows) x 8 members.
 cudaError_t launch_count_tma(const CUtensorMap &map, const RasterBatch &b, const Plane &p, int sign,
-                             int *flags, uint64_t timeout_ns, const DeviceCaps &caps, cudaStream_t s);
+                             int *flags, uint64_t timeout_ns, int box_bytes, const DeviceCaps &caps,
+                             cudaStream_t s);
 cudaError_t launch_depth_tma(const CUtensorMap &map, const RasterBatch &b, const Plane &p, int sign,
-                             int *flags, uint64_t timeout_ns, const DeviceCaps &caps, cudaStream_t s);
+                             int *flags, uint64_t timeout_ns, int box_bytes, const DeviceCaps &caps,
+                             cudaStream_t s);
+bool tma_box_supported(int box_bytes);
 // Returns 0 on success; a CUresult otherwise.  elem_bytes 1 (masks) or 4.
-int encode_tma_map(CUtensorMap *map, const RasterBatch &b, int width, int height, int elem_bytes);
+int encode_tma_map(CUtensorMap *map, const RasterBatch &b, int width, int height, int elem_bytes,
+                   int box_bytes);
 // Requirements of the TMA path for a batch (alignment of base and strides).
 bool tma_compatible(const RasterBatch &b);
 

@@ -10,9 +10,12 @@ namespace {
 constexpr int kThreads = 256;
 
 // floor(255 * c / n) for 0 <= c <= n, exact.  With n < 2^24 the product fits
-// in 32 bits; larger n take the 64-bit path.
+// in 32 bits; larger n take the 64-bit path.  A count above n (only possible
+// in a composite an underflow has already invalidated) is held at 255 so the
+// colour table is never indexed out of range.
 __device__ __forceinline__ uint32_t overlap_class(uint32_t c, uint64_t n) {
     if (n == 0) return 0;
+    if (c >= n) return 255;
     if (n < (1u << 24)) return (255u * c) / (uint32_t)n;
     return (uint32_t)((255ull * c) / n);
 }
@@ -34,7 +37,67 @@ render_counts_kernel(Plane p, uint64_t n_members, CountT *counts_out, uint8_t *b
         const uint32_t b = overlap_class(c, n_members);
         if (counts_out) counts_out[i] = (CountT)c;
         if (bucket_out) bucket_out[i] = (uint8_t)b;
-        if (rgba_out) rgba_out[i] = table[b & 0xFFu];
+        if (rgba_out) rgba_out[i] = table[b];
+    }
+}
+
+// 16 pixels of one row per thread, 16-byte stores; used when the width is a
+// multiple of 16 and every output is 16-byte aligned, so every dense output
+// row starts on a 16-byte boundary.
+template <typename CountT>
+__global__ void __launch_bounds__(kThreads)
+render_counts_vec_kernel(Plane p, uint64_t n_members, CountT *counts_out, uint8_t *bucket_out,
+                         uint32_t *rgba_out, Lut lut) {
+    __shared__ uint32_t table[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) table[i] = lut.rgba[i];
+    __syncthreads();
+    const CountT *plane = static_cast<const CountT *>(p.data);
+    const int gpr = p.width / 16;
+    const int64_t groups = (int64_t)gpr * p.height;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < groups;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int y = (int)(g / gpr);
+        const int x0 = (int)(g - (int64_t)y * gpr) * 16;
+        const int64_t out = (int64_t)y * p.width + x0;
+        uint32_t c[16];
+        const uint4 *src = reinterpret_cast<const uint4 *>(plane + (int64_t)y * p.pitch + x0);
+        if constexpr (sizeof(CountT) == 2) {
+            const uint4 a = src[0], b = src[1];
+            const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                c[2 * k] = w[k] & 0xFFFFu;
+                c[2 * k + 1] = w[k] >> 16;
+            }
+            if (counts_out) {
+                uint4 *d = reinterpret_cast<uint4 *>(counts_out + out);
+                d[0] = a;
+                d[1] = b;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint4 v = src[q];
+                c[4 * q] = v.x; c[4 * q + 1] = v.y; c[4 * q + 2] = v.z; c[4 * q + 3] = v.w;
+                if (counts_out) reinterpret_cast<uint4 *>(counts_out + out)[q] = v;
+            }
+        }
+        uint32_t b[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) b[j] = overlap_class(c[j], n_members);
+        if (bucket_out) {
+            uint32_t w[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                w[q] = b[4 * q] | (b[4 * q + 1] << 8) | (b[4 * q + 2] << 16) | (b[4 * q + 3] << 24);
+            *reinterpret_cast<uint4 *>(bucket_out + out) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        if (rgba_out) {
+            uint4 *d = reinterpret_cast<uint4 *>(rgba_out + out);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                d[q] = make_uint4(table[b[4 * q]], table[b[4 * q + 1]], table[b[4 * q + 2]], table[b[4 * q + 3]]);
+        }
     }
 }
 
@@ -65,6 +128,18 @@ cudaError_t launch_render_counts(const Plane &p, uint64_t n_members, void *count
                                  const DeviceCaps &caps, cudaStream_t s) {
     const int64_t total = (int64_t)p.width * p.height;
     if (!counts_out && !bucket_out && !rgba_out) return cudaSuccess;
+    const bool aligned = ((reinterpret_cast<uintptr_t>(counts_out) | reinterpret_cast<uintptr_t>(bucket_out) |
+                           reinterpret_cast<uintptr_t>(rgba_out)) % 16) == 0;
+    if (p.width % 16 == 0 && aligned) {
+        const int64_t groups = total / 16;
+        if (p.count_bits == 16)
+            render_counts_vec_kernel<uint16_t><<<grid_for(groups, caps), kThreads, 0, s>>>(
+                p, n_members, static_cast<uint16_t *>(counts_out), bucket_out, rgba_out, lut);
+        else
+            render_counts_vec_kernel<uint32_t><<<grid_for(groups, caps), kThreads, 0, s>>>(
+                p, n_members, static_cast<uint32_t *>(counts_out), bucket_out, rgba_out, lut);
+        return cudaGetLastError();
+    }
     if (p.count_bits == 16)
         render_counts_kernel<uint16_t><<<grid_for(total, caps), kThreads, 0, s>>>(
             p, n_members, static_cast<uint16_t *>(counts_out), bucket_out, rgba_out, lut);

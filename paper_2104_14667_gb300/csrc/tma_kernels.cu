@@ -2,10 +2,10 @@
 //
 // The batch is described to the tensor memory accelerator as a 3-D tensor
 // (x = pixel within a row, y = row, z = member).  A persistent CTA walks its
-// composite tiles (128 bytes x 16 rows); for every tile one producer thread
-// streams boxes of 128 B x 16 rows x 8 members through a ring of shared-memory
-// stages with cp.async.bulk.tensor, and four consumer warps fold each box
-// into registers, one 16-byte group per thread.  Boxes past the raster's
+// composite tiles (64, 128 or 256 bytes wide, 2 KiB per member); for every
+// tile one producer thread streams boxes of that tile x 8 members through a
+// ring of shared-memory stages with cp.async.bulk.tensor, and four consumer
+// warps fold each box into registers, one 16-byte group per thread.  Boxes past the raster's
 // edge or the last member are zero filled by the hardware, which counts as
 // "not flooded" and adds 0.0 to a depth sum.  Every mbarrier wait is bounded
 // in time; a wait that runs out raises the timeout flag and the CTA leaves
@@ -17,13 +17,13 @@
 namespace cpt {
 namespace {
 
-constexpr int kBoxRowBytes = 128;                   // x extent of a box, bytes
-constexpr int kBoxRows = 16;                        // y extent
+// A box is kBoxX bytes x (2048 / kBoxX) rows x kBoxMembers members: 2 KiB
+// per member, 16 KiB per box, one 16-byte group per consumer thread and member.
+constexpr int kMemberPlaneBytes = 2048;
 constexpr int kBoxMembers = 8;                      // z extent
-constexpr int kMemberPlaneBytes = kBoxRowBytes * kBoxRows;
 constexpr int kBoxBytes = kMemberPlaneBytes * kBoxMembers;   // 16 KiB
 constexpr int kStages = 6;
-constexpr int kConsumers = 128;                      // 8 groups x 16 rows
+constexpr int kConsumers = 128;                      // one 16-byte group each
 constexpr int kThreads = kConsumers + 32;            // + one producer warp
 constexpr int kCtasPerSm = 2;
 
@@ -99,7 +99,7 @@ __device__ __forceinline__ uint4 lds16(const uint8_t *p) {
 
 // The producer role: one thread issues every box of the CTA's tiles.
 __device__ void produce(TmaShared &sh, const CUtensorMap *map, int tiles, int tiles_x,
-                        int slabs, int box_x_elems, uint64_t timeout_ns, int *flags) {
+                        int slabs, int box_x_elems, int box_rows, uint64_t timeout_ns, int *flags) {
     uint32_t it = 0;
     bool ok = true;
     for (int tile = blockIdx.x; ok && tile < tiles; tile += gridDim.x) {
@@ -112,7 +112,7 @@ __device__ void produce(TmaShared &sh, const CUtensorMap *map, int tiles, int ti
                 break;
             }
             mbar_arrive_expect_tx(&sh.full[s], kBoxBytes);
-            tma_load_box(sh.stage[s], map, tx * box_x_elems, ty * kBoxRows, slab * kBoxMembers,
+            tma_load_box(sh.stage[s], map, tx * box_x_elems, ty * box_rows, slab * kBoxMembers,
                          &sh.full[s]);
         }
     }
@@ -128,15 +128,17 @@ __device__ void produce(TmaShared &sh, const CUtensorMap *map, int tiles, int ti
     }
 }
 
-template <typename CountT>
+template <typename CountT, int kBoxX>
 __global__ void __launch_bounds__(kThreads, kCtasPerSm)
 count_tma_kernel(const __grid_constant__ CUtensorMap map, Plane p, int n_members, int sign,
                  int *flags, uint64_t timeout_ns) {
+    constexpr int kRows = kMemberPlaneBytes / kBoxX;
+    constexpr int kGroupsPerRow = kBoxX / 16;
     extern __shared__ uint8_t smem_raw[];
     TmaShared &sh = *reinterpret_cast<TmaShared *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    const int tiles_x = (p.width + kBoxRowBytes - 1) / kBoxRowBytes;
-    const int tiles = tiles_x * ((p.height + kBoxRows - 1) / kBoxRows);
+    const int tiles_x = (p.width + kBoxX - 1) / kBoxX;
+    const int tiles = tiles_x * ((p.height + kRows - 1) / kRows);
     const int slabs = (n_members + kBoxMembers - 1) / kBoxMembers;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -150,13 +152,13 @@ count_tma_kernel(const __grid_constant__ CUtensorMap map, Plane p, int n_members
 
     if (threadIdx.x >= kConsumers) {
         if (threadIdx.x == kConsumers)
-            produce(sh, &map, tiles, tiles_x, slabs, kBoxRowBytes, timeout_ns, flags);
+            produce(sh, &map, tiles, tiles_x, slabs, kBoxX, kRows, timeout_ns, flags);
         return;
     }
 
     CountT *plane = static_cast<CountT *>(p.data);
-    const int row = threadIdx.x / 8, grp = threadIdx.x % 8;
-    const int offset = row * kBoxRowBytes + grp * 16;
+    const int row = threadIdx.x / kGroupsPerRow, grp = threadIdx.x % kGroupsPerRow;
+    const int offset = row * kBoxX + grp * 16;
     uint32_t it = 0;
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
         const int tx = tile % tiles_x, ty = tile / tiles_x;
@@ -190,23 +192,26 @@ count_tma_kernel(const __grid_constant__ CUtensorMap map, Plane p, int n_members
             }
         }
         widen16(wide, k0, k1, k2, k3);
-        const int y = ty * kBoxRows + row;
-        const int x0 = tx * kBoxRowBytes + grp * 16;
+        const int y = ty * kRows + row;
+        const int x0 = tx * kBoxX + grp * 16;
         if (y < p.height && x0 < p.width)
             apply_count_group<CountT>(plane + (int64_t)y * p.pitch + x0, min(16, p.width - x0),
                                       wide, sign, flags);
     }
 }
 
+template <int kBoxX>
 __global__ void __launch_bounds__(kThreads, kCtasPerSm)
 depth_tma_kernel(const __grid_constant__ CUtensorMap map, Plane p, int n_members, int sign,
                  int *flags, uint64_t timeout_ns) {
+    constexpr int kRows = kMemberPlaneBytes / kBoxX;
+    constexpr int kGroupsPerRow = kBoxX / 16;
+    constexpr int kBoxXElems = kBoxX / 4;      // float32 pixels per box row
     extern __shared__ uint8_t smem_raw[];
     TmaShared &sh = *reinterpret_cast<TmaShared *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    constexpr int kBoxX = kBoxRowBytes / 4;   // 32 float32 pixels per box row
-    const int tiles_x = (p.width + kBoxX - 1) / kBoxX;
-    const int tiles = tiles_x * ((p.height + kBoxRows - 1) / kBoxRows);
+    const int tiles_x = (p.width + kBoxXElems - 1) / kBoxXElems;
+    const int tiles = tiles_x * ((p.height + kRows - 1) / kRows);
     const int slabs = (n_members + kBoxMembers - 1) / kBoxMembers;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -220,13 +225,13 @@ depth_tma_kernel(const __grid_constant__ CUtensorMap map, Plane p, int n_members
 
     if (threadIdx.x >= kConsumers) {
         if (threadIdx.x == kConsumers)
-            produce(sh, &map, tiles, tiles_x, slabs, kBoxX, timeout_ns, flags);
+            produce(sh, &map, tiles, tiles_x, slabs, kBoxXElems, kRows, timeout_ns, flags);
         return;
     }
 
     float *plane = static_cast<float *>(p.data);
-    const int row = threadIdx.x / 8, grp = threadIdx.x % 8;
-    const int offset = row * kBoxRowBytes + grp * 16;
+    const int row = threadIdx.x / kGroupsPerRow, grp = threadIdx.x % kGroupsPerRow;
+    const int offset = row * kBoxX + grp * 16;
     uint32_t it = 0;
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
         const int tx = tile % tiles_x, ty = tile / tiles_x;
@@ -249,8 +254,8 @@ depth_tma_kernel(const __grid_constant__ CUtensorMap map, Plane p, int n_members
             }
             mbar_arrive(&sh.empty[s]);
         }
-        const int y = ty * kBoxRows + row;
-        const int x0 = tx * kBoxX + grp * 4;
+        const int y = ty * kRows + row;
+        const int x0 = tx * kBoxXElems + grp * 4;
         if (y < p.height && x0 < p.width)
             apply_depth_group(plane + (int64_t)y * p.pitch + x0, min(4, p.width - x0), acc, sign);
     }
@@ -289,12 +294,19 @@ bool tma_compatible(const RasterBatch &b) {
            b.member_stride < (int64_t(1) << 40);
 }
 
-int encode_tma_map(CUtensorMap *map, const RasterBatch &b, int width, int height, int elem_bytes) {
+bool tma_box_supported(int box_bytes) {
+    return box_bytes == 64 || box_bytes == 128 || box_bytes == 256;
+}
+
+int encode_tma_map(CUtensorMap *map, const RasterBatch &b, int width, int height, int elem_bytes,
+                   int box_bytes) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = get_encoder();
     if (!enc) return CUDA_ERROR_NOT_FOUND;
+    if (!tma_box_supported(box_bytes)) return CUDA_ERROR_INVALID_VALUE;
     cuuint64_t dims[3] = {(cuuint64_t)width, (cuuint64_t)height, (cuuint64_t)b.n};
     cuuint64_t strides[2] = {(cuuint64_t)b.row_pitch, (cuuint64_t)b.member_stride};
-    cuuint32_t box[3] = {(cuuint32_t)(kBoxRowBytes / elem_bytes), kBoxRows, kBoxMembers};
+    cuuint32_t box[3] = {(cuuint32_t)(box_bytes / elem_bytes), (cuuint32_t)(kMemberPlaneBytes / box_bytes),
+                         kBoxMembers};
     cuuint32_t estrides[3] = {1, 1, 1};
     CUresult r = enc(map,
                      elem_bytes == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
@@ -304,35 +316,60 @@ int encode_tma_map(CUtensorMap *map, const RasterBatch &b, int width, int height
     return (int)r;
 }
 
+template <typename CountT, int kBoxX>
+cudaError_t launch_count_tma_t(const CUtensorMap &map, const RasterBatch &b, const Plane &p, int sign,
+                               int *flags, uint64_t timeout_ns, const DeviceCaps &caps, cudaStream_t s) {
+    constexpr int kRows = kMemberPlaneBytes / kBoxX;
+    static cudaError_t prep = prepare(count_tma_kernel<CountT, kBoxX>);
+    if (prep != cudaSuccess) return prep;
+    const int tiles = ((p.width + kBoxX - 1) / kBoxX) * ((p.height + kRows - 1) / kRows);
+    count_tma_kernel<CountT, kBoxX><<<grid_for(tiles, caps), kThreads, kSmemBytes, s>>>(
+        map, p, b.n, sign, flags, timeout_ns);
+    return cudaGetLastError();
+}
+
+template <int kBoxX>
+cudaError_t launch_depth_tma_t(const CUtensorMap &map, const RasterBatch &b, const Plane &p, int sign,
+                               int *flags, uint64_t timeout_ns, const DeviceCaps &caps, cudaStream_t s) {
+    constexpr int kRows = kMemberPlaneBytes / kBoxX;
+    static cudaError_t prep = prepare(depth_tma_kernel<kBoxX>);
+    if (prep != cudaSuccess) return prep;
+    const int tiles = ((p.width + kBoxX / 4 - 1) / (kBoxX / 4)) * ((p.height + kRows - 1) / kRows);
+    depth_tma_kernel<kBoxX><<<grid_for(tiles, caps), kThreads, kSmemBytes, s>>>(map, p, b.n, sign, flags,
+                                                                                 timeout_ns);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_count_tma(const CUtensorMap &map, const RasterBatch &b, const Plane &p, int sign,
-                             int *flags, uint64_t timeout_ns, const DeviceCaps &caps, cudaStream_t s) {
+                             int *flags, uint64_t timeout_ns, int box_bytes, const DeviceCaps &caps,
+                             cudaStream_t s) {
     if (b.n <= 0) return cudaSuccess;
-    const int tiles = ((p.width + kBoxRowBytes - 1) / kBoxRowBytes) * ((p.height + kBoxRows - 1) / kBoxRows);
-    cudaError_t e;
-    if (p.count_bits == 16) {
-        static cudaError_t prep = prepare(count_tma_kernel<uint16_t>);
-        if (prep != cudaSuccess) return prep;
-        count_tma_kernel<uint16_t><<<grid_for(tiles, caps), kThreads, kSmemBytes, s>>>(
-            map, p, b.n, sign, flags, timeout_ns);
-    } else {
-        static cudaError_t prep = prepare(count_tma_kernel<uint32_t>);
-        if (prep != cudaSuccess) return prep;
-        count_tma_kernel<uint32_t><<<grid_for(tiles, caps), kThreads, kSmemBytes, s>>>(
-            map, p, b.n, sign, flags, timeout_ns);
+    const bool u16 = p.count_bits == 16;
+    switch (box_bytes) {
+        case 64:
+            return u16 ? launch_count_tma_t<uint16_t, 64>(map, b, p, sign, flags, timeout_ns, caps, s)
+                       : launch_count_tma_t<uint32_t, 64>(map, b, p, sign, flags, timeout_ns, caps, s);
+        case 128:
+            return u16 ? launch_count_tma_t<uint16_t, 128>(map, b, p, sign, flags, timeout_ns, caps, s)
+                       : launch_count_tma_t<uint32_t, 128>(map, b, p, sign, flags, timeout_ns, caps, s);
+        case 256:
+            return u16 ? launch_count_tma_t<uint16_t, 256>(map, b, p, sign, flags, timeout_ns, caps, s)
+                       : launch_count_tma_t<uint32_t, 256>(map, b, p, sign, flags, timeout_ns, caps, s);
+        default:
+            return cudaErrorInvalidValue;
     }
-    e = cudaGetLastError();
-    return e;
 }
 
 cudaError_t launch_depth_tma(const CUtensorMap &map, const RasterBatch &b, const Plane &p, int sign,
-                             int *flags, uint64_t timeout_ns, const DeviceCaps &caps, cudaStream_t s) {
+                             int *flags, uint64_t timeout_ns, int box_bytes, const DeviceCaps &caps,
+                             cudaStream_t s) {
     if (b.n <= 0) return cudaSuccess;
-    const int tiles = ((p.width + 31) / 32) * ((p.height + kBoxRows - 1) / kBoxRows);
-    static cudaError_t prep = prepare(depth_tma_kernel);
-    if (prep != cudaSuccess) return prep;
-    depth_tma_kernel<<<grid_for(tiles, caps), kThreads, kSmemBytes, s>>>(map, p, b.n, sign, flags,
-                                                                          timeout_ns);
-    return cudaGetLastError();
+    switch (box_bytes) {
+        case 64: return launch_depth_tma_t<64>(map, b, p, sign, flags, timeout_ns, caps, s);
+        case 128: return launch_depth_tma_t<128>(map, b, p, sign, flags, timeout_ns, caps, s);
+        case 256: return launch_depth_tma_t<256>(map, b, p, sign, flags, timeout_ns, caps, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace cpt

@@ -43,7 +43,8 @@ def test_begin_rejects_empty_raster(lib, w, h):
 @pytest.mark.parametrize("field,value", [("read_path", 3), ("staging_buffers", 0), ("staging_buffers", 9),
                                          ("chunk_members", 0), ("chunk_members", 256), ("count_bits", 8),
                                          ("mode", 2), ("trace", 2), ("wait_timeout_ms", -1),
-                                         ("host_read", 2)])
+                                         ("host_read", 2), ("tma_box_bytes", 32),
+                                         ("tma_box_bytes", 512)])
 def test_begin_rejects_bad_config(lib, field, value):
     cfg = binding.composite_default_config()
     setattr(cfg, field, value)

@@ -263,3 +263,20 @@ def test_host_read_in_place(w, h, n):
         comp.add(as_kind(m, "pinned"))
         comp.remove(as_kind(m[: n // 2], "pinned"))
         check_counts(comp, m[n // 2:])
+
+
+@pytest.mark.parametrize("box", [64, 128, 256])
+@pytest.mark.parametrize("mode", ["count", "mean_depth"])
+@pytest.mark.parametrize("w,h,n", [(1000, 37, 19), (13, 200, 9), (257, 129, 270)])
+def test_tma_box_widths(box, mode, w, h, n):
+    if mode == "count":
+        m = synth.scramble_nonzero(synth.random_masks(40 + box, n, h, w), 40)
+    else:
+        m = synth.random_depths(41 + box, n, h, w)
+    with binding.Composite(w, h, read_path="tma", tma_box_bytes=box, mode=mode) as comp:
+        comp.add(as_kind(m, "pinned"))
+        if mode == "count":
+            check_counts(comp, m)
+        else:
+            got = comp.render_host()["mean"]
+            assert np.abs(got.astype(np.float64) - oracle.mean_depth(m)).max() <= 1e-5 * n

@@ -1,0 +1,133 @@
+/*
+ * composite_engine.h -- C ABI of the batched composite engine.
+ *
+ * Many composites at once (the batched and interactive uses of the paper's
+ * flood-analysis program, Section 2 and Fig. 1: several member selections,
+ * each folded into its own composite and shown as its own saturation map).
+ * The engine holds composite planes in device memory (uint32 counts, one per
+ * plane) and applies "ops" to them: add or remove a set of device-resident
+ * uint8 masks to one plane.  All ops of one submit call run in ONE persistent
+ * kernel launch whose CTAs pull work items (op, member slab, tile of 256
+ * 16-pixel groups) from a device counter, so small and large composites share
+ * the GPU without one launch per composite; one render call likewise renders
+ * many planes in one launch.  A submit + render sequence can be captured in a
+ * CUDA graph and replayed, and an autotuner picks the slab depth and the CTAs
+ * per SM by timing candidates on the caller's ops.
+ *
+ * Per pixel p of plane P (members S_P, N_P = |S_P|), exactly as composite.h:
+ *   count(p) = #{m in S_P : mask_m(p) != 0}
+ *   bucket(p) = N_P == 0 ? 0 : floor(255 count(p) / N_P); rgba(p) = lut[bucket(p)]
+ *
+ * Conventions: every call returns CPT_OK (0) or a negative composite_status
+ * (composite.h); the message is in composite_engine_last_error.  Device
+ * pointers only (members, index lists, outputs); rasters need 16-byte
+ * aligned base, row pitch and member stride.  Work is queued on the engine's
+ * stream; host waits are bounded by wait_timeout_ms.  Members and index
+ * lists are borrowed until the next composite_engine_sync returns.
+ */
+#ifndef COMPOSITE_ENGINE_H
+#define COMPOSITE_ENGINE_H
+
+#include <stdint.h>
+
+#include "composite.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct composite_engine composite_engine;
+
+typedef struct composite_engine_config {
+    void *cuda_stream;        /* cudaStream_t for all engine work, NULL = engine-owned */
+    int32_t slab_members;     /* members per work item, 1..255; 0 = 128               */
+    int32_t ctas_per_sm;      /* persistent CTAs of 256 threads per SM, 1..8; 0 = 6   */
+    int64_t wait_timeout_ms;  /* bound on host waits; 0 = 10000                        */
+} composite_engine_config;
+
+/* One add or remove of n_members masks to one plane.  Member i of the op is
+ * the raster at members + idx(i) * member_stride_bytes, idx(i) =
+ * member_index[i] (a device int32 array) or i when member_index is NULL.
+ * The raster's width and height are the plane's. */
+typedef struct composite_op {
+    int32_t plane;
+    int32_t sign;                 /* +1 add, -1 remove */
+    const void *members;          /* device, 16-byte aligned */
+    const int32_t *member_index;  /* device, n_members entries, or NULL */
+    int32_t n_members;
+    int32_t row_pitch_bytes;      /* multiple of 16, >= width */
+    int64_t member_stride_bytes;  /* multiple of 16, >= row_pitch_bytes * height */
+} composite_op;
+
+/* Render of one plane into dense row-major device outputs (each may be NULL). */
+typedef struct composite_render_op {
+    int32_t plane;
+    uint32_t *counts_out;   /* width x height uint32, 4-byte aligned */
+    uint8_t *bucket_out;    /* width x height */
+    uint8_t *rgba_out;      /* width x height x 4, 4-byte aligned */
+} composite_render_op;
+
+int composite_engine_default_config(composite_engine_config *cfg);
+
+/* Creates an engine (no planes yet).  cfg NULL = defaults. */
+int composite_engine_begin(composite_engine **out, const composite_engine_config *cfg);
+
+/* Allocates a zeroed width x height uint32 plane (N = 0); *plane_out is its id. */
+int composite_engine_add_plane(composite_engine *eng, int32_t width, int32_t height, int32_t *plane_out);
+
+/* Frees a plane after the engine's queued work; its id is not reused. */
+int composite_engine_free_plane(composite_engine *eng, int32_t plane);
+
+/* Queues a clear of the plane (counts 0, N = 0, underflow state cleared). */
+int composite_engine_clear(composite_engine *eng, int32_t plane);
+
+/* Queues every op in one persistent accumulate launch.  Validates all ops on
+ * the host first (CPT_EINVAL and nothing queued if one is bad: unknown plane,
+ * sign not +-1, N of a plane would go negative or above 2^32-1, bad strides).
+ * A pixel count that would go below zero raises the plane's underflow state
+ * (reported by composite_engine_sync). */
+int composite_engine_submit(composite_engine *eng, const composite_op *ops, int32_t n_ops);
+
+/* Queues the render of every listed plane in one persistent launch.
+ * lut_rgba: 256 x 4 host bytes or NULL for the default white-to-blue ramp. */
+int composite_engine_render(composite_engine *eng, const composite_render_op *ops, int32_t n_ops,
+                            const uint8_t *lut_rgba);
+
+/* *n_out = N of the plane (host bookkeeping, exact). */
+int composite_engine_member_count(const composite_engine *eng, int32_t plane, int64_t *n_out);
+
+/* Waits (bounded) for the engine's queued work.  CPT_EUNDERFLOW if some
+ * plane underflowed since its last clear; *bad_plane_out (may be NULL) then
+ * holds the first such plane. */
+int composite_engine_sync(composite_engine *eng, int32_t *bad_plane_out);
+
+/* Captures "clear every target plane, submit ops, render rops" as a CUDA
+ * graph held by the engine (replacing any earlier one); the ops' member
+ * sets, index lists and outputs are fixed by the capture.  Does not run it. */
+int composite_engine_capture(composite_engine *eng, const composite_op *ops, int32_t n_ops,
+                             const composite_render_op *rops, int32_t n_rops, const uint8_t *lut_rgba);
+
+/* Launches the captured graph once on the engine's stream. */
+int composite_engine_replay(composite_engine *eng);
+
+/* Autotuner: times "clear the ops' planes + submit ops" for every candidate
+ * (slab_members in {32, 64, 128, 255} x ctas_per_sm in {4, 6, 8}), `repeats`
+ * runs each, keeps the fastest pair as the engine's configuration and
+ * reports it (either pointer may be NULL).  The planes end holding the
+ * result of the ops applied once to cleared planes. */
+int composite_engine_tune(composite_engine *eng, const composite_op *ops, int32_t n_ops, int32_t repeats,
+                          int32_t *slab_out, int32_t *ctas_per_sm_out);
+
+/* Current (slab_members, ctas_per_sm). */
+int composite_engine_get_tuning(const composite_engine *eng, int32_t *slab_out, int32_t *ctas_per_sm_out);
+
+/* Waits (bounded) and frees everything.  NULL is accepted. */
+int composite_engine_end(composite_engine *eng);
+
+const char *composite_engine_last_error(const composite_engine *eng);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* COMPOSITE_ENGINE_H */

@@ -31,6 +31,7 @@ READ_PATHS = {"linear": CPT_READ_LINEAR, "texture": CPT_READ_TEXTURE, "tma": CPT
 CPT_MODE_COUNT, CPT_MODE_MEAN_DEPTH = 0, 1
 
 HEADER = os.path.join(_build.INCLUDE, "composite.h")
+HEADERS = [os.path.join(_build.INCLUDE, h) for h in ("composite.h", "composite_engine.h")]
 
 
 class CompositeError(RuntimeError):
@@ -99,8 +100,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
 
 
 def declared_functions() -> list[str]:
-    """Every function the public header declares."""
-    text = open(HEADER).read()
+    """Every function the public headers declare."""
+    text = "".join(open(h).read() for h in HEADERS)
     return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(composite_\w+)\s*\(", text, re.M)))
 
 
@@ -340,6 +341,206 @@ class Composite:
             ctx, self.ctx = self.ctx, None
             composite_end(ctx)
             self._borrowed.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# --- the batched engine (include/composite_engine.h) -------------------------
+
+class EngineConfig(ctypes.Structure):
+    _fields_ = [
+        ("cuda_stream", ctypes.c_void_p),
+        ("slab_members", ctypes.c_int32),
+        ("ctas_per_sm", ctypes.c_int32),
+        ("wait_timeout_ms", ctypes.c_int64),
+    ]
+
+
+class Op(ctypes.Structure):
+    _fields_ = [
+        ("plane", ctypes.c_int32),
+        ("sign", ctypes.c_int32),
+        ("members", ctypes.c_void_p),
+        ("member_index", ctypes.c_void_p),
+        ("n_members", ctypes.c_int32),
+        ("row_pitch_bytes", ctypes.c_int32),
+        ("member_stride_bytes", ctypes.c_int64),
+    ]
+
+
+class RenderOp(ctypes.Structure):
+    _fields_ = [
+        ("plane", ctypes.c_int32),
+        ("counts_out", ctypes.c_void_p),
+        ("bucket_out", ctypes.c_void_p),
+        ("rgba_out", ctypes.c_void_p),
+    ]
+
+
+_engine_sig_done = False
+
+
+def _engine_lib():
+    global _engine_sig_done
+    lib = load()
+    if not _engine_sig_done:
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        p32, p64 = ctypes.POINTER(i32), ctypes.POINTER(i64)
+        sig = {
+            "composite_engine_default_config": (ctypes.c_int, [ctypes.POINTER(EngineConfig)]),
+            "composite_engine_begin": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(EngineConfig)]),
+            "composite_engine_add_plane": (ctypes.c_int, [vp, i32, i32, p32]),
+            "composite_engine_free_plane": (ctypes.c_int, [vp, i32]),
+            "composite_engine_clear": (ctypes.c_int, [vp, i32]),
+            "composite_engine_submit": (ctypes.c_int, [vp, ctypes.POINTER(Op), i32]),
+            "composite_engine_render": (ctypes.c_int, [vp, ctypes.POINTER(RenderOp), i32, vp]),
+            "composite_engine_member_count": (ctypes.c_int, [vp, i32, p64]),
+            "composite_engine_sync": (ctypes.c_int, [vp, p32]),
+            "composite_engine_capture": (ctypes.c_int, [vp, ctypes.POINTER(Op), i32, ctypes.POINTER(RenderOp),
+                                                        i32, vp]),
+            "composite_engine_replay": (ctypes.c_int, [vp]),
+            "composite_engine_tune": (ctypes.c_int, [vp, ctypes.POINTER(Op), i32, i32, p32, p32]),
+            "composite_engine_get_tuning": (ctypes.c_int, [vp, p32, p32]),
+            "composite_engine_end": (ctypes.c_int, [vp]),
+            "composite_engine_last_error": (ctypes.c_char_p, [vp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _engine_sig_done = True
+    return lib
+
+
+def _echeck(lib, eng, rc):
+    if rc != CPT_OK:
+        msg = lib.composite_engine_last_error(eng)
+        raise CompositeError(rc, msg.decode() if msg else "")
+
+
+def _lut_ptr(lut):
+    if lut is None:
+        return None, None
+    arr = np.ascontiguousarray(np.asarray(lut, dtype=np.uint8).reshape(256, 4))
+    return arr, arr.ctypes.data
+
+
+class Engine:
+    """Many composite planes on one GPU; ops on all of them run in one
+    persistent launch (include/composite_engine.h)."""
+
+    def __init__(self, stream=None, slab_members=0, ctas_per_sm=0, wait_timeout_ms=0):
+        self.lib = _engine_lib()
+        cfg = EngineConfig()
+        self.lib.composite_engine_default_config(ctypes.byref(cfg))
+        cfg.cuda_stream = stream
+        cfg.slab_members = slab_members
+        cfg.ctas_per_sm = ctas_per_sm
+        cfg.wait_timeout_ms = wait_timeout_ms
+        h = ctypes.c_void_p()
+        _echeck(self.lib, None, self.lib.composite_engine_begin(ctypes.byref(h), ctypes.byref(cfg)))
+        self.h = h
+        self._keep = []
+        self.shapes = {}
+
+    def add_plane(self, width: int, height: int) -> int:
+        pid = ctypes.c_int32()
+        _echeck(self.lib, self.h, self.lib.composite_engine_add_plane(self.h, width, height, ctypes.byref(pid)))
+        self.shapes[pid.value] = (width, height)
+        return pid.value
+
+    def free_plane(self, plane: int):
+        _echeck(self.lib, self.h, self.lib.composite_engine_free_plane(self.h, plane))
+
+    def clear(self, plane: int):
+        _echeck(self.lib, self.h, self.lib.composite_engine_clear(self.h, plane))
+
+    @staticmethod
+    def op(plane: int, members, sign: int = 1, index=None) -> Op:
+        """An op from a device tensor of masks [n, H, W] (or the whole
+        ensemble when an int32 device index tensor selects members)."""
+        ptr, n, _, _, stride, pitch, _, _ = _raster_view(members)
+        o = Op()
+        o.plane, o.sign, o.members = plane, sign, ptr
+        o.row_pitch_bytes, o.member_stride_bytes = pitch, stride
+        if index is not None:
+            o.member_index = index.data_ptr()
+            o.n_members = int(index.numel())
+        else:
+            o.member_index = None
+            o.n_members = n
+        return o
+
+    @staticmethod
+    def render_op(plane: int, counts_out=None, bucket_out=None, rgba_out=None) -> RenderOp:
+        r = RenderOp()
+        r.plane = plane
+        r.counts_out, r.bucket_out, r.rgba_out = _ptr(counts_out), _ptr(bucket_out), _ptr(rgba_out)
+        return r
+
+    def submit(self, ops, keep=()):
+        arr = (Op * len(ops))(*ops)
+        self._keep.extend(keep)
+        _echeck(self.lib, self.h, self.lib.composite_engine_submit(self.h, arr, len(ops)))
+
+    def render(self, rops, lut=None, keep=()):
+        arr = (RenderOp * len(rops))(*rops)
+        l, lp = _lut_ptr(lut)
+        self._keep.extend(keep)
+        _echeck(self.lib, self.h, self.lib.composite_engine_render(self.h, arr, len(rops), lp))
+
+    def member_count(self, plane: int) -> int:
+        n = ctypes.c_int64()
+        _echeck(self.lib, self.h, self.lib.composite_engine_member_count(self.h, plane, ctypes.byref(n)))
+        return n.value
+
+    def sync(self):
+        bad = ctypes.c_int32()
+        rc = self.lib.composite_engine_sync(self.h, ctypes.byref(bad))
+        self._keep.clear()
+        if rc != CPT_OK:
+            msg = self.lib.composite_engine_last_error(self.h)
+            err = CompositeError(rc, msg.decode() if msg else "")
+            err.plane = bad.value
+            raise err
+
+    def capture(self, ops, rops, lut=None, keep=()):
+        a = (Op * len(ops))(*ops)
+        r = (RenderOp * len(rops))(*rops)
+        l, lp = _lut_ptr(lut)
+        self._graph_keep = list(keep)
+        _echeck(self.lib, self.h, self.lib.composite_engine_capture(self.h, a, len(ops), r, len(rops), lp))
+
+    def replay(self):
+        _echeck(self.lib, self.h, self.lib.composite_engine_replay(self.h))
+
+    def tune(self, ops, repeats: int = 2):
+        a = (Op * len(ops))(*ops)
+        s, c = ctypes.c_int32(), ctypes.c_int32()
+        _echeck(self.lib, self.h, self.lib.composite_engine_tune(self.h, a, len(ops), repeats,
+                                                                  ctypes.byref(s), ctypes.byref(c)))
+        return s.value, c.value
+
+    def tuning(self):
+        s, c = ctypes.c_int32(), ctypes.c_int32()
+        _echeck(self.lib, self.h, self.lib.composite_engine_get_tuning(self.h, ctypes.byref(s), ctypes.byref(c)))
+        return s.value, c.value
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            h, self.h = self.h, None
+            self.lib.composite_engine_end(h)
+            self._keep.clear()
 
     def __enter__(self):
         return self

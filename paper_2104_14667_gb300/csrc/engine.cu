@@ -1,0 +1,790 @@
+// engine.cu -- the batched composite engine of include/composite_engine.h.
+//
+// A submit turns every op (add/remove a member set to one plane) into work
+// items (op, member slab, tile of 256 16-pixel groups), numbered op after op,
+// slab after slab, tile after tile.  One persistent launch of
+// num_SMs x ctas_per_sm CTAs pulls item numbers from a device counter; the
+// op owning an item is found by binary search over the ops' first items.
+// Each thread of the CTA folds its group of one slab's members into packed
+// byte counters (member i of the op read at base + idx(i) * stride, the
+// slab's indices staged in shared memory) and adds the counts into the
+// op's uint32 plane with L2 atomics.  The render launch works the same way
+// over (plane, tile) items.  Consecutive items are neighbouring tiles of the
+// same slab, so concurrently running CTAs read neighbouring bytes of the
+// same members.
+#include <algorithm>
+#include <chrono>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "composite_engine.h"
+#include "device_common.cuh"
+
+namespace {
+
+using cpt::DeviceCaps;
+using cpt::Lut;
+
+constexpr int kThreads = 256;          // threads per CTA = 16-pixel groups per tile
+constexpr int kMaxPlanes = 1 << 16;
+constexpr int kMaxSlab = 255;          // packed byte counters
+
+struct OpDesc {
+    const uint8_t *base;
+    const int32_t *index;
+    uint32_t *plane;
+    int64_t stride;
+    int64_t plane_pitch;   // elements
+    int64_t item_start;
+    int32_t pitch;
+    int32_t n;
+    int32_t width;
+    int32_t height;
+    int32_t groups_per_row;
+    int32_t tiles;
+    int32_t slab;
+    int32_t sign;
+    int32_t plane_id;
+    int32_t pad;
+};
+
+struct RenderDesc {
+    const uint32_t *plane;
+    uint32_t *counts_out;
+    uint8_t *bucket_out;
+    uint32_t *rgba_out;
+    int64_t plane_pitch;
+    int64_t item_start;
+    uint64_t n_members;
+    int32_t width;
+    int32_t height;
+    int32_t groups_per_row;
+    int32_t tiles;
+    int32_t vec;           // 16-byte stores allowed
+    int32_t pad;
+};
+
+template <typename Desc>
+__device__ __forceinline__ int find_desc(const Desc *d, int n, int64_t item) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (d[mid].item_start <= item)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kThreads, 6)
+engine_accumulate_kernel(const OpDesc *ops, int n_ops, uint32_t n_items, uint32_t *counter, int *flags) {
+    __shared__ uint32_t s_item;
+    __shared__ int32_t s_index[kMaxSlab];
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1u);
+        __syncthreads();
+        const uint32_t item = s_item;
+        if (item >= n_items) break;
+        const OpDesc &op = ops[find_desc(ops, n_ops, item)];
+        const uint32_t local = item - (uint32_t)op.item_start;
+        const int sl = (int)(local / (uint32_t)op.tiles);
+        const int tile = (int)(local - (uint32_t)sl * op.tiles);
+        const int m0 = sl * op.slab;
+        const int cnt = min(op.n - m0, op.slab);
+        if (op.index)
+            for (int i = threadIdx.x; i < cnt; i += kThreads) s_index[i] = op.index[m0 + i];
+        __syncthreads();
+        const int64_t g = (int64_t)tile * kThreads + threadIdx.x;
+        if (g < (int64_t)op.groups_per_row * op.height) {
+            const int y = (int)(g / op.groups_per_row);
+            const int x0 = (int)(g - (int64_t)y * op.groups_per_row) * 16;
+            const int valid = min(16, op.width - x0);
+            const uint8_t *row = op.base + (int64_t)y * op.pitch + x0;
+            uint32_t k[4] = {0u, 0u, 0u, 0u};
+            if (valid == 16) {
+#pragma unroll 8
+                for (int i = 0; i < cnt; ++i) {
+                    const int64_t mi = op.index ? s_index[i] : (int64_t)(m0 + i);
+                    const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(row + mi * op.stride));
+                    k[0] += cpt::nonzero_bytes(v.x);
+                    k[1] += cpt::nonzero_bytes(v.y);
+                    k[2] += cpt::nonzero_bytes(v.z);
+                    k[3] += cpt::nonzero_bytes(v.w);
+                }
+            } else {
+                for (int i = 0; i < cnt; ++i) {
+                    const int64_t mi = op.index ? s_index[i] : (int64_t)(m0 + i);
+                    const uint8_t *q = row + mi * op.stride;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (j < valid) k[j / 4] += (uint32_t)(q[j] != 0) << (8 * (j % 4));
+                }
+            }
+            uint32_t wide[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) wide[j] = 0;
+            cpt::widen16(wide, k[0], k[1], k[2], k[3]);
+            cpt::atomic_count_group<uint32_t>(op.plane + (int64_t)y * op.plane_pitch + x0, wide, op.sign,
+                                              flags + op.plane_id);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+engine_render_kernel(const RenderDesc *ops, int n_ops, uint32_t n_items, uint32_t *counter, Lut lut) {
+    __shared__ uint32_t table[256];
+    __shared__ uint32_t s_item;
+    for (int i = threadIdx.x; i < 256; i += kThreads) table[i] = lut.rgba[i];
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1u);
+        __syncthreads();
+        const uint32_t item = s_item;
+        if (item >= n_items) break;
+        const RenderDesc op = ops[find_desc(ops, n_ops, item)];
+        const int64_t g = (int64_t)(item - (uint32_t)op.item_start) * kThreads + threadIdx.x;
+        if (g < (int64_t)op.groups_per_row * op.height) {
+            const int y = (int)(g / op.groups_per_row);
+            const int x0 = (int)(g - (int64_t)y * op.groups_per_row) * 16;
+            const int valid = min(16, op.width - x0);
+            const uint4 *src = reinterpret_cast<const uint4 *>(op.plane + (int64_t)y * op.plane_pitch + x0);
+            uint32_t c[16];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint4 v = src[q];
+                c[4 * q] = v.x; c[4 * q + 1] = v.y; c[4 * q + 2] = v.z; c[4 * q + 3] = v.w;
+            }
+            uint32_t b[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) b[j] = cpt::overlap_class(c[j], op.n_members);
+            const int64_t out = (int64_t)y * op.width + x0;
+            if (op.vec && valid == 16) {
+                if (op.counts_out) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        reinterpret_cast<uint4 *>(op.counts_out + out)[q] =
+                            make_uint4(c[4 * q], c[4 * q + 1], c[4 * q + 2], c[4 * q + 3]);
+                }
+                if (op.bucket_out) {
+                    uint32_t w[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        w[q] = b[4 * q] | (b[4 * q + 1] << 8) | (b[4 * q + 2] << 16) | (b[4 * q + 3] << 24);
+                    *reinterpret_cast<uint4 *>(op.bucket_out + out) = make_uint4(w[0], w[1], w[2], w[3]);
+                }
+                if (op.rgba_out) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        reinterpret_cast<uint4 *>(op.rgba_out + out)[q] =
+                            make_uint4(table[b[4 * q]], table[b[4 * q + 1]], table[b[4 * q + 2]], table[b[4 * q + 3]]);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    if (j < valid) {
+                        if (op.counts_out) op.counts_out[out + j] = c[j];
+                        if (op.bucket_out) op.bucket_out[out + j] = (uint8_t)b[j];
+                        if (op.rgba_out) op.rgba_out[out + j] = table[b[j]];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+struct PlaneRec {
+    int32_t width = 0, height = 0;
+    int64_t pitch_px = 0;
+    uint32_t *data = nullptr;
+    int64_t n = 0;
+    bool alive = false;
+};
+
+// A device buffer of descriptors with its pinned host mirror.
+struct Upload {
+    void *d = nullptr;
+    void *h = nullptr;
+    size_t cap = 0;
+    cudaEvent_t done = nullptr;
+    bool used = false;
+};
+
+thread_local std::string g_engine_error;
+
+}  // namespace
+
+struct composite_engine {
+    composite_engine_config cfg{};
+    int device = 0;
+    DeviceCaps caps{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<PlaneRec> planes;
+    int *d_flags = nullptr;
+    int *h_flags = nullptr;
+    uint32_t *d_counter = nullptr;
+    Upload up_ops[2], up_render[2];
+    int up_i = 0, rup_i = 0;
+    cudaEvent_t done_ev = nullptr;
+    Lut default_lut{};
+    // captured graph
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    void *graph_ops = nullptr;
+    void *graph_rops = nullptr;
+    uint32_t *graph_counters = nullptr;
+    std::vector<std::pair<int32_t, int64_t>> graph_n;   // plane -> N after a replay
+    std::vector<int32_t> graph_planes;                  // every plane the graph touches
+    std::string err;
+};
+
+namespace {
+
+int efail(composite_engine *e, int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (e)
+        e->err = buf;
+    else
+        g_engine_error = buf;
+    return code;
+}
+
+int ecuda(composite_engine *e, cudaError_t err, const char *what) {
+    return efail(e, err == cudaErrorMemoryAllocation ? CPT_ENOMEM : CPT_ECUDA, "%s: %s", what,
+                 cudaGetErrorString(err));
+}
+
+#define ECK(e, call)                                      \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return ecuda(e, e_, #call); \
+    } while (0)
+
+int64_t etimeout(const composite_engine *e) { return e->cfg.wait_timeout_ms > 0 ? e->cfg.wait_timeout_ms : 10000; }
+
+int ewait(composite_engine *e, cudaEvent_t ev) {
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::milliseconds(etimeout(e));
+    for (unsigned spin = 0;; ++spin) {
+        const cudaError_t r = cudaEventQuery(ev);
+        if (r == cudaSuccess) return CPT_OK;
+        if (r != cudaErrorNotReady) return ecuda(e, r, "cudaEventQuery");
+        if (std::chrono::steady_clock::now() > deadline)
+            return efail(e, CPT_ETIMEOUT, "wait exceeded %lld ms", (long long)etimeout(e));
+        if (spin < 2000)
+            std::this_thread::yield();
+        else
+            std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+}
+
+int drain(composite_engine *e) {
+    ECK(e, cudaEventRecord(e->done_ev, e->stream));
+    return ewait(e, e->done_ev);
+}
+
+Lut make_lut(const uint8_t *rgba) {
+    Lut l;
+    for (int b = 0; b < 256; ++b) {
+        const uint32_t r = rgba ? rgba[4 * b] : 255u - b, g = rgba ? rgba[4 * b + 1] : 255u - b;
+        const uint32_t bl = rgba ? rgba[4 * b + 2] : 255u, a = rgba ? rgba[4 * b + 3] : 255u;
+        l.rgba[b] = r | (g << 8) | (bl << 16) | (a << 24);
+    }
+    return l;
+}
+
+// Copies `bytes` of descriptors into the next slot of a two-slot upload ring
+// and queues their upload; returns the device copy.
+int upload(composite_engine *e, Upload *ring, int *idx, const void *src, size_t bytes, void **dev) {
+    Upload &u = ring[*idx];
+    *idx ^= 1;
+    if (u.used) {
+        int rc = ewait(e, u.done);
+        if (rc) return rc;
+    }
+    if (u.cap < bytes) {
+        if (u.d) cudaFree(u.d);
+        if (u.h) cudaFreeHost(u.h);
+        u.d = u.h = nullptr;
+        u.cap = 0;
+        const size_t cap = std::max<size_t>(bytes, 4096);
+        ECK(e, cudaMalloc(&u.d, cap));
+        ECK(e, cudaHostAlloc(&u.h, cap, cudaHostAllocDefault));
+        u.cap = cap;
+    }
+    memcpy(u.h, src, bytes);
+    ECK(e, cudaMemcpyAsync(u.d, u.h, bytes, cudaMemcpyHostToDevice, e->stream));
+    ECK(e, cudaEventRecord(u.done, e->stream));
+    u.used = true;
+    *dev = u.d;
+    return CPT_OK;
+}
+
+bool plane_ok(const composite_engine *e, int32_t p) {
+    return p >= 0 && p < (int32_t)e->planes.size() && e->planes[p].alive;
+}
+
+// Validates ops and builds their descriptors.  n_after holds, per plane
+// touched, the member count after the ops starting from `start` counts.
+int plan_ops(composite_engine *e, const composite_op *ops, int32_t n_ops, std::vector<OpDesc> *descs,
+             int64_t *n_items, std::vector<std::pair<int32_t, int64_t>> *n_after, bool from_zero) {
+    if (n_ops < 0 || (n_ops > 0 && !ops)) return efail(e, CPT_EINVAL, "bad op list");
+    descs->clear();
+    n_after->clear();
+    std::vector<int64_t> n(e->planes.size(), -1);
+    int64_t items = 0;
+    const int slab = e->cfg.slab_members;
+    for (int32_t i = 0; i < n_ops; ++i) {
+        const composite_op &o = ops[i];
+        if (!plane_ok(e, o.plane)) return efail(e, CPT_EINVAL, "op %d: no plane %d", i, o.plane);
+        if (o.sign != 1 && o.sign != -1) return efail(e, CPT_EINVAL, "op %d: sign must be +1 or -1", i);
+        if (o.n_members < 0) return efail(e, CPT_EINVAL, "op %d: n_members < 0", i);
+        const PlaneRec &p = e->planes[o.plane];
+        if (n[o.plane] < 0) n[o.plane] = from_zero ? 0 : p.n;
+        n[o.plane] += (int64_t)o.sign * o.n_members;
+        if (n[o.plane] < 0) return efail(e, CPT_EINVAL, "op %d: plane %d would hold fewer than 0 members", i, o.plane);
+        if (n[o.plane] > 0xFFFFFFFFll) return efail(e, CPT_EINVAL, "op %d: plane %d would exceed 2^32-1 members", i, o.plane);
+        if (o.n_members == 0) continue;
+        if (!o.members) return efail(e, CPT_EINVAL, "op %d: members is NULL", i);
+        if ((reinterpret_cast<uintptr_t>(o.members) % 16) || (o.row_pitch_bytes % 16) || (o.member_stride_bytes % 16))
+            return efail(e, CPT_EINVAL, "op %d: members, row pitch and stride must be 16-byte aligned", i);
+        if (o.row_pitch_bytes < p.width || o.member_stride_bytes < (int64_t)o.row_pitch_bytes * p.height)
+            return efail(e, CPT_EINVAL, "op %d: row pitch or member stride too small", i);
+        OpDesc d{};
+        d.base = static_cast<const uint8_t *>(o.members);
+        d.index = o.member_index;
+        d.plane = p.data;
+        d.stride = o.member_stride_bytes;
+        d.plane_pitch = p.pitch_px;
+        d.item_start = items;
+        d.pitch = o.row_pitch_bytes;
+        d.n = o.n_members;
+        d.width = p.width;
+        d.height = p.height;
+        d.groups_per_row = (int32_t)(p.pitch_px / 16);
+        const int64_t groups = (int64_t)d.groups_per_row * p.height;
+        d.tiles = (int32_t)((groups + kThreads - 1) / kThreads);
+        d.slab = slab;
+        d.sign = o.sign;
+        d.plane_id = o.plane;
+        const int64_t slabs = (o.n_members + slab - 1) / slab;
+        items += slabs * d.tiles;
+        descs->push_back(d);
+    }
+    if (items >= (int64_t)1 << 31) return efail(e, CPT_EINVAL, "too many work items in one submit");
+    for (size_t p = 0; p < n.size(); ++p)
+        if (n[p] >= 0) n_after->push_back({(int32_t)p, n[p]});
+    *n_items = items;
+    return CPT_OK;
+}
+
+int plan_render(composite_engine *e, const composite_render_op *ops, int32_t n_ops, std::vector<RenderDesc> *descs,
+                int64_t *n_items, const std::vector<std::pair<int32_t, int64_t>> *n_override) {
+    if (n_ops < 0 || (n_ops > 0 && !ops)) return efail(e, CPT_EINVAL, "bad render list");
+    descs->clear();
+    int64_t items = 0;
+    for (int32_t i = 0; i < n_ops; ++i) {
+        const composite_render_op &o = ops[i];
+        if (!plane_ok(e, o.plane)) return efail(e, CPT_EINVAL, "render %d: no plane %d", i, o.plane);
+        if ((reinterpret_cast<uintptr_t>(o.counts_out) % 4) || (reinterpret_cast<uintptr_t>(o.rgba_out) % 4))
+            return efail(e, CPT_EINVAL, "render %d: counts_out and rgba_out must be 4-byte aligned", i);
+        const PlaneRec &p = e->planes[o.plane];
+        int64_t n = p.n;
+        if (n_override)
+            for (const auto &pn : *n_override)
+                if (pn.first == o.plane) n = pn.second;
+        RenderDesc d{};
+        d.plane = p.data;
+        d.counts_out = o.counts_out;
+        d.bucket_out = o.bucket_out;
+        d.rgba_out = reinterpret_cast<uint32_t *>(o.rgba_out);
+        d.plane_pitch = p.pitch_px;
+        d.item_start = items;
+        d.n_members = (uint64_t)n;
+        d.width = p.width;
+        d.height = p.height;
+        d.groups_per_row = (int32_t)(p.pitch_px / 16);
+        const int64_t groups = (int64_t)d.groups_per_row * p.height;
+        d.tiles = (int32_t)((groups + kThreads - 1) / kThreads);
+        const uintptr_t a = reinterpret_cast<uintptr_t>(o.counts_out) | reinterpret_cast<uintptr_t>(o.bucket_out) |
+                            reinterpret_cast<uintptr_t>(o.rgba_out);
+        d.vec = (p.width % 16 == 0) && (a % 16 == 0);
+        items += d.tiles;
+        descs->push_back(d);
+    }
+    if (items >= (int64_t)1 << 31) return efail(e, CPT_EINVAL, "too many render items");
+    *n_items = items;
+    return CPT_OK;
+}
+
+unsigned persistent_grid(const composite_engine *e, int64_t items) {
+    const int64_t cap = (int64_t)e->caps.num_sms * e->cfg.ctas_per_sm;
+    return (unsigned)std::max<int64_t>(1, std::min(cap, items));
+}
+
+int launch_accumulate(composite_engine *e, const void *d_ops, int n_ops, int64_t n_items, uint32_t *counter) {
+    ECK(e, cudaMemsetAsync(counter, 0, sizeof(uint32_t), e->stream));
+    engine_accumulate_kernel<<<persistent_grid(e, n_items), kThreads, 0, e->stream>>>(
+        static_cast<const OpDesc *>(d_ops), n_ops, (uint32_t)n_items, counter, e->d_flags);
+    ECK(e, cudaGetLastError());
+    return CPT_OK;
+}
+
+int launch_render(composite_engine *e, const void *d_ops, int n_ops, int64_t n_items, uint32_t *counter,
+                  const Lut &lut) {
+    ECK(e, cudaMemsetAsync(counter, 0, sizeof(uint32_t), e->stream));
+    engine_render_kernel<<<persistent_grid(e, n_items), kThreads, 0, e->stream>>>(
+        static_cast<const RenderDesc *>(d_ops), n_ops, (uint32_t)n_items, counter, lut);
+    ECK(e, cudaGetLastError());
+    return CPT_OK;
+}
+
+int clear_plane(composite_engine *e, int32_t p) {
+    PlaneRec &r = e->planes[p];
+    ECK(e, cudaMemsetAsync(r.data, 0, (size_t)r.pitch_px * r.height * sizeof(uint32_t), e->stream));
+    ECK(e, cudaMemsetAsync(e->d_flags + p, 0, sizeof(int), e->stream));
+    r.n = 0;
+    return CPT_OK;
+}
+
+int submit_internal(composite_engine *e, const composite_op *ops, int32_t n_ops) {
+    std::vector<OpDesc> descs;
+    std::vector<std::pair<int32_t, int64_t>> n_after;
+    int64_t items = 0;
+    int rc = plan_ops(e, ops, n_ops, &descs, &items, &n_after, false);
+    if (rc) return rc;
+    if (items > 0) {
+        void *d = nullptr;
+        rc = upload(e, e->up_ops, &e->up_i, descs.data(), descs.size() * sizeof(OpDesc), &d);
+        if (rc) return rc;
+        rc = launch_accumulate(e, d, (int)descs.size(), items, e->d_counter);
+        if (rc) return rc;
+    }
+    for (const auto &pn : n_after) e->planes[pn.first].n = pn.second;
+    return CPT_OK;
+}
+
+void destroy_graph(composite_engine *e) {
+    if (e->graph_exec) cudaGraphExecDestroy(e->graph_exec);
+    if (e->graph) cudaGraphDestroy(e->graph);
+    if (e->graph_ops) cudaFree(e->graph_ops);
+    if (e->graph_rops) cudaFree(e->graph_rops);
+    if (e->graph_counters) cudaFree(e->graph_counters);
+    e->graph_exec = nullptr;
+    e->graph = nullptr;
+    e->graph_ops = e->graph_rops = nullptr;
+    e->graph_counters = nullptr;
+    e->graph_n.clear();
+    e->graph_planes.clear();
+}
+
+void destroy_engine(composite_engine *e) {
+    destroy_graph(e);
+    for (PlaneRec &p : e->planes)
+        if (p.data) cudaFree(p.data);
+    for (Upload *ring : {e->up_ops, e->up_render})
+        for (int i = 0; i < 2; ++i) {
+            if (ring[i].d) cudaFree(ring[i].d);
+            if (ring[i].h) cudaFreeHost(ring[i].h);
+            if (ring[i].done) cudaEventDestroy(ring[i].done);
+        }
+    if (e->d_flags) cudaFree(e->d_flags);
+    if (e->h_flags) cudaFreeHost(e->h_flags);
+    if (e->d_counter) cudaFree(e->d_counter);
+    if (e->done_ev) cudaEventDestroy(e->done_ev);
+    if (e->own_stream && e->stream) cudaStreamDestroy(e->stream);
+    delete e;
+}
+
+}  // namespace
+
+extern "C" {
+
+int composite_engine_default_config(composite_engine_config *cfg) {
+    if (!cfg) return CPT_EINVAL;
+    memset(cfg, 0, sizeof *cfg);
+    cfg->slab_members = 128;
+    cfg->ctas_per_sm = 6;
+    return CPT_OK;
+}
+
+int composite_engine_begin(composite_engine **out, const composite_engine_config *cfg) {
+    g_engine_error.clear();
+    if (!out) return efail(nullptr, CPT_EINVAL, "out is NULL");
+    *out = nullptr;
+    composite_engine_config c;
+    composite_engine_default_config(&c);
+    if (cfg) {
+        c.cuda_stream = cfg->cuda_stream;
+        c.wait_timeout_ms = cfg->wait_timeout_ms;
+        if (cfg->slab_members) c.slab_members = cfg->slab_members;
+        if (cfg->ctas_per_sm) c.ctas_per_sm = cfg->ctas_per_sm;
+    }
+    if (c.slab_members < 1 || c.slab_members > kMaxSlab) return efail(nullptr, CPT_EINVAL, "slab_members not in 1..255");
+    if (c.ctas_per_sm < 1 || c.ctas_per_sm > 8) return efail(nullptr, CPT_EINVAL, "ctas_per_sm not in 1..8");
+    if (c.wait_timeout_ms < 0) return efail(nullptr, CPT_EINVAL, "negative timeout");
+    composite_engine *e = new composite_engine();
+    e->cfg = c;
+    auto setup = [&]() -> int {
+        ECK(e, cudaGetDevice(&e->device));
+        ECK(e, cudaDeviceGetAttribute(&e->caps.num_sms, cudaDevAttrMultiProcessorCount, e->device));
+        if (c.cuda_stream) {
+            e->stream = static_cast<cudaStream_t>(c.cuda_stream);
+        } else {
+            ECK(e, cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking));
+            e->own_stream = true;
+        }
+        ECK(e, cudaMalloc(&e->d_flags, kMaxPlanes * sizeof(int)));
+        ECK(e, cudaMemsetAsync(e->d_flags, 0, kMaxPlanes * sizeof(int), e->stream));
+        ECK(e, cudaHostAlloc(&e->h_flags, kMaxPlanes * sizeof(int), cudaHostAllocDefault));
+        ECK(e, cudaMalloc(&e->d_counter, sizeof(uint32_t)));
+        ECK(e, cudaEventCreateWithFlags(&e->done_ev, cudaEventDisableTiming));
+        for (Upload *ring : {e->up_ops, e->up_render})
+            for (int i = 0; i < 2; ++i) ECK(e, cudaEventCreateWithFlags(&ring[i].done, cudaEventDisableTiming));
+        e->default_lut = make_lut(nullptr);
+        return CPT_OK;
+    };
+    const int rc = setup();
+    if (rc) {
+        g_engine_error = e->err;
+        destroy_engine(e);
+        return rc;
+    }
+    *out = e;
+    return CPT_OK;
+}
+
+int composite_engine_add_plane(composite_engine *e, int32_t width, int32_t height, int32_t *plane_out) {
+    if (!e || !plane_out) return CPT_EINVAL;
+    e->err.clear();
+    if (width <= 0 || height <= 0) return efail(e, CPT_EINVAL, "plane %d x %d is empty", width, height);
+    if ((int)e->planes.size() >= kMaxPlanes) return efail(e, CPT_EINVAL, "at most %d planes", kMaxPlanes);
+    PlaneRec r;
+    r.width = width;
+    r.height = height;
+    r.pitch_px = ((int64_t)width + 15) / 16 * 16;
+    ECK(e, cudaMalloc(&r.data, (size_t)r.pitch_px * height * sizeof(uint32_t)));
+    r.alive = true;
+    e->planes.push_back(r);
+    const int32_t id = (int32_t)e->planes.size() - 1;
+    const int rc = clear_plane(e, id);
+    if (rc) return rc;
+    *plane_out = id;
+    return CPT_OK;
+}
+
+int composite_engine_free_plane(composite_engine *e, int32_t plane) {
+    if (!e) return CPT_EINVAL;
+    e->err.clear();
+    if (!plane_ok(e, plane)) return efail(e, CPT_EINVAL, "no plane %d", plane);
+    int rc = drain(e);
+    if (rc) return rc;
+    cudaFree(e->planes[plane].data);
+    e->planes[plane] = PlaneRec();
+    return CPT_OK;
+}
+
+int composite_engine_clear(composite_engine *e, int32_t plane) {
+    if (!e) return CPT_EINVAL;
+    e->err.clear();
+    if (!plane_ok(e, plane)) return efail(e, CPT_EINVAL, "no plane %d", plane);
+    return clear_plane(e, plane);
+}
+
+int composite_engine_submit(composite_engine *e, const composite_op *ops, int32_t n_ops) {
+    if (!e) return CPT_EINVAL;
+    e->err.clear();
+    return submit_internal(e, ops, n_ops);
+}
+
+int composite_engine_render(composite_engine *e, const composite_render_op *ops, int32_t n_ops,
+                            const uint8_t *lut_rgba) {
+    if (!e) return CPT_EINVAL;
+    e->err.clear();
+    std::vector<RenderDesc> descs;
+    int64_t items = 0;
+    int rc = plan_render(e, ops, n_ops, &descs, &items, nullptr);
+    if (rc || items == 0) return rc;
+    void *d = nullptr;
+    rc = upload(e, e->up_render, &e->rup_i, descs.data(), descs.size() * sizeof(RenderDesc), &d);
+    if (rc) return rc;
+    return launch_render(e, d, (int)descs.size(), items, e->d_counter, lut_rgba ? make_lut(lut_rgba) : e->default_lut);
+}
+
+int composite_engine_member_count(const composite_engine *e, int32_t plane, int64_t *n_out) {
+    if (!e || !n_out || !plane_ok(e, plane)) return CPT_EINVAL;
+    *n_out = e->planes[plane].n;
+    return CPT_OK;
+}
+
+int composite_engine_sync(composite_engine *e, int32_t *bad_plane_out) {
+    if (!e) return CPT_EINVAL;
+    e->err.clear();
+    if (bad_plane_out) *bad_plane_out = -1;
+    const size_t n = e->planes.size();
+    if (n) ECK(e, cudaMemcpyAsync(e->h_flags, e->d_flags, n * sizeof(int), cudaMemcpyDeviceToHost, e->stream));
+    int rc = drain(e);
+    if (rc) return rc;
+    for (size_t p = 0; p < n; ++p)
+        if (e->planes[p].alive && e->h_flags[p]) {
+            if (bad_plane_out) *bad_plane_out = (int32_t)p;
+            return efail(e, CPT_EUNDERFLOW, "plane %zu: a remove took away a member that was never added", p);
+        }
+    return CPT_OK;
+}
+
+int composite_engine_capture(composite_engine *e, const composite_op *ops, int32_t n_ops,
+                             const composite_render_op *rops, int32_t n_rops, const uint8_t *lut_rgba) {
+    if (!e) return CPT_EINVAL;
+    e->err.clear();
+    std::vector<OpDesc> descs;
+    std::vector<RenderDesc> rdescs;
+    std::vector<std::pair<int32_t, int64_t>> n_after;
+    int64_t items = 0, ritems = 0;
+    int rc = plan_ops(e, ops, n_ops, &descs, &items, &n_after, true);
+    if (rc) return rc;
+    rc = plan_render(e, rops, n_rops, &rdescs, &ritems, &n_after);
+    if (rc) return rc;
+    rc = drain(e);
+    if (rc) return rc;
+    destroy_graph(e);
+    ECK(e, cudaMalloc(&e->graph_counters, 2 * sizeof(uint32_t)));
+    if (!descs.empty()) {
+        ECK(e, cudaMalloc(&e->graph_ops, descs.size() * sizeof(OpDesc)));
+        ECK(e, cudaMemcpy(e->graph_ops, descs.data(), descs.size() * sizeof(OpDesc), cudaMemcpyHostToDevice));
+    }
+    if (!rdescs.empty()) {
+        ECK(e, cudaMalloc(&e->graph_rops, rdescs.size() * sizeof(RenderDesc)));
+        ECK(e, cudaMemcpy(e->graph_rops, rdescs.data(), rdescs.size() * sizeof(RenderDesc), cudaMemcpyHostToDevice));
+    }
+    const Lut lut = lut_rgba ? make_lut(lut_rgba) : e->default_lut;
+    ECK(e, cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal));
+    auto body = [&]() -> int {
+        for (const auto &pn : n_after) {
+            PlaneRec &r = e->planes[pn.first];
+            ECK(e, cudaMemsetAsync(r.data, 0, (size_t)r.pitch_px * r.height * sizeof(uint32_t), e->stream));
+            ECK(e, cudaMemsetAsync(e->d_flags + pn.first, 0, sizeof(int), e->stream));
+        }
+        if (items > 0) {
+            int r = launch_accumulate(e, e->graph_ops, (int)descs.size(), items, e->graph_counters);
+            if (r) return r;
+        }
+        if (ritems > 0) {
+            int r = launch_render(e, e->graph_rops, (int)rdescs.size(), ritems, e->graph_counters + 1, lut);
+            if (r) return r;
+        }
+        return CPT_OK;
+    };
+    const int brc = body();
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(e->stream, &g);
+    if (brc) {
+        if (g) cudaGraphDestroy(g);
+        return brc;
+    }
+    if (ec != cudaSuccess) return ecuda(e, ec, "cudaStreamEndCapture");
+    e->graph = g;
+    ECK(e, cudaGraphInstantiate(&e->graph_exec, e->graph, 0));
+    e->graph_n = n_after;
+    for (const auto &pn : n_after) e->graph_planes.push_back(pn.first);
+    for (int32_t i = 0; i < n_rops; ++i) e->graph_planes.push_back(rops[i].plane);
+    return CPT_OK;
+}
+
+int composite_engine_replay(composite_engine *e) {
+    if (!e) return CPT_EINVAL;
+    e->err.clear();
+    if (!e->graph_exec) return efail(e, CPT_ESTATE, "nothing captured");
+    for (const int32_t p : e->graph_planes)
+        if (!plane_ok(e, p)) return efail(e, CPT_ESTATE, "a captured plane was freed");
+    ECK(e, cudaGraphLaunch(e->graph_exec, e->stream));
+    for (const auto &pn : e->graph_n) e->planes[pn.first].n = pn.second;
+    return CPT_OK;
+}
+
+int composite_engine_tune(composite_engine *e, const composite_op *ops, int32_t n_ops, int32_t repeats,
+                          int32_t *slab_out, int32_t *ctas_out) {
+    if (!e) return CPT_EINVAL;
+    e->err.clear();
+    if (repeats < 1) return efail(e, CPT_EINVAL, "repeats < 1");
+    std::vector<OpDesc> descs;
+    std::vector<std::pair<int32_t, int64_t>> n_after;
+    int64_t items = 0;
+    int rc = plan_ops(e, ops, n_ops, &descs, &items, &n_after, true);
+    if (rc) return rc;
+    static const int slabs[] = {32, 64, 128, 255};
+    static const int ctas[] = {4, 6, 8};
+    cudaEvent_t a, b;
+    ECK(e, cudaEventCreate(&a));
+    ECK(e, cudaEventCreate(&b));
+    float best = 1e30f;
+    int best_slab = e->cfg.slab_members, best_ctas = e->cfg.ctas_per_sm;
+    auto run = [&]() -> int {
+        for (const auto &pn : n_after) {
+            int r = clear_plane(e, pn.first);
+            if (r) return r;
+        }
+        return submit_internal(e, ops, n_ops);
+    };
+    for (int s : slabs)
+        for (int c : ctas) {
+            e->cfg.slab_members = s;
+            e->cfg.ctas_per_sm = c;
+            float t_best = 1e30f;
+            for (int r = 0; r < repeats && rc == CPT_OK; ++r) {
+                if ((rc = run())) break;             // warm and measure alike: clear + submit
+                if (cudaEventRecord(a, e->stream) != cudaSuccess) { rc = CPT_ECUDA; break; }
+                if ((rc = run())) break;
+                if (cudaEventRecord(b, e->stream) != cudaSuccess) { rc = CPT_ECUDA; break; }
+                if ((rc = ewait(e, b))) break;
+                float ms = 0;
+                cudaEventElapsedTime(&ms, a, b);
+                t_best = std::min(t_best, ms);
+            }
+            if (rc) break;
+            if (t_best < best) {
+                best = t_best;
+                best_slab = s;
+                best_ctas = c;
+            }
+        }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    e->cfg.slab_members = best_slab;
+    e->cfg.ctas_per_sm = best_ctas;
+    if (rc) return rc;
+    rc = run();
+    if (rc) return rc;
+    if (slab_out) *slab_out = best_slab;
+    if (ctas_out) *ctas_out = best_ctas;
+    return CPT_OK;
+}
+
+int composite_engine_get_tuning(const composite_engine *e, int32_t *slab_out, int32_t *ctas_out) {
+    if (!e) return CPT_EINVAL;
+    if (slab_out) *slab_out = e->cfg.slab_members;
+    if (ctas_out) *ctas_out = e->cfg.ctas_per_sm;
+    return CPT_OK;
+}
+
+int composite_engine_end(composite_engine *e) {
+    if (!e) return CPT_OK;
+    const int rc = drain(e);
+    destroy_engine(e);
+    return rc;
+}
+
+const char *composite_engine_last_error(const composite_engine *e) {
+    return e ? e->err.c_str() : g_engine_error.c_str();
+}
+
+}  // extern "C"

@@ -69,3 +69,20 @@ def test_begin_without_gpu_fails_loudly(lib):
     with pytest.raises(binding.CompositeError) as e:
         binding.composite_begin(16, 16)
     assert e.value.code in (binding.CPT_ECUDA, binding.CPT_ENOMEM)
+
+
+def test_engine_defaults_and_no_gpu(lib):
+    eng_lib = binding._engine_lib()
+    cfg = binding.EngineConfig()
+    assert eng_lib.composite_engine_default_config(ctypes.byref(cfg)) == binding.CPT_OK
+    assert (cfg.slab_members, cfg.ctas_per_sm) == (128, 6)
+    assert ctypes.sizeof(binding.Op) == 40 and ctypes.sizeof(binding.RenderOp) == 32
+    assert eng_lib.composite_engine_end(None) == binding.CPT_OK
+    bad = binding.EngineConfig()
+    bad.slab_members = 256
+    h = ctypes.c_void_p()
+    assert eng_lib.composite_engine_begin(ctypes.byref(h), ctypes.byref(bad)) == binding.CPT_EINVAL
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        with pytest.raises(binding.CompositeError):
+            binding.Engine()

@@ -1,0 +1,154 @@
+"""The batched engine (include/composite_engine.h) against the CPU oracle:
+many planes of different shapes in one persistent launch, member index lists,
+add/remove, underflow per plane, CUDA-graph capture/replay and the autotuner."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+from paper_2104_14667_gb300 import binding  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def padded(m: np.ndarray):
+    """Device copy of uint8[n, H, W] with rows padded to 16 bytes."""
+    n, h, w = m.shape
+    pitch = (w + 15) // 16 * 16
+    buf = torch.zeros((n, h, pitch), dtype=torch.uint8, device="cuda")
+    buf[:, :, :w] = torch.from_numpy(m).cuda()
+    return buf[:, :, :w]
+
+
+def outputs(w, h):
+    return (torch.empty((h, w), dtype=torch.int32, device="cuda"),
+            torch.empty((h, w), dtype=torch.uint8, device="cuda"),
+            torch.empty((h, w, 4), dtype=torch.uint8, device="cuda"))
+
+
+def check(outs, masks_np, lut=None):
+    counts, bucket, rgba = outs
+    c = oracle.count(masks_np)
+    b = oracle.bucket(c, masks_np.shape[0])
+    np.testing.assert_array_equal(counts.cpu().numpy().astype(np.int64), c)
+    np.testing.assert_array_equal(bucket.cpu().numpy(), b)
+    np.testing.assert_array_equal(rgba.cpu().numpy(), oracle.rgba(b, lut))
+
+
+SHAPES = [(1024, 1024, 16), (13, 7, 5), (100, 37, 40), (257, 131, 300), (4096, 3, 9), (1, 1, 2), (48, 600, 1)]
+
+
+def test_many_planes_one_launch():
+    with binding.Engine() as eng:
+        data, ops, rops, outs = [], [], [], []
+        for i, (w, h, n) in enumerate(SHAPES):
+            m = synth.scramble_nonzero(synth.random_masks(50 + i, n, h, w, density=0.3 + 0.05 * i), i)
+            p = eng.add_plane(w, h)
+            dev = padded(m)
+            o = outputs(w, h)
+            data.append((m, dev))
+            outs.append(o)
+            ops.append(eng.op(p, dev))
+            rops.append(eng.render_op(p, *o))
+        eng.submit(ops)
+        eng.render(rops)
+        eng.sync()
+        for (m, _), o, (w, h, n), p in zip(data, outs, SHAPES, range(len(SHAPES))):
+            assert eng.member_count(p) == n
+            check(o, m)
+
+
+def test_index_lists_add_and_remove():
+    w, h, total = 300, 70, 500
+    ens = synth.scramble_nonzero(synth.random_masks(60, total, h, w, density=0.2), 60)
+    dev = padded(ens)
+    rng = np.random.default_rng(1)
+    a = rng.choice(total, 300, replace=False).astype(np.int32)
+    b = rng.choice(total, 120, replace=False).astype(np.int32)
+    drop = a[:170]
+    with binding.Engine(slab_members=64) as eng:
+        p = eng.add_plane(w, h)
+        q = eng.add_plane(w, h)
+        ia, ib, idrop = (torch.from_numpy(x).cuda() for x in (a, b, drop))
+        eng.submit([eng.op(p, dev, 1, ia), eng.op(q, dev, 1, ib), eng.op(p, dev, 1, ib)])
+        eng.submit([eng.op(p, dev, -1, idrop)])
+        op_, oq = outputs(w, h), outputs(w, h)
+        eng.render([eng.render_op(p, *op_), eng.render_op(q, *oq)])
+        eng.sync()
+        keep = np.concatenate([a[170:], b])
+        check(op_, ens[keep])
+        check(oq, ens[b])
+        assert eng.member_count(p) == len(keep)
+
+
+def test_underflow_is_reported_per_plane_and_cleared():
+    w, h = 64, 20
+    m = synth.random_masks(61, 2, h, w, density=0.5)
+    dev = padded(m)
+    with binding.Engine() as eng:
+        good = eng.add_plane(w, h)
+        bad = eng.add_plane(w, h)
+        eng.submit([eng.op(good, dev), eng.op(bad, dev[:1])])
+        eng.submit([eng.op(bad, dev[1:], -1)])
+        with pytest.raises(binding.CompositeError) as e:
+            eng.sync()
+        assert e.value.code == binding.CPT_EUNDERFLOW and e.value.plane == bad
+        eng.clear(bad)
+        eng.submit([eng.op(bad, dev)])
+        o = outputs(w, h)
+        eng.render([eng.render_op(bad, *o)])
+        eng.sync()
+        check(o, m)
+
+
+def test_capture_replay_matches_direct_and_repeats():
+    shapes = [(512, 64, 37), (77, 45, 260), (16, 16, 3)]
+    with binding.Engine() as eng:
+        items = []
+        for i, (w, h, n) in enumerate(shapes):
+            m = synth.random_masks(70 + i, n, h, w, density=0.4)
+            items.append((m, padded(m), eng.add_plane(w, h), outputs(w, h)))
+        ops = [eng.op(p, dev) for _, dev, p, _ in items]
+        rops = [eng.render_op(p, *o) for _, _, p, o in items]
+        eng.capture(ops, rops)
+        for _ in range(3):
+            eng.replay()
+            eng.sync()
+            for m, _, p, o in items:
+                check(o, m)
+                assert eng.member_count(p) == m.shape[0]
+
+
+def test_tuner_picks_a_candidate_and_keeps_results_exact():
+    shapes = [(1024, 256, 300), (130, 90, 40)]
+    with binding.Engine() as eng:
+        items = []
+        for i, (w, h, n) in enumerate(shapes):
+            m = synth.random_masks(80 + i, n, h, w, density=0.25)
+            items.append((m, padded(m), eng.add_plane(w, h), outputs(w, h)))
+        slab, ctas = eng.tune([eng.op(p, dev) for _, dev, p, _ in items], repeats=1)
+        assert slab in (32, 64, 128, 255) and ctas in (4, 6, 8)
+        assert eng.tuning() == (slab, ctas)
+        eng.render([eng.render_op(p, *o) for _, _, p, o in items])
+        eng.sync()
+        for m, _, p, o in items:
+            check(o, m)
+
+
+def test_invalid_ops_rejected_before_anything_runs():
+    with binding.Engine() as eng:
+        p = eng.add_plane(32, 8)
+        dev = padded(synth.random_masks(90, 2, 8, 32))
+        with pytest.raises(binding.CompositeError) as e:
+            eng.submit([eng.op(p + 7, dev)])
+        assert e.value.code == binding.CPT_EINVAL
+        with pytest.raises(binding.CompositeError) as e:
+            eng.submit([eng.op(p, dev, -1)])
+        assert e.value.code == binding.CPT_EINVAL
+        odd = torch.zeros((2, 8, 33), dtype=torch.uint8, device="cuda")[:, :, 1:]
+        with pytest.raises(binding.CompositeError) as e:
+            eng.submit([eng.op(p, odd)])
+        assert e.value.code == binding.CPT_EINVAL
+        assert eng.member_count(p) == 0

@@ -59,7 +59,7 @@ def parse_args():
                    help="target CPU time of the oracle baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--sweep", choices=["readpath", "layout", "streaming", "tiny"], default=None,
+    p.add_argument("--sweep", choices=["readpath", "layout", "streaming", "tiny", "batched"], default=None,
                    help="print one JSON line per point of a workload sweep instead of the bench line")
     p.add_argument("--e2e-mode", choices=["staged", "host_read"], default="staged",
                    help="which host-to-device path the e2e value reports (both are measured)")
@@ -585,6 +585,79 @@ def sweep_streaming(args, torch, binding, device, stream, sides=None, counts=Non
     pools.clear()
 
 
+def sweep_batched(args, torch, binding, device, stream):
+    """64 composite requests of uneven member counts and raster shapes,
+    device resident: 64 sequential plain runs (one context each: clear, add,
+    render) against the engine's captured graph (clear every plane, one
+    persistent accumulate launch, one persistent render launch), after the
+    engine's autotuner picked slab depth and CTAs per SM."""
+    import synth
+    reqs = synth.batched_requests(4, 64)
+    terrains, data = {}, []
+    for r, (w, h, n) in enumerate(reqs):
+        if (w, h) not in terrains:
+            t = synth.terrain(4, w, h)
+            terrains[(w, h)] = (t, np.sort(t, axis=None), torch.from_numpy(t).to(device))
+        t, srt, tdev = terrains[(w, h)]
+        ens = synth.ensemble_from_terrain(4, t, n, member_offset=r * 4096, flat_sorted=srt)
+        dev = torch.empty((n, h, w), dtype=torch.uint8, device=device)
+        synth.fill_masks_torch(ens, dev, terrain_t=tdev)
+        data.append(dev)
+    terrains.clear()
+    member_px = sum(w * h * n for w, h, n in reqs)
+    out_plain = [(torch.empty((h, w), dtype=torch.uint8, device=device),
+                  torch.empty((h, w, 4), dtype=torch.uint8, device=device)) for w, h, _ in reqs]
+    out_batch = [(torch.empty((h, w), dtype=torch.uint8, device=device),
+                  torch.empty((h, w, 4), dtype=torch.uint8, device=device)) for w, h, _ in reqs]
+    ctxs = [binding.Composite(w, h, staging_buffers=1, chunk_members=1, stream=stream.cuda_stream)
+            for w, h, _ in reqs]
+
+    def plain_all():
+        for ctx, dev, (b, c) in zip(ctxs, data, out_plain):
+            ctx.clear()
+            ctx.add(dev)
+            ctx.render(bucket_out=b, rgba_out=c)
+
+    ms_plain = _timed(torch, stream, plain_all, args.steps, args.warmup)
+    for ctx in ctxs:
+        ctx.sync()
+        ctx.close()
+    eng = binding.Engine(stream=stream.cuda_stream)
+    planes = [eng.add_plane(w, h) for w, h, _ in reqs]
+    ops = [eng.op(p, dev) for p, dev in zip(planes, data)]
+    rops = [eng.render_op(p, None, b, c) for p, (b, c) in zip(planes, out_batch)]
+    t0 = time.perf_counter()
+    slab, ctas = eng.tune(ops, repeats=2)
+    tune_s = time.perf_counter() - t0
+    eng.capture(ops, rops)
+    ms_graph = _timed(torch, stream, eng.replay, args.steps, args.warmup)
+    eng.sync()
+    same = all(torch.equal(a, b) and torch.equal(c, d) for (a, c), (b, d) in zip(out_plain, out_batch))
+
+    def direct():
+        for p in planes:
+            eng.clear(p)
+        eng.submit(ops)
+        eng.render(rops)
+
+    ms_direct = _timed(torch, stream, direct, args.steps, args.warmup)
+    eng.sync()
+    eng.close()
+    peaks, _ = measured_peaks()
+    hbm = lambda ms: member_px / (ms * 1e-3) / 1e9
+    print(json.dumps({
+        "sweep": "batched", "requests": len(reqs), "member_px": member_px,
+        "members_total": sum(n for _, _, n in reqs),
+        "plain_sequential_ms": ms_plain, "batched_graph_ms": ms_graph, "batched_no_graph_ms": ms_direct,
+        "plain_composites_per_s": len(reqs) / (ms_plain * 1e-3),
+        "batched_composites_per_s": len(reqs) / (ms_graph * 1e-3),
+        "speedup": ms_plain / ms_graph, "plain_member_px_per_s": member_px / (ms_plain * 1e-3),
+        "batched_member_px_per_s": member_px / (ms_graph * 1e-3),
+        "batched_mask_gbs": hbm(ms_graph), "batched_frac_of_hbm": hbm(ms_graph) / peaks["hbm_gbs"],
+        "tuned_slab_members": slab, "tuned_ctas_per_sm": ctas, "tune_seconds": tune_s,
+        "outputs_identical": bool(same)}), flush=True)
+
+
 def run_sweep(args):
     import torch
     from paper_2104_14667_gb300 import binding
@@ -602,6 +675,8 @@ def run_sweep(args):
     elif args.sweep == "streaming":
         sweep_streaming(args, torch, binding, device, stream, chunks=[1, 2, 4, 8, 16, 64, 128],
                         stagings=[1, 3, 4])
+    elif args.sweep == "batched":
+        sweep_batched(args, torch, binding, device, stream)
     elif args.sweep == "tiny":
         sweep_streaming(args, torch, binding, device, stream,
                         plan=[(1024, 16, c, k) for c in (16, 1, 2, 4, 8) for k in (2, 1)])

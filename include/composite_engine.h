@@ -7,7 +7,7 @@
  * The engine holds composite planes in device memory (uint32 counts, one per
  * plane) and applies "ops" to them: add or remove a set of device-resident
  * uint8 masks to one plane.  All ops of one submit call run in ONE persistent
- * kernel launch whose CTAs pull work items (op, member slab, tile of 256
+ * kernel launch whose warps pull work items (op, member slab, chunk of
  * 16-pixel groups) from a device counter, so small and large composites share
  * the GPU without one launch per composite; one render call likewise renders
  * many planes in one launch.  A submit + render sequence can be captured in a
@@ -38,11 +38,18 @@ extern "C" {
 
 typedef struct composite_engine composite_engine;
 
+/* How the accumulate launch hands work items to warps. */
+enum {
+    CPT_SCHEDULE_PERSISTENT = 0,  /* num_SMs x ctas_per_sm CTAs; warps claim items from a counter */
+    CPT_SCHEDULE_GRID = 1         /* one CTA per 8 items; the hardware schedules the CTAs        */
+};
+
 typedef struct composite_engine_config {
     void *cuda_stream;        /* cudaStream_t for all engine work, NULL = engine-owned */
     int32_t slab_members;     /* members per work item, 1..255; 0 = 128               */
-    int32_t ctas_per_sm;      /* persistent CTAs of 256 threads per SM, 1..8; 0 = 6   */
+    int32_t ctas_per_sm;      /* persistent CTAs of 256 threads per SM, 1..8; 0 = 5   */
     int64_t wait_timeout_ms;  /* bound on host waits; 0 = 10000                        */
+    int32_t schedule;         /* CPT_SCHEDULE_*; default CPT_SCHEDULE_PERSISTENT       */
 } composite_engine_config;
 
 /* One add or remove of n_members masks to one plane.  Member i of the op is
@@ -111,14 +118,15 @@ int composite_engine_capture(composite_engine *eng, const composite_op *ops, int
 int composite_engine_replay(composite_engine *eng);
 
 /* Autotuner: times "clear the ops' planes + submit ops" for every candidate
- * (slab_members in {32, 64, 128, 255} x ctas_per_sm in {4, 6, 8}), `repeats`
- * runs each, keeps the fastest pair as the engine's configuration and
- * reports it (either pointer may be NULL).  The planes end holding the
- * result of the ops applied once to cleared planes. */
+ * (slab_members in {32, 64, 128, 255} x schedule {grid, persistent with
+ * ctas_per_sm 3, 4, 5}), `repeats` runs each, keeps the fastest as the
+ * engine's configuration and reports it (either pointer may be NULL;
+ * *ctas_per_sm_out = 0 means the grid schedule won).  The planes end holding
+ * the result of the ops applied once to cleared planes. */
 int composite_engine_tune(composite_engine *eng, const composite_op *ops, int32_t n_ops, int32_t repeats,
                           int32_t *slab_out, int32_t *ctas_per_sm_out);
 
-/* Current (slab_members, ctas_per_sm). */
+/* Current (slab_members, ctas_per_sm); ctas_per_sm 0 = grid schedule. */
 int composite_engine_get_tuning(const composite_engine *eng, int32_t *slab_out, int32_t *ctas_per_sm_out);
 
 /* Waits (bounded) and frees everything.  NULL is accepted. */

@@ -363,7 +363,11 @@ class EngineConfig(ctypes.Structure):
         ("slab_members", ctypes.c_int32),
         ("ctas_per_sm", ctypes.c_int32),
         ("wait_timeout_ms", ctypes.c_int64),
+        ("schedule", ctypes.c_int32),
     ]
+
+
+CPT_SCHEDULE_PERSISTENT, CPT_SCHEDULE_GRID = 0, 1
 
 
 class Op(ctypes.Structure):
@@ -439,7 +443,7 @@ class Engine:
     """Many composite planes on one GPU; ops on all of them run in one
     persistent launch (include/composite_engine.h)."""
 
-    def __init__(self, stream=None, slab_members=0, ctas_per_sm=0, wait_timeout_ms=0):
+    def __init__(self, stream=None, slab_members=0, ctas_per_sm=0, wait_timeout_ms=0, schedule="persistent"):
         self.lib = _engine_lib()
         cfg = EngineConfig()
         self.lib.composite_engine_default_config(ctypes.byref(cfg))
@@ -447,6 +451,7 @@ class Engine:
         cfg.slab_members = slab_members
         cfg.ctas_per_sm = ctas_per_sm
         cfg.wait_timeout_ms = wait_timeout_ms
+        cfg.schedule = {"persistent": CPT_SCHEDULE_PERSISTENT, "grid": CPT_SCHEDULE_GRID}[schedule]
         h = ctypes.c_void_p()
         _echeck(self.lib, None, self.lib.composite_engine_begin(ctypes.byref(h), ctypes.byref(cfg)))
         self.h = h

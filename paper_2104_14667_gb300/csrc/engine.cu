@@ -1,17 +1,18 @@
 // engine.cu -- the batched composite engine of include/composite_engine.h.
 //
 // A submit turns every op (add/remove a member set to one plane) into work
-// items (op, member slab, tile of 256 16-pixel groups), numbered op after op,
-// slab after slab, tile after tile.  One persistent launch of
-// num_SMs x ctas_per_sm CTAs pulls item numbers from a device counter; the
-// op owning an item is found by binary search over the ops' first items.
-// Each thread of the CTA folds its group of one slab's members into packed
-// byte counters (member i of the op read at base + idx(i) * stride, the
-// slab's indices staged in shared memory) and adds the counts into the
-// op's uint32 plane with L2 atomics.  The render launch works the same way
-// over (plane, tile) items.  Consecutive items are neighbouring tiles of the
-// same slab, so concurrently running CTAs read neighbouring bytes of the
-// same members.
+// items (op, member slab, chunk of 16-pixel groups), numbered op after op,
+// slab after slab, chunk after chunk.  One persistent launch of
+// num_SMs x ctas_per_sm CTAs runs warps that each pull item numbers from a
+// device counter; the op owning an item is found by binary search over the
+// ops' first items.  Each lane folds its groups of one slab's members into
+// packed byte counters (member i of the op read at base + idx(i) * stride,
+// the slab's indices staged in the warp's shared memory) and adds the counts
+// into the op's uint32 plane: with L2 atomics, or with a plain read-modify-
+// write when the op is alone on its plane and has a single slab.  The render
+// launch works the same way over (plane, tile) items, per CTA.  Consecutive
+// items are neighbouring chunks of the same slab, so concurrently running
+// warps read neighbouring bytes of the same members.
 #include <algorithm>
 #include <chrono>
 #include <cstdarg>
@@ -49,7 +50,8 @@ struct OpDesc {
     int32_t slab;
     int32_t sign;
     int32_t plane_id;
-    int32_t pad;
+    int32_t groups_per_thread;   // groups per lane per item (short slabs take several)
+    int32_t exclusive;           // the only op on its plane, one slab: plain read-modify-write
 };
 
 struct RenderDesc {
@@ -68,6 +70,8 @@ struct RenderDesc {
     int32_t pad;
 };
 
+constexpr int kSmemStarts = 2048;      // ops whose first items fit in shared memory
+
 template <typename Desc>
 __device__ __forceinline__ int find_desc(const Desc *d, int n, int64_t item) {
     int lo = 0, hi = n - 1;
@@ -81,72 +85,142 @@ __device__ __forceinline__ int find_desc(const Desc *d, int n, int64_t item) {
     return lo;
 }
 
-__global__ void __launch_bounds__(kThreads, 6)
-engine_accumulate_kernel(const OpDesc *ops, int n_ops, uint32_t n_items, uint32_t *counter, int *flags) {
-    __shared__ uint32_t s_item;
-    __shared__ int32_t s_index[kMaxSlab];
-    for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1u);
-        __syncthreads();
-        const uint32_t item = s_item;
-        if (item >= n_items) break;
-        const OpDesc &op = ops[find_desc(ops, n_ops, item)];
-        const uint32_t local = item - (uint32_t)op.item_start;
-        const int sl = (int)(local / (uint32_t)op.tiles);
-        const int tile = (int)(local - (uint32_t)sl * op.tiles);
-        const int m0 = sl * op.slab;
-        const int cnt = min(op.n - m0, op.slab);
-        if (op.index)
-            for (int i = threadIdx.x; i < cnt; i += kThreads) s_index[i] = op.index[m0 + i];
-        __syncthreads();
-        const int64_t g = (int64_t)tile * kThreads + threadIdx.x;
-        if (g < (int64_t)op.groups_per_row * op.height) {
-            const int y = (int)(g / op.groups_per_row);
-            const int x0 = (int)(g - (int64_t)y * op.groups_per_row) * 16;
-            const int valid = min(16, op.width - x0);
-            const uint8_t *row = op.base + (int64_t)y * op.pitch + x0;
-            uint32_t k[4] = {0u, 0u, 0u, 0u};
-            if (valid == 16) {
-#pragma unroll 8
-                for (int i = 0; i < cnt; ++i) {
-                    const int64_t mi = op.index ? s_index[i] : (int64_t)(m0 + i);
-                    const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(row + mi * op.stride));
-                    k[0] += cpt::nonzero_bytes(v.x);
-                    k[1] += cpt::nonzero_bytes(v.y);
-                    k[2] += cpt::nonzero_bytes(v.z);
-                    k[3] += cpt::nonzero_bytes(v.w);
-                }
-            } else {
-                for (int i = 0; i < cnt; ++i) {
-                    const int64_t mi = op.index ? s_index[i] : (int64_t)(m0 + i);
-                    const uint8_t *q = row + mi * op.stride;
-#pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if (j < valid) k[j / 4] += (uint32_t)(q[j] != 0) << (8 * (j % 4));
-                }
-            }
-            uint32_t wide[16];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) wide[j] = 0;
-            cpt::widen16(wide, k[0], k[1], k[2], k[3]);
-            cpt::atomic_count_group<uint32_t>(op.plane + (int64_t)y * op.plane_pitch + x0, wide, op.sign,
-                                              flags + op.plane_id);
-        }
-        __syncthreads();
+// The op owning `item`: binary search over the first items, in shared memory
+// when the op list is short enough, else over the descriptors themselves.
+template <typename Desc>
+__device__ __forceinline__ int find_op(const Desc *d, int n, const uint32_t *starts, uint32_t item) {
+    if (n > kSmemStarts) return find_desc(d, n, item);
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (starts[mid] <= item)
+            lo = mid;
+        else
+            hi = mid - 1;
     }
+    return lo;
+}
+
+template <typename Desc>
+__device__ __forceinline__ void load_starts(const Desc *d, int n, uint32_t *starts) {
+    if (n <= kSmemStarts)
+        for (int i = threadIdx.x; i < n; i += blockDim.x) starts[i] = (uint32_t)d[i].item_start;
+}
+
+// One warp item: (op, member slab, chunk of 32 x groups_per_thread groups).
+// The slab's member indices are staged in the warp's slice of shared memory.
+__device__ __forceinline__ void process_item(const OpDesc &op, uint32_t item, int lane, int32_t *index,
+                                             int *flags) {
+    const uint32_t local = item - (uint32_t)op.item_start;
+    const int sl = (int)(local / (uint32_t)op.tiles);
+    const int chunk = (int)(local - (uint32_t)sl * op.tiles);
+    const int m0 = sl * op.slab;
+    const int cnt = min(op.n - m0, op.slab);
+    const bool gather = op.index != nullptr;
+    if (gather) {
+        for (int i = lane; i < cnt; i += 32) index[i] = op.index[m0 + i];
+        __syncwarp();
+    }
+    const int64_t groups = (int64_t)op.groups_per_row * op.height;
+    const int gpt = op.groups_per_thread;
+    for (int j = 0; j < gpt; ++j) {
+        const int64_t g = ((int64_t)chunk * gpt + j) * 32 + lane;
+        if (g >= groups) break;
+        const int y = (int)(g / op.groups_per_row);
+        const int x0 = (int)(g - (int64_t)y * op.groups_per_row) * 16;
+        const int valid = min(16, op.width - x0);
+        const uint8_t *row = op.base + (int64_t)y * op.pitch + x0;
+        const int64_t stride = op.stride;
+        uint32_t k[4] = {0u, 0u, 0u, 0u};
+        if (valid == 16 && !gather) {
+            const uint8_t *q = row + (int64_t)m0 * stride;
+#pragma unroll 8
+            for (int i = 0; i < cnt; ++i) {
+                const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(q));
+                q += stride;
+                k[0] += cpt::nonzero_bytes(v.x);
+                k[1] += cpt::nonzero_bytes(v.y);
+                k[2] += cpt::nonzero_bytes(v.z);
+                k[3] += cpt::nonzero_bytes(v.w);
+            }
+        } else if (valid == 16) {
+#pragma unroll 8
+            for (int i = 0; i < cnt; ++i) {
+                const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(row + (int64_t)index[i] * stride));
+                k[0] += cpt::nonzero_bytes(v.x);
+                k[1] += cpt::nonzero_bytes(v.y);
+                k[2] += cpt::nonzero_bytes(v.z);
+                k[3] += cpt::nonzero_bytes(v.w);
+            }
+        } else {
+            for (int i = 0; i < cnt; ++i) {
+                const int64_t mi = gather ? index[i] : (int64_t)(m0 + i);
+                const uint8_t *q = row + mi * stride;
+#pragma unroll
+                for (int jj = 0; jj < 16; ++jj)
+                    if (jj < valid) k[jj / 4] += (uint32_t)(q[jj] != 0) << (8 * (jj % 4));
+            }
+        }
+        uint32_t wide[16];
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) wide[jj] = 0;
+        cpt::widen16(wide, k[0], k[1], k[2], k[3]);
+        uint32_t *dst = op.plane + (int64_t)y * op.plane_pitch + x0;
+        if (op.exclusive)
+            cpt::apply_count_group<uint32_t>(dst, valid, wide, op.sign, flags + op.plane_id);
+        else
+            cpt::atomic_count_group<uint32_t>(dst, wide, op.sign, flags + op.plane_id);
+    }
+    if (gather) __syncwarp();
+}
+
+// Persistent schedule: warps claim items from the counter one ahead (lane 0
+// asks for the next while the warp works on the current one), so warps
+// never wait for one another and uneven items balance across the GPU.
+__global__ void __launch_bounds__(kThreads, 5)
+engine_accumulate_kernel(const OpDesc *ops, int n_ops, uint32_t n_items, uint32_t *counter, int *flags) {
+    __shared__ int32_t s_index[kThreads / 32][kMaxSlab + 1];
+    __shared__ uint32_t s_starts[kSmemStarts];
+    load_starts(ops, n_ops, s_starts);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    int32_t *index = s_index[threadIdx.x >> 5];
+    uint32_t next = 0;
+    if (lane == 0) next = atomicAdd(counter, 1u);
+    next = __shfl_sync(0xFFFFFFFFu, next, 0);
+    while (next < n_items) {
+        const uint32_t item = next;
+        if (lane == 0) next = atomicAdd(counter, 1u);
+        process_item(ops[find_op(ops, n_ops, s_starts, item)], item, lane, index, flags);
+        next = __shfl_sync(0xFFFFFFFFu, next, 0);
+    }
+}
+
+// Grid schedule: one launch of ceil(items / 8) CTAs, warp w of CTA b takes
+// item 8b + w; the hardware block scheduler balances the CTAs.
+__global__ void __launch_bounds__(kThreads)
+engine_accumulate_grid_kernel(const OpDesc *ops, int n_ops, uint32_t n_items, int *flags) {
+    __shared__ int32_t s_index[kThreads / 32][kMaxSlab + 1];
+    const int lane = threadIdx.x & 31;
+    const uint32_t item = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+    if (item >= n_items) return;
+    process_item(ops[find_desc(ops, n_ops, item)], item, lane, s_index[threadIdx.x >> 5], flags);
 }
 
 __global__ void __launch_bounds__(kThreads)
 engine_render_kernel(const RenderDesc *ops, int n_ops, uint32_t n_items, uint32_t *counter, Lut lut) {
     __shared__ uint32_t table[256];
-    __shared__ uint32_t s_item;
+    __shared__ uint32_t s_item[2];
+    __shared__ uint32_t s_starts[kSmemStarts];
     for (int i = threadIdx.x; i < 256; i += kThreads) table[i] = lut.rgba[i];
-    for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1u);
+    load_starts(ops, n_ops, s_starts);
+    if (threadIdx.x == 0) s_item[0] = atomicAdd(counter, 1u);
+    for (int turn = 0;; turn ^= 1) {
         __syncthreads();
-        const uint32_t item = s_item;
+        const uint32_t item = s_item[turn];
         if (item >= n_items) break;
-        const RenderDesc op = ops[find_desc(ops, n_ops, item)];
+        if (threadIdx.x == 0) s_item[turn ^ 1] = atomicAdd(counter, 1u);
+        const RenderDesc &op = ops[find_op(ops, n_ops, s_starts, item)];
         const int64_t g = (int64_t)(item - (uint32_t)op.item_start) * kThreads + threadIdx.x;
         if (g < (int64_t)op.groups_per_row * op.height) {
             const int y = (int)(g / op.groups_per_row);
@@ -194,7 +268,6 @@ engine_render_kernel(const RenderDesc *ops, int n_ops, uint32_t n_items, uint32_
                 }
             }
         }
-        __syncthreads();
     }
 }
 
@@ -372,14 +445,25 @@ int plan_ops(composite_engine *e, const composite_op *ops, int32_t n_ops, std::v
         d.height = p.height;
         d.groups_per_row = (int32_t)(p.pitch_px / 16);
         const int64_t groups = (int64_t)d.groups_per_row * p.height;
-        d.tiles = (int32_t)((groups + kThreads - 1) / kThreads);
+        // a warp item: 32 lanes x groups_per_thread groups, so that a lane
+        // streams about 512 member-groups per item whatever the slab length
+        const int first_slab = std::min(o.n_members, slab);
+        d.groups_per_thread = std::max(1, 512 / first_slab);
+        const int64_t per_item = 32ll * d.groups_per_thread;
+        d.tiles = (int32_t)((groups + per_item - 1) / per_item);
         d.slab = slab;
         d.sign = o.sign;
         d.plane_id = o.plane;
+        d.exclusive = 0;
         const int64_t slabs = (o.n_members + slab - 1) / slab;
         items += slabs * d.tiles;
         descs->push_back(d);
     }
+    // An op that is alone on its plane in this submit and has a single slab
+    // owns every pixel it touches: no atomics needed.
+    std::vector<int> ops_on_plane(e->planes.size(), 0);
+    for (const OpDesc &d : *descs) ++ops_on_plane[d.plane_id];
+    for (OpDesc &d : *descs) d.exclusive = (ops_on_plane[d.plane_id] == 1 && d.n <= d.slab) ? 1 : 0;
     if (items >= (int64_t)1 << 31) return efail(e, CPT_EINVAL, "too many work items in one submit");
     for (size_t p = 0; p < n.size(); ++p)
         if (n[p] >= 0) n_after->push_back({(int32_t)p, n[p]});
@@ -432,9 +516,17 @@ unsigned persistent_grid(const composite_engine *e, int64_t items) {
 }
 
 int launch_accumulate(composite_engine *e, const void *d_ops, int n_ops, int64_t n_items, uint32_t *counter) {
-    ECK(e, cudaMemsetAsync(counter, 0, sizeof(uint32_t), e->stream));
-    engine_accumulate_kernel<<<persistent_grid(e, n_items), kThreads, 0, e->stream>>>(
-        static_cast<const OpDesc *>(d_ops), n_ops, (uint32_t)n_items, counter, e->d_flags);
+    if (e->cfg.schedule == CPT_SCHEDULE_GRID) {
+        const int64_t ctas = (n_items + kThreads / 32 - 1) / (kThreads / 32);
+        engine_accumulate_grid_kernel<<<(unsigned)ctas, kThreads, 0, e->stream>>>(
+            static_cast<const OpDesc *>(d_ops), n_ops, (uint32_t)n_items, e->d_flags);
+    } else {
+        ECK(e, cudaMemsetAsync(counter, 0, sizeof(uint32_t), e->stream));
+        const int64_t warps_needed = (n_items + kThreads / 32 - 1) / (kThreads / 32);
+        engine_accumulate_kernel<<<(unsigned)std::min<int64_t>(persistent_grid(e, n_items), warps_needed),
+                                   kThreads, 0, e->stream>>>(static_cast<const OpDesc *>(d_ops), n_ops,
+                                                             (uint32_t)n_items, counter, e->d_flags);
+    }
     ECK(e, cudaGetLastError());
     return CPT_OK;
 }
@@ -513,7 +605,8 @@ int composite_engine_default_config(composite_engine_config *cfg) {
     if (!cfg) return CPT_EINVAL;
     memset(cfg, 0, sizeof *cfg);
     cfg->slab_members = 128;
-    cfg->ctas_per_sm = 6;
+    cfg->ctas_per_sm = 5;
+    cfg->schedule = CPT_SCHEDULE_PERSISTENT;
     return CPT_OK;
 }
 
@@ -528,7 +621,10 @@ int composite_engine_begin(composite_engine **out, const composite_engine_config
         c.wait_timeout_ms = cfg->wait_timeout_ms;
         if (cfg->slab_members) c.slab_members = cfg->slab_members;
         if (cfg->ctas_per_sm) c.ctas_per_sm = cfg->ctas_per_sm;
+        c.schedule = cfg->schedule;
     }
+    if (c.schedule != CPT_SCHEDULE_PERSISTENT && c.schedule != CPT_SCHEDULE_GRID)
+        return efail(nullptr, CPT_EINVAL, "schedule must be CPT_SCHEDULE_PERSISTENT or CPT_SCHEDULE_GRID");
     if (c.slab_members < 1 || c.slab_members > kMaxSlab) return efail(nullptr, CPT_EINVAL, "slab_members not in 1..255");
     if (c.ctas_per_sm < 1 || c.ctas_per_sm > 8) return efail(nullptr, CPT_EINVAL, "ctas_per_sm not in 1..8");
     if (c.wait_timeout_ms < 0) return efail(nullptr, CPT_EINVAL, "negative timeout");
@@ -722,12 +818,13 @@ int composite_engine_tune(composite_engine *e, const composite_op *ops, int32_t 
     int rc = plan_ops(e, ops, n_ops, &descs, &items, &n_after, true);
     if (rc) return rc;
     static const int slabs[] = {32, 64, 128, 255};
-    static const int ctas[] = {4, 6, 8};
+    // ctas_per_sm 0 stands for the grid schedule
+    static const int ctas[] = {0, 3, 4, 5};
     cudaEvent_t a, b;
     ECK(e, cudaEventCreate(&a));
     ECK(e, cudaEventCreate(&b));
     float best = 1e30f;
-    int best_slab = e->cfg.slab_members, best_ctas = e->cfg.ctas_per_sm;
+    int best_slab = e->cfg.slab_members, best_ctas = e->cfg.ctas_per_sm, best_sched = e->cfg.schedule;
     auto run = [&]() -> int {
         for (const auto &pn : n_after) {
             int r = clear_plane(e, pn.first);
@@ -738,7 +835,8 @@ int composite_engine_tune(composite_engine *e, const composite_op *ops, int32_t 
     for (int s : slabs)
         for (int c : ctas) {
             e->cfg.slab_members = s;
-            e->cfg.ctas_per_sm = c;
+            e->cfg.schedule = c ? CPT_SCHEDULE_PERSISTENT : CPT_SCHEDULE_GRID;
+            e->cfg.ctas_per_sm = c ? c : best_ctas;
             float t_best = 1e30f;
             for (int r = 0; r < repeats && rc == CPT_OK; ++r) {
                 if ((rc = run())) break;             // warm and measure alike: clear + submit
@@ -754,25 +852,27 @@ int composite_engine_tune(composite_engine *e, const composite_op *ops, int32_t 
             if (t_best < best) {
                 best = t_best;
                 best_slab = s;
-                best_ctas = c;
+                best_sched = e->cfg.schedule;
+                if (c) best_ctas = c;
             }
         }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     e->cfg.slab_members = best_slab;
     e->cfg.ctas_per_sm = best_ctas;
+    e->cfg.schedule = best_sched;
     if (rc) return rc;
     rc = run();
     if (rc) return rc;
     if (slab_out) *slab_out = best_slab;
-    if (ctas_out) *ctas_out = best_ctas;
+    if (ctas_out) *ctas_out = best_sched == CPT_SCHEDULE_GRID ? 0 : best_ctas;
     return CPT_OK;
 }
 
 int composite_engine_get_tuning(const composite_engine *e, int32_t *slab_out, int32_t *ctas_out) {
     if (!e) return CPT_EINVAL;
     if (slab_out) *slab_out = e->cfg.slab_members;
-    if (ctas_out) *ctas_out = e->cfg.ctas_per_sm;
+    if (ctas_out) *ctas_out = e->cfg.schedule == CPT_SCHEDULE_GRID ? 0 : e->cfg.ctas_per_sm;
     return CPT_OK;
 }
 

@@ -118,8 +118,15 @@ class Ensemble:
 def ensemble(seed: int, width: int, height: int, n_members: int,
              member_offset: int = 0) -> Ensemble:
     """Water levels for members ``member_offset .. member_offset+n-1``."""
-    t = terrain(seed, width, height)
-    flat_sorted = np.sort(t, axis=None)
+    return ensemble_from_terrain(seed, terrain(seed, width, height), n_members, member_offset)
+
+
+def ensemble_from_terrain(seed: int, t: np.ndarray, n_members: int, member_offset: int = 0,
+                          flat_sorted: np.ndarray | None = None) -> Ensemble:
+    """As ensemble, over a terrain already computed (and optionally sorted)."""
+    height, width = t.shape
+    if flat_sorted is None:
+        flat_sorted = np.sort(t, axis=None)
     p = width * height
     levels = np.empty(n_members, dtype=np.float32)
     flooded = np.empty(n_members, dtype=np.int64)
@@ -131,6 +138,23 @@ def ensemble(seed: int, width: int, height: int, n_members: int,
         levels[i] = flat_sorted[k]
         flooded[i] = int(np.searchsorted(flat_sorted, levels[i], side="left"))
     return Ensemble(seed, width, height, t, levels, flooded)
+
+
+BATCH_SIDES = (256, 512, 1024, 2048, 4096)
+
+
+def batched_requests(seed: int, count: int, n_range=(8, 2048), sides=BATCH_SIDES):
+    """(width, height, members) of `count` composite requests: members
+    log-uniform in n_range, width and height drawn independently from
+    `sides` (so shapes are often not square)."""
+    u = uniforms(_substream(seed, 0xBA7C4), 3 * count).reshape(count, 3)
+    lo, hi = math.log(n_range[0]), math.log(n_range[1])
+    out = []
+    for a, b, c in u:
+        n = int(math.floor(math.exp(lo + a * (hi - lo))))
+        n = min(max(n, n_range[0]), n_range[1])
+        out.append((sides[int(b * len(sides))], sides[int(c * len(sides))], n))
+    return out
 
 
 def fill_masks(ens: Ensemble, out: np.ndarray, members: range | None = None) -> np.ndarray:

@@ -40,8 +40,9 @@ def check(outs, masks_np, lut=None):
 SHAPES = [(1024, 1024, 16), (13, 7, 5), (100, 37, 40), (257, 131, 300), (4096, 3, 9), (1, 1, 2), (48, 600, 1)]
 
 
-def test_many_planes_one_launch():
-    with binding.Engine() as eng:
+@pytest.mark.parametrize("schedule", ["persistent", "grid"])
+def test_many_planes_one_launch(schedule):
+    with binding.Engine(schedule=schedule) as eng:
         data, ops, rops, outs = [], [], [], []
         for i, (w, h, n) in enumerate(SHAPES):
             m = synth.scramble_nonzero(synth.random_masks(50 + i, n, h, w, density=0.3 + 0.05 * i), i)
@@ -60,7 +61,8 @@ def test_many_planes_one_launch():
             check(o, m)
 
 
-def test_index_lists_add_and_remove():
+@pytest.mark.parametrize("schedule", ["persistent", "grid"])
+def test_index_lists_add_and_remove(schedule):
     w, h, total = 300, 70, 500
     ens = synth.scramble_nonzero(synth.random_masks(60, total, h, w, density=0.2), 60)
     dev = padded(ens)
@@ -68,7 +70,7 @@ def test_index_lists_add_and_remove():
     a = rng.choice(total, 300, replace=False).astype(np.int32)
     b = rng.choice(total, 120, replace=False).astype(np.int32)
     drop = a[:170]
-    with binding.Engine(slab_members=64) as eng:
+    with binding.Engine(slab_members=64, schedule=schedule) as eng:
         p = eng.add_plane(w, h)
         q = eng.add_plane(w, h)
         ia, ib, idrop = (torch.from_numpy(x).cuda() for x in (a, b, drop))
@@ -129,7 +131,7 @@ def test_tuner_picks_a_candidate_and_keeps_results_exact():
             m = synth.random_masks(80 + i, n, h, w, density=0.25)
             items.append((m, padded(m), eng.add_plane(w, h), outputs(w, h)))
         slab, ctas = eng.tune([eng.op(p, dev) for _, dev, p, _ in items], repeats=1)
-        assert slab in (32, 64, 128, 255) and ctas in (4, 6, 8)
+        assert slab in (32, 64, 128, 255) and ctas in (0, 3, 4, 5)
         assert eng.tuning() == (slab, ctas)
         eng.render([eng.render_op(p, *o) for _, _, p, o in items])
         eng.sync()

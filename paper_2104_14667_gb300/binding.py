@@ -31,7 +31,7 @@ READ_PATHS = {"linear": CPT_READ_LINEAR, "texture": CPT_READ_TEXTURE, "tma": CPT
 CPT_MODE_COUNT, CPT_MODE_MEAN_DEPTH = 0, 1
 
 HEADER = os.path.join(_build.INCLUDE, "composite.h")
-HEADERS = [os.path.join(_build.INCLUDE, h) for h in ("composite.h", "composite_engine.h")]
+HEADERS = [os.path.join(_build.INCLUDE, h) for h in ("composite.h", "composite_engine.h", "composite_server.h")]
 
 
 class CompositeError(RuntimeError):
@@ -546,6 +546,157 @@ class Engine:
             h, self.h = self.h, None
             self.lib.composite_engine_end(h)
             self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# --- the interactive server (include/composite_server.h) ---------------------
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [
+        ("width", ctypes.c_int32),
+        ("height", ctypes.c_int32),
+        ("resident", ctypes.c_void_p),
+        ("n_resident", ctypes.c_int32),
+        ("overflow", ctypes.c_void_p),
+        ("n_overflow", ctypes.c_int32),
+        ("row_pitch_bytes", ctypes.c_int32),
+        ("member_stride_bytes", ctypes.c_int64),
+        ("max_sessions", ctypes.c_int32),
+        ("max_batch", ctypes.c_int32),
+        ("staging_members", ctypes.c_int32),
+        ("max_cycles_in_flight", ctypes.c_int32),
+        ("hbm_budget_bytes", ctypes.c_int64),
+        ("cuda_stream", ctypes.c_void_p),
+        ("wait_timeout_ms", ctypes.c_int64),
+    ]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int64) for name in
+                ("requests_done", "cycles", "members_added", "members_removed", "recomputes",
+                 "overflow_uploads", "queued", "in_flight")]
+
+
+_server_sig_done = False
+
+
+def _server_lib():
+    global _server_sig_done
+    lib = load()
+    if not _server_sig_done:
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        sig = {
+            "composite_server_default_config": (ctypes.c_int, [ctypes.POINTER(ServerConfig)]),
+            "composite_server_begin": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(ServerConfig)]),
+            "composite_server_open_session": (ctypes.c_int, [vp, ctypes.POINTER(i32)]),
+            "composite_server_close_session": (ctypes.c_int, [vp, i32]),
+            "composite_server_request": (ctypes.c_int, [vp, i32, vp, i32, vp, vp, vp, ctypes.POINTER(i64)]),
+            "composite_server_pump": (ctypes.c_int, [vp, vp, i32, ctypes.POINTER(i32)]),
+            "composite_server_drain": (ctypes.c_int, [vp]),
+            "composite_server_session_members": (ctypes.c_int, [vp, i32, ctypes.POINTER(i64)]),
+            "composite_server_get_stats": (ctypes.c_int, [vp, ctypes.POINTER(ServerStats)]),
+            "composite_server_end": (ctypes.c_int, [vp]),
+            "composite_server_last_error": (ctypes.c_char_p, [vp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _server_sig_done = True
+    return lib
+
+
+def _scheck(lib, srv, rc):
+    if rc != CPT_OK:
+        msg = lib.composite_server_last_error(srv)
+        raise CompositeError(rc, msg.decode() if msg else "")
+
+
+class Server:
+    """Sessions, requests and continuous batching (include/composite_server.h).
+    ``resident``: device uint8[n_r, H, W]; ``overflow``: pinned host uint8[n_o, H, W]
+    with the same row pitch and member stride, or None."""
+
+    def __init__(self, resident, overflow=None, max_sessions=64, max_batch=64, staging_members=64,
+                 max_cycles_in_flight=4, hbm_budget_bytes=0, stream=None, wait_timeout_ms=0):
+        self.lib = _server_lib()
+        rptr, rn, h, w, rstride, rpitch, _, _ = _raster_view(resident)
+        cfg = ServerConfig()
+        self.lib.composite_server_default_config(ctypes.byref(cfg))
+        cfg.width, cfg.height = w, h
+        cfg.resident, cfg.n_resident = rptr, rn
+        cfg.row_pitch_bytes, cfg.member_stride_bytes = rpitch, rstride
+        if overflow is not None:
+            optr, on, oh, ow, ostride, opitch, _, _ = _raster_view(overflow)
+            if (oh, ow, ostride, opitch) != (h, w, rstride, rpitch):
+                raise ValueError("overflow must have the resident part's layout")
+            cfg.overflow, cfg.n_overflow = optr, on
+        cfg.max_sessions, cfg.max_batch = max_sessions, max_batch
+        cfg.staging_members, cfg.max_cycles_in_flight = staging_members, max_cycles_in_flight
+        cfg.hbm_budget_bytes, cfg.cuda_stream, cfg.wait_timeout_ms = hbm_budget_bytes, stream, wait_timeout_ms
+        srv = ctypes.c_void_p()
+        _scheck(self.lib, None, self.lib.composite_server_begin(ctypes.byref(srv), ctypes.byref(cfg)))
+        self.h = srv
+        self.width, self.height = w, h
+        self._members = (resident, overflow)
+        self._pending = {}
+
+    def open_session(self) -> int:
+        s = ctypes.c_int32()
+        _scheck(self.lib, self.h, self.lib.composite_server_open_session(self.h, ctypes.byref(s)))
+        return s.value
+
+    def close_session(self, session: int):
+        _scheck(self.lib, self.h, self.lib.composite_server_close_session(self.h, session))
+
+    def request(self, session: int, toggle, counts_out=None, bucket_out=None, rgba_out=None) -> int:
+        ids = np.ascontiguousarray(np.asarray(toggle, dtype=np.int32))
+        rid = ctypes.c_int64()
+        _scheck(self.lib, self.h, self.lib.composite_server_request(
+            self.h, session, ids.ctypes.data if ids.size else None, int(ids.size), _ptr(counts_out),
+            _ptr(bucket_out), _ptr(rgba_out), ctypes.byref(rid)))
+        self._pending[rid.value] = (counts_out, bucket_out, rgba_out)
+        return rid.value
+
+    def pump(self, capacity: int = 4096) -> list:
+        buf = (ctypes.c_int64 * capacity)()
+        n = ctypes.c_int32()
+        _scheck(self.lib, self.h, self.lib.composite_server_pump(self.h, buf, capacity, ctypes.byref(n)))
+        done = list(buf[: n.value])
+        for rid in done:
+            self._pending.pop(rid, None)
+        return done
+
+    def drain(self):
+        _scheck(self.lib, self.h, self.lib.composite_server_drain(self.h))
+        self._pending.clear()
+
+    def session_members(self, session: int) -> int:
+        n = ctypes.c_int64()
+        _scheck(self.lib, self.h, self.lib.composite_server_session_members(self.h, session, ctypes.byref(n)))
+        return n.value
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _scheck(self.lib, self.h, self.lib.composite_server_get_stats(self.h, ctypes.byref(st)))
+        return {name: getattr(st, name) for name, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            h, self.h = self.h, None
+            self.lib.composite_server_end(h)
+            self._pending.clear()
 
     def __enter__(self):
         return self

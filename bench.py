@@ -59,8 +59,17 @@ def parse_args():
                    help="target CPU time of the oracle baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--sweep", choices=["readpath", "layout", "streaming", "tiny", "batched"], default=None,
+    p.add_argument("--sweep", choices=["readpath", "layout", "streaming", "tiny", "batched", "serving"],
+                   default=None,
                    help="print one JSON line per point of a workload sweep instead of the bench line")
+    p.add_argument("--resident", type=int, default=2048, help="serving: members resident in HBM")
+    p.add_argument("--overflow", type=int, default=4096, help="serving: members in pinned host memory")
+    p.add_argument("--sessions", type=int, default=16, help="serving: open sessions")
+    p.add_argument("--requests", type=int, default=200, help="serving: requests per offered rate")
+    p.add_argument("--max-batch", type=int, default=64, help="serving: requests per cycle")
+    p.add_argument("--poll-us", type=float, default=100.0, help="serving: host back-off between idle polls")
+    p.add_argument("--rates", type=float, nargs="+", default=[50, 100, 200, 500],
+                   help="serving: offered request rates (per second)")
     p.add_argument("--e2e-mode", choices=["staged", "host_read"], default="staged",
                    help="which host-to-device path the e2e value reports (both are measured)")
     return p.parse_args()
@@ -658,6 +667,101 @@ def sweep_batched(args, torch, binding, device, stream):
         "outputs_identical": bool(same)}), flush=True)
 
 
+def sweep_serving(args, torch, binding, device, stream):
+    """The interactive server: a resident ensemble in HBM plus overflow members
+    in pinned host memory, sessions toggling member subsets on a Poisson
+    trace; continuous batching against serving one request at a time, on the
+    same trace.  Latency = completion seen by the host - scheduled arrival."""
+    import synth
+    from paper_2104_14667_gb300 import metrics
+    W = H = args.width
+    R, O = args.resident, args.overflow
+    try:
+        ram = os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES")
+    except (ValueError, OSError):
+        ram = 0
+    if ram and O * W * H > 0.4 * ram:
+        O = int(0.4 * ram // (W * H))
+    t_setup = time.perf_counter()
+    ens = synth.ensemble(5, W, H, R + O)
+    tdev = torch.from_numpy(ens.terrain).to(device)
+    resident = torch.empty((R, H, W), dtype=torch.uint8, device=device)
+    synth.fill_masks_torch(ens, resident, range(R), terrain_t=tdev)
+    overflow = torch.empty((O, H, W), dtype=torch.uint8, pin_memory=True) if O else None
+    step = 256
+    tmp = torch.empty((step, H, W), dtype=torch.uint8, device=device)
+    for m0 in range(0, O, step):
+        m1 = min(O, m0 + step)
+        synth.fill_masks_torch(ens, tmp[: m1 - m0], range(R + m0, R + m1), terrain_t=tdev)
+        overflow[m0:m1].copy_(tmp[: m1 - m0])
+    del tmp
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t_setup
+    sorted_levels = ens.levels
+    n_sessions = args.sessions
+    outs = [(torch.empty((H, W), dtype=torch.uint8, device=device),
+             torch.empty((H, W, 4), dtype=torch.uint8, device=device)) for _ in range(n_sessions)]
+
+    def run(trace, max_batch, cycles_in_flight):
+        checks = {}
+        with binding.Server(resident, overflow, max_sessions=n_sessions, max_batch=max_batch,
+                            staging_members=args.chunk * 2, max_cycles_in_flight=cycles_in_flight,
+                            stream=stream.cuda_stream) as srv:
+            sessions = [srv.open_session() for _ in range(n_sessions)]
+            sets = [np.zeros(R + O, bool) for _ in range(n_sessions)]
+            arrival, done_at = {}, {}
+            t0 = time.perf_counter()
+            i = 0
+            while i < len(trace) or len(done_at) < len(trace):
+                now = time.perf_counter() - t0
+                while i < len(trace) and trace[i][0] <= now:
+                    t_arr, s, ids = trace[i]
+                    for t in ids:
+                        sets[s][t] ^= True
+                    if i % 25 == 0:
+                        c = torch.empty((H, W), dtype=torch.int32, device=device)
+                        rid = srv.request(sessions[s], ids, c, None, None)
+                        checks[rid] = (c, np.flatnonzero(sets[s]))
+                    else:
+                        rid = srv.request(sessions[s], ids, None, *outs[s])
+                    arrival[rid] = t_arr
+                    i += 1
+                done = srv.pump()
+                for rid in done:
+                    done_at[rid] = time.perf_counter() - t0
+                if not done and (i >= len(trace) or trace[i][0] > time.perf_counter() - t0):
+                    time.sleep(args.poll_us * 1e-6)     # back off: hot polling slows the host link
+                if time.perf_counter() - t0 > 300:
+                    raise RuntimeError("serving run exceeded 300 s")
+            wall = max(done_at.values()) - trace[0][0]
+            stats = srv.stats()
+        torch.cuda.synchronize()
+        lat = [1e3 * (done_at[r] - arrival[r]) for r in done_at]
+        # exactness: sampled requests against the terrain-threshold identity
+        exact = True
+        for rid, (c, members) in checks.items():
+            lv = np.sort(sorted_levels[members])
+            ident = len(members) - np.searchsorted(lv, ens.terrain.ravel(), side="right").reshape(H, W)
+            exact &= bool(np.array_equal(c.cpu().numpy().astype(np.int64), ident))
+        return {"composites_per_s": len(trace) / wall, "p50_ms": metrics.percentile(lat, 50),
+                "p99_ms": metrics.percentile(lat, 99), "mean_ms": float(np.mean(lat)), "wall_s": wall,
+                "cycles": stats["cycles"], "overflow_uploads": stats["overflow_uploads"],
+                "members_added": stats["members_added"], "members_removed": stats["members_removed"],
+                "recomputes": stats["recomputes"], "checked": len(checks), "exact": exact,
+                "cycle_device_s": stats["cycle_device_us"] * 1e-6, "enqueue_host_s": stats["enqueue_host_us"] * 1e-6}
+
+    for rate in args.rates:
+        trace = synth.serving_trace(5, args.requests, rate, n_sessions, R + O)
+        batched = run(trace, args.max_batch, 4)
+        single = run(trace, 1, 1)      # the queue alone: one request on the device at a time
+        print(json.dumps({"sweep": "serving", "rate_per_s": rate, "requests": len(trace), "resident": R,
+                          "overflow": O, "side": W, "sessions": n_sessions, "setup_s": setup_s,
+                          "toggle_members_mean": float(np.mean([len(t[2]) for t in trace])),
+                          "batched": batched, "one_at_a_time": single,
+                          "throughput_gain": batched["composites_per_s"] / single["composites_per_s"],
+                          "p99_gain": single["p99_ms"] / batched["p99_ms"]}), flush=True)
+
+
 def run_sweep(args):
     import torch
     from paper_2104_14667_gb300 import binding
@@ -675,6 +779,8 @@ def run_sweep(args):
     elif args.sweep == "streaming":
         sweep_streaming(args, torch, binding, device, stream, chunks=[1, 2, 4, 8, 16, 64, 128],
                         stagings=[1, 3, 4])
+    elif args.sweep == "serving":
+        sweep_serving(args, torch, binding, device, stream)
     elif args.sweep == "batched":
         sweep_batched(args, torch, binding, device, stream)
     elif args.sweep == "tiny":

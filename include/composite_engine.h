@@ -50,6 +50,11 @@ typedef struct composite_engine_config {
     int32_t ctas_per_sm;      /* persistent CTAs of 256 threads per SM, 1..8; 0 = 5   */
     int64_t wait_timeout_ms;  /* bound on host waits; 0 = 10000                        */
     int32_t schedule;         /* CPT_SCHEDULE_*; default CPT_SCHEDULE_PERSISTENT       */
+    void *upload_stream;      /* cudaStream_t for the engine's small host-to-device
+                                 uploads (op descriptors), NULL = cuda_stream; a caller
+                                 that streams its own rasters on a copy stream passes
+                                 it here so the small uploads queue behind its uploads
+                                 in order instead of competing for a copy engine      */
 } composite_engine_config;
 
 /* One add or remove of n_members masks to one plane.  Member i of the op is

@@ -74,6 +74,9 @@ typedef struct composite_server_stats {
     int64_t overflow_uploads;      /* overflow rasters uploaded                           */
     int64_t queued;                /* requests waiting now                                 */
     int64_t in_flight;             /* requests in cycles not yet completed                 */
+    int64_t cycle_device_us;       /* sum over completed cycles of the time from the cycle's
+                                      first queued operation to its completion (events)  */
+    int64_t enqueue_host_us;       /* host time spent building and queueing cycles         */
 } composite_server_stats;
 
 int composite_server_default_config(composite_server_config *cfg);

@@ -364,6 +364,7 @@ class EngineConfig(ctypes.Structure):
         ("ctas_per_sm", ctypes.c_int32),
         ("wait_timeout_ms", ctypes.c_int64),
         ("schedule", ctypes.c_int32),
+        ("upload_stream", ctypes.c_void_p),
     ]
 
 
@@ -585,7 +586,7 @@ class ServerConfig(ctypes.Structure):
 class ServerStats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in
                 ("requests_done", "cycles", "members_added", "members_removed", "recomputes",
-                 "overflow_uploads", "queued", "in_flight")]
+                 "overflow_uploads", "queued", "in_flight", "cycle_device_us", "enqueue_host_us")]
 
 
 _server_sig_done = False

@@ -110,7 +110,9 @@ int64_t timeout_ms(const composite_ctx *ctx) {
     return ctx->cfg.wait_timeout_ms > 0 ? ctx->cfg.wait_timeout_ms : 10000;
 }
 
-// Polls an event until it completes or the context's timeout runs out.
+// Polls an event until it completes or the context's timeout runs out; after
+// a short spin it sleeps between polls (tight polling loops were measured to
+// slow host-to-device copies over the host link).
 int wait_event(composite_ctx *ctx, cudaEvent_t ev) {
     const auto deadline = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms(ctx));
     for (unsigned spin = 0;; ++spin) {
@@ -119,7 +121,7 @@ int wait_event(composite_ctx *ctx, cudaEvent_t ev) {
         if (e != cudaErrorNotReady) return cuda_fail(ctx, e, "cudaEventQuery");
         if (std::chrono::steady_clock::now() > deadline)
             return fail(ctx, CPT_ETIMEOUT, "wait exceeded %lld ms", (long long)timeout_ms(ctx));
-        if (spin < 2000)
+        if (spin < 200)
             std::this_thread::yield();
         else
             std::this_thread::sleep_for(std::chrono::microseconds(50));

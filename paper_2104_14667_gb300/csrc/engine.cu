@@ -33,6 +33,7 @@ using cpt::Lut;
 constexpr int kThreads = 256;          // threads per CTA = 16-pixel groups per tile
 constexpr int kMaxPlanes = 1 << 16;
 constexpr int kMaxSlab = 255;          // packed byte counters
+constexpr int kUploadRing = 64;        // descriptor uploads in flight before the host waits
 
 struct OpDesc {
     const uint8_t *base;
@@ -284,7 +285,8 @@ struct Upload {
     void *d = nullptr;
     void *h = nullptr;
     size_t cap = 0;
-    cudaEvent_t done = nullptr;
+    cudaEvent_t done = nullptr;      // the upload out of h finished (upload stream)
+    cudaEvent_t consumed = nullptr;  // the launch that read d finished (engine stream)
     bool used = false;
 };
 
@@ -302,7 +304,7 @@ struct composite_engine {
     int *d_flags = nullptr;
     int *h_flags = nullptr;
     uint32_t *d_counter = nullptr;
-    Upload up_ops[2], up_render[2];
+    Upload up_ops[kUploadRing], up_render[kUploadRing];
     int up_i = 0, rup_i = 0;
     cudaEvent_t done_ev = nullptr;
     Lut default_lut{};
@@ -353,7 +355,7 @@ int ewait(composite_engine *e, cudaEvent_t ev) {
         if (r != cudaErrorNotReady) return ecuda(e, r, "cudaEventQuery");
         if (std::chrono::steady_clock::now() > deadline)
             return efail(e, CPT_ETIMEOUT, "wait exceeded %lld ms", (long long)etimeout(e));
-        if (spin < 2000)
+        if (spin < 200)
             std::this_thread::yield();
         else
             std::this_thread::sleep_for(std::chrono::microseconds(50));
@@ -375,15 +377,19 @@ Lut make_lut(const uint8_t *rgba) {
     return l;
 }
 
-// Copies `bytes` of descriptors into the next slot of a two-slot upload ring
-// and queues their upload; returns the device copy.
-int upload(composite_engine *e, Upload *ring, int *idx, const void *src, size_t bytes, void **dev) {
+// Copies `bytes` of descriptors into the next slot of the upload ring
+// and queues their upload, on the upload stream when the engine has one (so
+// that small uploads follow the caller's own uploads in order instead of
+// waiting behind them on a copy engine); returns the slot.  The caller
+// records slot->consumed on the engine stream after the launch that reads it.
+int upload(composite_engine *e, Upload *ring, int *idx, const void *src, size_t bytes, Upload **slot) {
     Upload &u = ring[*idx];
-    *idx ^= 1;
+    *idx = (*idx + 1) % kUploadRing;
     if (u.used) {
         int rc = ewait(e, u.done);
         if (rc) return rc;
     }
+    cudaStream_t us = e->cfg.upload_stream ? static_cast<cudaStream_t>(e->cfg.upload_stream) : e->stream;
     if (u.cap < bytes) {
         if (u.d) cudaFree(u.d);
         if (u.h) cudaFreeHost(u.h);
@@ -395,10 +401,12 @@ int upload(composite_engine *e, Upload *ring, int *idx, const void *src, size_t 
         u.cap = cap;
     }
     memcpy(u.h, src, bytes);
-    ECK(e, cudaMemcpyAsync(u.d, u.h, bytes, cudaMemcpyHostToDevice, e->stream));
-    ECK(e, cudaEventRecord(u.done, e->stream));
+    if (us != e->stream && u.used) ECK(e, cudaStreamWaitEvent(us, u.consumed, 0));
+    ECK(e, cudaMemcpyAsync(u.d, u.h, bytes, cudaMemcpyHostToDevice, us));
+    ECK(e, cudaEventRecord(u.done, us));
+    if (us != e->stream) ECK(e, cudaStreamWaitEvent(e->stream, u.done, 0));
     u.used = true;
-    *dev = u.d;
+    *slot = &u;
     return CPT_OK;
 }
 
@@ -555,11 +563,12 @@ int submit_internal(composite_engine *e, const composite_op *ops, int32_t n_ops)
     int rc = plan_ops(e, ops, n_ops, &descs, &items, &n_after, false);
     if (rc) return rc;
     if (items > 0) {
-        void *d = nullptr;
-        rc = upload(e, e->up_ops, &e->up_i, descs.data(), descs.size() * sizeof(OpDesc), &d);
+        Upload *u = nullptr;
+        rc = upload(e, e->up_ops, &e->up_i, descs.data(), descs.size() * sizeof(OpDesc), &u);
         if (rc) return rc;
-        rc = launch_accumulate(e, d, (int)descs.size(), items, e->d_counter);
+        rc = launch_accumulate(e, u->d, (int)descs.size(), items, e->d_counter);
         if (rc) return rc;
+        ECK(e, cudaEventRecord(u->consumed, e->stream));
     }
     for (const auto &pn : n_after) e->planes[pn.first].n = pn.second;
     return CPT_OK;
@@ -584,10 +593,11 @@ void destroy_engine(composite_engine *e) {
     for (PlaneRec &p : e->planes)
         if (p.data) cudaFree(p.data);
     for (Upload *ring : {e->up_ops, e->up_render})
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < kUploadRing; ++i) {
             if (ring[i].d) cudaFree(ring[i].d);
             if (ring[i].h) cudaFreeHost(ring[i].h);
             if (ring[i].done) cudaEventDestroy(ring[i].done);
+            if (ring[i].consumed) cudaEventDestroy(ring[i].consumed);
         }
     if (e->d_flags) cudaFree(e->d_flags);
     if (e->h_flags) cudaFreeHost(e->h_flags);
@@ -622,6 +632,7 @@ int composite_engine_begin(composite_engine **out, const composite_engine_config
         if (cfg->slab_members) c.slab_members = cfg->slab_members;
         if (cfg->ctas_per_sm) c.ctas_per_sm = cfg->ctas_per_sm;
         c.schedule = cfg->schedule;
+        c.upload_stream = cfg->upload_stream;
     }
     if (c.schedule != CPT_SCHEDULE_PERSISTENT && c.schedule != CPT_SCHEDULE_GRID)
         return efail(nullptr, CPT_EINVAL, "schedule must be CPT_SCHEDULE_PERSISTENT or CPT_SCHEDULE_GRID");
@@ -645,7 +656,10 @@ int composite_engine_begin(composite_engine **out, const composite_engine_config
         ECK(e, cudaMalloc(&e->d_counter, sizeof(uint32_t)));
         ECK(e, cudaEventCreateWithFlags(&e->done_ev, cudaEventDisableTiming));
         for (Upload *ring : {e->up_ops, e->up_render})
-            for (int i = 0; i < 2; ++i) ECK(e, cudaEventCreateWithFlags(&ring[i].done, cudaEventDisableTiming));
+            for (int i = 0; i < kUploadRing; ++i) {
+                ECK(e, cudaEventCreateWithFlags(&ring[i].done, cudaEventDisableTiming));
+                ECK(e, cudaEventCreateWithFlags(&ring[i].consumed, cudaEventDisableTiming));
+            }
         e->default_lut = make_lut(nullptr);
         return CPT_OK;
     };
@@ -710,10 +724,13 @@ int composite_engine_render(composite_engine *e, const composite_render_op *ops,
     int64_t items = 0;
     int rc = plan_render(e, ops, n_ops, &descs, &items, nullptr);
     if (rc || items == 0) return rc;
-    void *d = nullptr;
-    rc = upload(e, e->up_render, &e->rup_i, descs.data(), descs.size() * sizeof(RenderDesc), &d);
+    Upload *u = nullptr;
+    rc = upload(e, e->up_render, &e->rup_i, descs.data(), descs.size() * sizeof(RenderDesc), &u);
     if (rc) return rc;
-    return launch_render(e, d, (int)descs.size(), items, e->d_counter, lut_rgba ? make_lut(lut_rgba) : e->default_lut);
+    rc = launch_render(e, u->d, (int)descs.size(), items, e->d_counter, lut_rgba ? make_lut(lut_rgba) : e->default_lut);
+    if (rc) return rc;
+    ECK(e, cudaEventRecord(u->consumed, e->stream));
+    return CPT_OK;
 }
 
 int composite_engine_member_count(const composite_engine *e, int32_t plane, int64_t *n_out) {

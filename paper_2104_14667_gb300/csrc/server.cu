@@ -39,7 +39,9 @@ struct Request {
 
 struct Cycle {
     bool in_flight = false;
-    cudaEvent_t done = nullptr;
+    cudaEvent_t start = nullptr;   // timed: recorded on the copy stream when the cycle is queued
+    cudaEvent_t done = nullptr;    // timed: the cycle's last operation (compute stream)
+    cudaEvent_t index_ready = nullptr;
     std::vector<int64_t> ids;
     std::vector<int32_t> sessions;
     int32_t *d_index = nullptr;
@@ -52,6 +54,7 @@ struct OverflowItem {
     int32_t request;   // index into the cycle's admitted requests
     int32_t sign;
     int32_t member;    // overflow id (0-based within the overflow part)
+    int32_t pos;       // position of the member among the cycle's distinct overflow ids
 };
 
 thread_local std::string g_server_error;
@@ -150,6 +153,8 @@ int reap(composite_server *s, int64_t *completed, int32_t capacity, int32_t *n_c
         const cudaError_t q = cudaEventQuery(c.done);
         if (q == cudaErrorNotReady) continue;
         if (q != cudaSuccess) return scuda(s, q, "cudaEventQuery");
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c.start, c.done) == cudaSuccess) s->stats.cycle_device_us += (int64_t)(1000.0f * ms);
         for (int64_t id : c.ids) {
             if (completed && n_completed && *n_completed < capacity) completed[(*n_completed)++] = id;
             ++s->stats.requests_done;
@@ -220,7 +225,7 @@ int launch_cycle(composite_server *s, bool *launched) {
                     if (id < R)
                         (sign > 0 ? res_add[r] : res_rem[r]).push_back(id);
                     else
-                        ovf.push_back({(int32_t)r, sign, id - R});
+                        ovf.push_back({(int32_t)r, sign, id - R, 0});
                 }
             }
         }
@@ -231,12 +236,23 @@ int launch_cycle(composite_server *s, bool *launched) {
         ss.n = n_after;
         ss.busy = true;
     }
-    std::stable_sort(ovf.begin(), ovf.end(), [](const OverflowItem &a, const OverflowItem &b) {
-        return a.request != b.request ? a.request < b.request : a.sign > b.sign;
+    // Distinct overflow members of the cycle: each is uploaded once, whatever
+    // number of requests toggle it; requests gather it from staging by index.
+    std::vector<int32_t> distinct;
+    distinct.reserve(ovf.size());
+    for (const OverflowItem &o : ovf) distinct.push_back(o.member);
+    std::sort(distinct.begin(), distinct.end());
+    distinct.erase(std::unique(distinct.begin(), distinct.end()), distinct.end());
+    for (OverflowItem &o : ovf)
+        o.pos = (int32_t)(std::lower_bound(distinct.begin(), distinct.end(), o.member) - distinct.begin());
+    std::sort(ovf.begin(), ovf.end(), [](const OverflowItem &a, const OverflowItem &b) {
+        if (a.request != b.request) return a.request < b.request;
+        if (a.sign != b.sign) return a.sign > b.sign;
+        return a.pos < b.pos;
     });
 
-    // index lists of the resident ops, uploaded on the compute stream
-    size_t total = 0;
+    // index lists of the resident ops (and, after them, of the overflow ops)
+    size_t total = ovf.size();
     for (size_t r = 0; r < batch.size(); ++r) total += res_add[r].size() + res_rem[r].size();
     int rc = reserve_index(s, *cyc, std::max<size_t>(total, 1));
     if (rc) return rc;
@@ -264,43 +280,71 @@ int launch_cycle(composite_server *s, bool *launched) {
             off += ids.size();
         }
     }
-    if (off) SCK(s, cudaMemcpyAsync(cyc->d_index, cyc->h_index, off * sizeof(int32_t), cudaMemcpyHostToDevice, s->compute));
+    SCK(s, cudaEventRecord(cyc->start, s->copy));
+    if (off) {
+        // on the copy stream, ahead of this cycle's raster uploads
+        SCK(s, cudaMemcpyAsync(cyc->d_index, cyc->h_index, off * sizeof(int32_t), cudaMemcpyHostToDevice, s->copy));
+        SCK(s, cudaEventRecord(cyc->index_ready, s->copy));
+        SCK(s, cudaStreamWaitEvent(s->compute, cyc->index_ready, 0));
+    }
     if (!ops.empty()) {
         rc = engine_rc(s, composite_engine_submit(s->eng, ops.data(), (int32_t)ops.size()));
         if (rc) return rc;
     }
 
-    // overflow members through the two staging halves
+    // Overflow members through the two staging halves: chunk c uploads the
+    // distinct members [c0, c1) into half h on the copy stream, then one
+    // engine submit folds, for every (request, sign) group, the group's
+    // members in that chunk (their staging slots as an index list).
+    std::vector<size_t> group_start, cursor;
+    for (size_t i = 0; i < ovf.size(); ++i)
+        if (i == 0 || ovf[i].request != ovf[i - 1].request || ovf[i].sign != ovf[i - 1].sign) group_start.push_back(i);
+    cursor = group_start;
+    group_start.push_back(ovf.size());
     const int half = s->cfg.staging_members;
-    for (size_t c0 = 0; c0 < ovf.size(); c0 += half) {
-        const size_t c1 = std::min(ovf.size(), c0 + (size_t)half);
+    for (size_t c0 = 0; c0 < distinct.size(); c0 += half) {
+        const size_t c1 = std::min(distinct.size(), c0 + (size_t)half);
         const int h = s->stage_half;
         s->stage_half ^= 1;
         uint8_t *base = s->d_stage + (int64_t)h * half * s->cfg.member_stride_bytes;
-        SCK(s, cudaStreamWaitEvent(s->copy, s->stage_free[h], 0));
-        for (size_t i = c0; i < c1; ++i) {
-            const uint8_t *src = static_cast<const uint8_t *>(s->cfg.overflow) + (int64_t)ovf[i].member * s->cfg.member_stride_bytes;
-            SCK(s, cudaMemcpyAsync(base + (int64_t)(i - c0) * s->cfg.member_stride_bytes, src, (size_t)s->raster_bytes,
-                                   cudaMemcpyDefault, s->copy));
-        }
-        s->stats.overflow_uploads += (int64_t)(c1 - c0);
-        SCK(s, cudaEventRecord(s->stage_ready[h], s->copy));
-        SCK(s, cudaStreamWaitEvent(s->compute, s->stage_ready[h], 0));
         std::vector<composite_op> chunk_ops;
-        for (size_t i = c0; i < c1;) {
-            size_t j = i;
-            while (j < c1 && ovf[j].request == ovf[i].request && ovf[j].sign == ovf[i].sign) ++j;
+        const size_t off0 = off;
+        for (size_t g = 0; g + 1 < group_start.size(); ++g) {
+            size_t &cur = cursor[g];
+            const size_t first = cur;
+            while (cur < group_start[g + 1] && (size_t)ovf[cur].pos < c1) {
+                cyc->h_index[off + (cur - first)] = ovf[cur].pos - (int32_t)c0;
+                ++cur;
+            }
+            if (cur == first) continue;
             composite_op o{};
-            o.plane = s->sessions[batch[ovf[i].request].session].plane;
-            o.sign = ovf[i].sign;
-            o.members = base + (int64_t)(i - c0) * s->cfg.member_stride_bytes;
-            o.member_index = nullptr;
-            o.n_members = (int32_t)(j - i);
+            o.plane = s->sessions[batch[ovf[first].request].session].plane;
+            o.sign = ovf[first].sign;
+            o.members = base;
+            o.member_index = cyc->d_index + off;
+            o.n_members = (int32_t)(cur - first);
             o.row_pitch_bytes = s->cfg.row_pitch_bytes;
             o.member_stride_bytes = s->cfg.member_stride_bytes;
             chunk_ops.push_back(o);
+            off += cur - first;
+        }
+        SCK(s, cudaStreamWaitEvent(s->copy, s->stage_free[h], 0));
+        for (size_t i = c0; i < c1;) {
+            // consecutive overflow ids go up in one copy
+            size_t j = i + 1;
+            while (j < c1 && distinct[j] == distinct[j - 1] + 1) ++j;
+            const uint8_t *src = static_cast<const uint8_t *>(s->cfg.overflow) + (int64_t)distinct[i] * s->cfg.member_stride_bytes;
+            const size_t bytes = (size_t)((int64_t)(j - i - 1) * s->cfg.member_stride_bytes + s->raster_bytes);
+            SCK(s, cudaMemcpyAsync(base + (int64_t)(i - c0) * s->cfg.member_stride_bytes, src, bytes,
+                                   cudaMemcpyDefault, s->copy));
             i = j;
         }
+        s->stats.overflow_uploads += (int64_t)(c1 - c0);
+        if (off > off0)
+            SCK(s, cudaMemcpyAsync(cyc->d_index + off0, cyc->h_index + off0, (off - off0) * sizeof(int32_t),
+                                   cudaMemcpyHostToDevice, s->copy));
+        SCK(s, cudaEventRecord(s->stage_ready[h], s->copy));
+        SCK(s, cudaStreamWaitEvent(s->compute, s->stage_ready[h], 0));
         rc = engine_rc(s, composite_engine_submit(s->eng, chunk_ops.data(), (int32_t)chunk_ops.size()));
         if (rc) return rc;
         SCK(s, cudaEventRecord(s->stage_free[h], s->compute));
@@ -337,6 +381,8 @@ void destroy_server(composite_server *s) {
     if (s->eng) composite_engine_end(s->eng);
     for (Cycle &c : s->cycles) {
         if (c.done) cudaEventDestroy(c.done);
+        if (c.start) cudaEventDestroy(c.start);
+        if (c.index_ready) cudaEventDestroy(c.index_ready);
         if (c.d_index) cudaFree(c.d_index);
         if (c.h_index) cudaFreeHost(c.h_index);
     }
@@ -418,6 +464,7 @@ int composite_server_begin(composite_server **out, const composite_server_config
         ec.cuda_stream = s->compute;
         ec.wait_timeout_ms = c.wait_timeout_ms;
         ec.slab_members = 255;
+        ec.upload_stream = s->copy;
         int rc = composite_engine_begin(&s->eng, &ec);
         if (rc) return sfail(s, rc, "engine: %s", composite_engine_last_error(nullptr));
         const int64_t stage = c.n_overflow > 0 ? 2ll * c.staging_members * c.member_stride_bytes : 0;
@@ -429,7 +476,11 @@ int composite_server_begin(composite_server **out, const composite_server_config
             SCK(s, cudaEventCreateWithFlags(&s->stage_free[h], cudaEventDisableTiming));
         }
         s->cycles.resize(c.max_cycles_in_flight);
-        for (Cycle &cy : s->cycles) SCK(s, cudaEventCreateWithFlags(&cy.done, cudaEventDisableTiming));
+        for (Cycle &cy : s->cycles) {
+            SCK(s, cudaEventCreate(&cy.start));
+            SCK(s, cudaEventCreate(&cy.done));
+            SCK(s, cudaEventCreateWithFlags(&cy.index_ready, cudaEventDisableTiming));
+        }
         return CPT_OK;
     };
     const int rc = setup();
@@ -526,7 +577,11 @@ int composite_server_pump(composite_server *s, int64_t *completed, int32_t capac
     if (rc) return rc;
     for (;;) {
         bool launched = false;
+        const auto t0 = std::chrono::steady_clock::now();
         rc = launch_cycle(s, &launched);
+        if (launched)
+            s->stats.enqueue_host_us +=
+                std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - t0).count();
         if (rc || !launched) return rc;
     }
 }
@@ -545,7 +600,7 @@ int composite_server_drain(composite_server *s) {
         } else if (std::chrono::steady_clock::now() > deadline) {
             return sfail(s, CPT_ETIMEOUT, "no request completed within %lld ms", (long long)timeout_ms(s));
         }
-        if (spin > 1000) std::this_thread::sleep_for(std::chrono::microseconds(20));
+        if (spin > 200) std::this_thread::sleep_for(std::chrono::microseconds(50));
     }
     return CPT_OK;
 }

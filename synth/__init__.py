@@ -157,6 +157,24 @@ def batched_requests(seed: int, count: int, n_range=(8, 2048), sides=BATCH_SIDES
     return out
 
 
+def serving_trace(seed: int, n_requests: int, rate_per_s: float, n_sessions: int, n_members: int,
+                  size_range=(8, 4096)):
+    """Requests of an interactive session mix: Poisson arrivals at rate_per_s
+    (exponential gaps), a uniform session, and a toggle set whose size is
+    log-uniform in size_range, drawn uniformly from all members.
+    Returns [(arrival_s, session, int32 ids)]."""
+    u = uniforms(_substream(seed, 0x5E7E), 3 * n_requests).reshape(n_requests, 3)
+    lo, hi = math.log(size_range[0]), math.log(size_range[1])
+    t = 0.0
+    out = []
+    for r, (a, b, c) in enumerate(u):
+        t += -math.log1p(-a) / rate_per_s
+        k = min(max(int(math.exp(lo + c * (hi - lo))), size_range[0]), size_range[1], n_members)
+        ids = (splitmix64(_substream(seed, 0x70661E + r), k) % np.uint64(n_members)).astype(np.int32)
+        out.append((t, int(b * n_sessions), ids))
+    return out
+
+
 def fill_masks(ens: Ensemble, out: np.ndarray, members: range | None = None) -> np.ndarray:
     """Writes uint8 {0,1} masks of ``members`` into ``out`` (uint8[n, H, W])."""
     idx = range(ens.n) if members is None else members

@@ -20,8 +20,9 @@
  *     message is available from composite_last_error(ctx) until the next call
  *     on that context.
  *   - A raster is `height` rows of `width` elements; element type uint8 in
- *     CPT_MODE_COUNT, float32 in CPT_MODE_MEAN_DEPTH.  Row y of member m
- *     starts at members + m * member_stride_bytes + y * row_pitch_bytes.
+ *     CPT_MODE_COUNT (or one bit per pixel with CPT_MASK_BITS), float32 in
+ *     CPT_MODE_MEAN_DEPTH.  Row y of member m starts at members +
+ *     m * member_stride_bytes + y * row_pitch_bytes.
  *   - Memory kind of `members` is detected (cudaPointerGetAttributes):
  *       pageable host  -> copied through the library's pinned ring; the
  *                         caller may reuse the memory as soon as the call
@@ -74,6 +75,16 @@ enum {
     CPT_MODE_MEAN_DEPTH = 1   /* float32 depths -> per-pixel mean (float32)   */
 };
 
+/* How a mask raster is stored (CPT_MODE_COUNT).  Bit-packed masks are the
+ * compressed upload the paper proposes (Section 7.1: compress the input and
+ * decompress it on the GPU): 8 times fewer bytes over the host link and in
+ * device memory, decoded inside the accumulation kernel. */
+enum {
+    CPT_MASK_BYTES = 0,       /* one byte per pixel, nonzero = flooded                  */
+    CPT_MASK_BITS = 1         /* one bit per pixel: pixel x is bit (x & 7) of byte x >> 3
+                                 of its row; a row is ceil(width / 8) bytes            */
+};
+
 typedef struct composite_config {
     int32_t read_path;          /* CPT_READ_*; default CPT_READ_LINEAR                    */
     int32_t staging_buffers;    /* k device receiving buffers, 1..8; 1 is the paper's
@@ -98,6 +109,8 @@ typedef struct composite_config {
     int32_t tma_box_bytes;      /* CPT_READ_TMA box width in bytes: 64, 128 or 256 (a box is
                                    2 KiB per member: width x 2048/width rows, x 8 members);
                                    0 = 256                                                */
+    int32_t mask_format;        /* CPT_MASK_*; CPT_MASK_BITS needs CPT_MODE_COUNT and
+                                   CPT_READ_LINEAR; default CPT_MASK_BYTES                */
 } composite_config;
 
 /* Fills *cfg with the defaults listed above.  CPT_EINVAL if cfg is NULL. */
@@ -120,9 +133,9 @@ int composite_clear(composite_ctx *ctx);
 /* Adds n_members rasters to the multiset: count(p) += [mask(p) != 0], or in
  * mean-depth mode sum(p) += d(p) (Fig. 3, steps 3-7: upload into receiving
  * buffer slot i mod k, accumulate, advance).
- * member_stride_bytes >= row_pitch_bytes * height; row_pitch_bytes >=
- * width * element size; float32 rasters need 4-byte aligned pointer, pitch
- * and stride.  n_members == 0 is a no-op.  Errors: CPT_EINVAL (NULL members
+ * member_stride_bytes >= row_pitch_bytes * height; row_pitch_bytes >= the
+ * row's bytes (width x element size, or ceil(width / 8) for bit-packed
+ * masks); float32 rasters need 4-byte aligned pointer, pitch and stride.  n_members == 0 is a no-op.  Errors: CPT_EINVAL (NULL members
  * with n > 0, bad strides, N would exceed 65535 with count_bits 16),
  * CPT_ESTATE, CPT_ECUDA, CPT_ETIMEOUT. */
 int composite_add_members(composite_ctx *ctx, const void *members, int32_t n_members,

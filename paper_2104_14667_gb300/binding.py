@@ -29,6 +29,7 @@ STATUS_NAMES = {0: "CPT_OK", -1: "CPT_EINVAL", -2: "CPT_ENOMEM", -3: "CPT_ECUDA"
 CPT_READ_LINEAR, CPT_READ_TEXTURE, CPT_READ_TMA = 0, 1, 2
 READ_PATHS = {"linear": CPT_READ_LINEAR, "texture": CPT_READ_TEXTURE, "tma": CPT_READ_TMA}
 CPT_MODE_COUNT, CPT_MODE_MEAN_DEPTH = 0, 1
+CPT_MASK_BYTES, CPT_MASK_BITS = 0, 1
 
 HEADER = os.path.join(_build.INCLUDE, "composite.h")
 HEADERS = [os.path.join(_build.INCLUDE, h) for h in ("composite.h", "composite_engine.h", "composite_server.h")]
@@ -53,6 +54,7 @@ class Config(ctypes.Structure):
         ("wait_timeout_ms", ctypes.c_int64),
         ("host_read", ctypes.c_int32),
         ("tma_box_bytes", ctypes.c_int32),
+        ("mask_format", ctypes.c_int32),
     ]
 
 
@@ -270,7 +272,7 @@ def composite_oneshot_static(members, counts_out=None, bucket_out=None, rgba_out
 
 def make_config(read_path="linear", staging_buffers=2, chunk_members=16, count_bits=16,
                 mode="count", trace=False, pinned_ring_bytes=0, stream=None,
-                wait_timeout_ms=0, host_read=False, tma_box_bytes=0) -> Config:
+                wait_timeout_ms=0, host_read=False, tma_box_bytes=0, mask_format="bytes") -> Config:
     cfg = composite_default_config()
     cfg.read_path = READ_PATHS[read_path] if isinstance(read_path, str) else int(read_path)
     cfg.staging_buffers = staging_buffers
@@ -283,6 +285,8 @@ def make_config(read_path="linear", staging_buffers=2, chunk_members=16, count_b
     cfg.wait_timeout_ms = wait_timeout_ms
     cfg.host_read = 1 if host_read else 0
     cfg.tma_box_bytes = tma_box_bytes
+    cfg.mask_format = {"bytes": CPT_MASK_BYTES, "bits": CPT_MASK_BITS}[mask_format] \
+        if isinstance(mask_format, str) else int(mask_format)
     return cfg
 
 

@@ -56,8 +56,11 @@ struct composite_ctx {
     composite_config cfg{};
     int elem = 1;              // bytes per raster element
     int vec_px = 16;           // pixels per 16-byte group
-    int64_t pitch_px = 0;      // plane and staging row pitch, elements
+    int64_t pitch_px = 0;      // plane row pitch, elements
+    int64_t row_bytes = 0;     // bytes of one raster row as the caller lays it out (unpadded)
+    int64_t stage_pitch = 0;   // staging row pitch, bytes (a multiple of 16)
     int64_t member_bytes = 0;  // staging raster stride, bytes
+    bool bits = false;         // masks are bit-packed
     Plane plane{};
     int *flags = nullptr;      // device flags
     int *h_flags = nullptr;    // pinned copy of the flags
@@ -191,6 +194,10 @@ int check_config(const composite_config &c) {
     if (c.trace != 0 && c.trace != 1) return fail(nullptr, CPT_EINVAL, "trace must be 0 or 1");
     if (c.pinned_ring_bytes < 0 || c.wait_timeout_ms < 0) return fail(nullptr, CPT_EINVAL, "negative ring budget or timeout");
     if (c.host_read != 0 && c.host_read != 1) return fail(nullptr, CPT_EINVAL, "host_read must be 0 or 1");
+    if (c.mask_format != CPT_MASK_BYTES && c.mask_format != CPT_MASK_BITS)
+        return fail(nullptr, CPT_EINVAL, "mask_format %d out of range", c.mask_format);
+    if (c.mask_format == CPT_MASK_BITS && (c.mode != CPT_MODE_COUNT || c.read_path != CPT_READ_LINEAR))
+        return fail(nullptr, CPT_EINVAL, "bit-packed masks need CPT_MODE_COUNT and CPT_READ_LINEAR");
     if (c.tma_box_bytes != 0 && !cpt::tma_box_supported(c.tma_box_bytes))
         return fail(nullptr, CPT_EINVAL, "tma_box_bytes %d is not 0, 64, 128 or 256", c.tma_box_bytes);
     return CPT_OK;
@@ -307,6 +314,8 @@ int accumulate(composite_ctx *ctx, const RasterBatch &b, int sign) {
         if (r != 0) return fail(ctx, CPT_ECUDA, "cuTensorMapEncodeTiled failed (CUresult %d)", r);
         e = count ? cpt::launch_count_tma(map, b, ctx->plane, sign, ctx->flags, tns, box, ctx->caps, ctx->compute)
                   : cpt::launch_depth_tma(map, b, ctx->plane, sign, ctx->flags, tns, box, ctx->caps, ctx->compute);
+    } else if (ctx->bits) {
+        e = cpt::launch_count_bits(b, ctx->plane, sign, ctx->flags, ctx->caps, ctx->compute);
     } else {
         e = count ? cpt::launch_count_linear(b, ctx->plane, sign, ctx->flags, ctx->caps, ctx->compute)
                   : cpt::launch_depth_linear(b, ctx->plane, sign, ctx->flags, ctx->caps, ctx->compute);
@@ -345,11 +354,11 @@ int convert_to_array(composite_ctx *ctx, Slot &s, const void *src, int64_t pitch
 // Consumes one staged chunk on the compute stream.
 int consume_slot(composite_ctx *ctx, Slot &s, int c, int sign) {
     if (ctx->cfg.read_path == CPT_READ_TEXTURE) {
-        int rc = convert_to_array(ctx, s, s.stage, ctx->pitch_px * ctx->elem, c, ctx->compute);
+        int rc = convert_to_array(ctx, s, s.stage, ctx->stage_pitch, c, ctx->compute);
         if (rc) return rc;
         return accumulate_texture(ctx, s, c, sign);
     }
-    RasterBatch b{s.stage, ctx->member_bytes, ctx->pitch_px * ctx->elem, c};
+    RasterBatch b{s.stage, ctx->member_bytes, ctx->stage_pitch, c};
     return accumulate(ctx, b, sign);
 }
 
@@ -357,8 +366,8 @@ int consume_slot(composite_ctx *ctx, Slot &s, int c, int sign) {
 // row pitch pitch_px * elem and raster stride member_bytes.
 int upload(composite_ctx *ctx, uint8_t *dst, const uint8_t *src, int c, int64_t stride,
            int64_t pitch) {
-    const int64_t row = (int64_t)ctx->width * ctx->elem;
-    const int64_t dpitch = ctx->pitch_px * ctx->elem;
+    const int64_t row = ctx->row_bytes;
+    const int64_t dpitch = ctx->stage_pitch;
     const int64_t h = ctx->height;
     if (pitch == row && row == dpitch && stride == pitch * h) {
         CK(ctx, cudaMemcpyAsync(dst, src, (size_t)c * ctx->member_bytes, cudaMemcpyDefault, ctx->copy));
@@ -434,8 +443,8 @@ int run_ring(composite_ctx *ctx, const uint8_t *src, int n, int64_t stride, int6
         ctx->ring_chunk = chunk;
     }
     const int C = (int)ctx->ring_chunk;
-    const int64_t row = (int64_t)ctx->width * ctx->elem;
-    const int64_t dpitch = ctx->pitch_px * ctx->elem;
+    const int64_t row = ctx->row_bytes;
+    const int64_t dpitch = ctx->stage_pitch;
     for (int m0 = 0; m0 < n; m0 += C) {
         const int c = n - m0 < C ? n - m0 : C;
         Slot &s = next_slot(ctx);
@@ -476,8 +485,8 @@ int apply(composite_ctx *ctx, const void *members, int32_t n, int64_t stride, in
     if (n < 0) return fail(ctx, CPT_EINVAL, "n_members %d < 0", n);
     if (n == 0) return CPT_OK;
     if (!members) return fail(ctx, CPT_EINVAL, "members is NULL");
-    const int64_t row = (int64_t)ctx->width * ctx->elem;
-    if (pitch < row) return fail(ctx, CPT_EINVAL, "row_pitch_bytes %d < width * element size %lld", pitch, (long long)row);
+    const int64_t row = ctx->row_bytes;
+    if (pitch < row) return fail(ctx, CPT_EINVAL, "row_pitch_bytes %d < the row's %lld bytes", pitch, (long long)row);
     if (stride < (int64_t)pitch * ctx->height)
         return fail(ctx, CPT_EINVAL, "member_stride_bytes %lld < row_pitch_bytes * height", (long long)stride);
     if (ctx->elem == 4 && ((reinterpret_cast<uintptr_t>(members) | (uintptr_t)pitch | (uintptr_t)stride) & 3))
@@ -562,6 +571,7 @@ int composite_default_config(composite_config *cfg) {
     cfg->wait_timeout_ms = 0;
     cfg->host_read = 0;
     cfg->tma_box_bytes = 0;
+    cfg->mask_format = CPT_MASK_BYTES;
     return CPT_OK;
 }
 
@@ -585,7 +595,10 @@ int composite_begin(composite_ctx **out, int32_t width, int32_t height, const co
     ctx->elem = c.mode == CPT_MODE_COUNT ? 1 : 4;
     ctx->vec_px = 16 / ctx->elem;
     ctx->pitch_px = ((int64_t)width + ctx->vec_px - 1) / ctx->vec_px * ctx->vec_px;
-    ctx->member_bytes = ctx->pitch_px * ctx->elem * height;
+    ctx->bits = c.mask_format == CPT_MASK_BITS;
+    ctx->row_bytes = ctx->bits ? ((int64_t)width + 7) / 8 : (int64_t)width * ctx->elem;
+    ctx->stage_pitch = (ctx->row_bytes + 15) / 16 * 16;
+    ctx->member_bytes = ctx->stage_pitch * height;
     rc = setup(ctx);
     if (rc) {
         g_begin_error = ctx->err;

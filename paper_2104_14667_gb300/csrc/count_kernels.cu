@@ -75,6 +75,80 @@ count_linear_kernel(RasterBatch b, Plane p, int sign, int *flags, int64_t groups
     }
 }
 
+// Bit-packed masks: pixel x of a row is bit (x & 7) of byte x >> 3 of the
+// row.  A thread owns one 32-pixel word of a composite row (a warp reads 128
+// contiguous bytes per member) and keeps the slab's counts bit-sliced: bit i
+// of counter word j is bit j of pixel i's count, so adding a member's word is
+// a ripple-carry over eight words (two logic operations per level), 32
+// pixels at a time.  Eight levels hold counts up to 255, one slab.
+__device__ __forceinline__ void bitslice_add(uint32_t (&c)[8], uint32_t m) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const uint32_t carry = c[j] & m;
+        c[j] ^= m;
+        m = carry;
+    }
+}
+
+// Count of pixel i (0..31) from bit-sliced counters.
+__device__ __forceinline__ uint32_t bitslice_get(const uint32_t (&c)[8], int i) {
+    uint32_t v = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v |= ((c[j] >> i) & 1u) << j;
+    return v;
+}
+
+template <typename CountT>
+__global__ void __launch_bounds__(kThreads)
+count_bits_kernel(RasterBatch b, Plane p, int sign, int *flags, int64_t words, int words_per_row,
+                  int slab, int slabs) {
+    CountT *plane = static_cast<CountT *>(p.data);
+    const int64_t stride = b.member_stride;
+    const int64_t units = words * slabs;
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < units;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        const int sl = (int)(u / words);
+        const int64_t g = u - (int64_t)sl * words;
+        const int y = (int)(g / words_per_row);
+        const int gx = (int)(g - (int64_t)y * words_per_row);
+        const int x0 = gx * 32;
+        const int valid = min(32, p.width - x0);
+        const int m0 = sl * slab;
+        const int m1 = min(b.n, m0 + slab);
+        const uint8_t *q = static_cast<const uint8_t *>(b.base) + y * b.row_pitch + gx * 4 + (int64_t)m0 * stride;
+        uint32_t c[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+        if (valid == 32) {
+#pragma unroll 8
+            for (int m = m0; m < m1; ++m) {
+                bitslice_add(c, __ldcs(reinterpret_cast<const uint32_t *>(q)));
+                q += stride;
+            }
+        } else {
+            // ragged right edge: only the row's own bytes, bits past the width dropped
+            const int nbytes = (valid + 7) / 8;
+            const uint32_t keep = valid == 32 ? 0xFFFFFFFFu : ((1u << valid) - 1u);
+            for (int m = m0; m < m1; ++m, q += stride) {
+                uint32_t w = 0;
+                for (int k = 0; k < nbytes; ++k) w |= (uint32_t)q[k] << (8 * k);
+                bitslice_add(c, w & keep);
+            }
+        }
+        CountT *dst = plane + (int64_t)y * p.pitch + x0;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {           // two 16-pixel groups
+            uint32_t wide[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) wide[j] = bitslice_get(c, 16 * h + j);
+            const int v = min(16, valid - 16 * h);
+            if (v <= 0) break;
+            if (slabs == 1)
+                apply_count_group<CountT>(dst + 16 * h, v, wide, sign, flags);
+            else
+                atomic_count_group<CountT>(dst + 16 * h, wide, sign, flags);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kThreads)
 depth_linear_kernel(RasterBatch b, Plane p, int sign, int64_t groups, int groups_per_row) {
     float *plane = static_cast<float *>(p.data);
@@ -192,6 +266,26 @@ cudaError_t launch_count_linear(const RasterBatch &b, const Plane &p, int sign, 
         count_linear_kernel<uint16_t><<<grid, kThreads, 0, s>>>(b, p, sign, flags, groups, gpr, slab, (int)slabs);
     else
         count_linear_kernel<uint32_t><<<grid, kThreads, 0, s>>>(b, p, sign, flags, groups, gpr, slab, (int)slabs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_bits(const RasterBatch &b, const Plane &p, int sign, int *flags,
+                              const DeviceCaps &caps, cudaStream_t s) {
+    const int wpr = (p.width + 31) / 32;
+    const int64_t words = (int64_t)wpr * p.height;
+    if (b.n <= 0 || words == 0) return cudaSuccess;
+    // member slabs as in the byte kernel: at most 255 (eight counter levels)
+    const int64_t target_units = 8ll * caps.num_sms * 2048;
+    int64_t slabs = (b.n + kPackedLimit - 1) / kPackedLimit;
+    const int64_t want = std::min<int64_t>((target_units + words - 1) / words, (b.n + 31) / 32);
+    slabs = std::max<int64_t>(std::max<int64_t>(slabs, want), 1);
+    const int slab = (int)((b.n + slabs - 1) / slabs);
+    slabs = (b.n + slab - 1) / slab;
+    const unsigned grid = (unsigned)blocks_for(words * slabs);
+    if (p.count_bits == 16)
+        count_bits_kernel<uint16_t><<<grid, kThreads, 0, s>>>(b, p, sign, flags, words, wpr, slab, (int)slabs);
+    else
+        count_bits_kernel<uint32_t><<<grid, kThreads, 0, s>>>(b, p, sign, flags, words, wpr, slab, (int)slabs);
     return cudaGetLastError();
 }
 

@@ -40,6 +40,10 @@ cudaError_t launch_count_linear(const RasterBatch &b, const Plane &p, int sign, 
                                 const DeviceCaps &caps, cudaStream_t s);
 cudaError_t launch_depth_linear(const RasterBatch &b, const Plane &p, int sign, int *flags,
                                 const DeviceCaps &caps, cudaStream_t s);
+// Bit-packed masks (pixel x = bit x & 7 of byte x >> 3 of its row); the
+// plane pitch must be a multiple of 32 pixels.
+cudaError_t launch_count_bits(const RasterBatch &b, const Plane &p, int sign, int *flags,
+                              const DeviceCaps &caps, cudaStream_t s);
 
 // Texture read path: a layered cudaArray with 16-byte texels (uint4 for
 // masks, float4 for depths); n_layers members.

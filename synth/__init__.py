@@ -213,6 +213,12 @@ def fill_depths_torch(ens: Ensemble, out, members: range | None = None, terrain_
     return out
 
 
+def pack_masks(m: np.ndarray) -> np.ndarray:
+    """Bit-packed copy of uint8[..., H, W] masks: uint8[..., H, ceil(W/8)],
+    pixel x in bit (x & 7) of byte x >> 3, any nonzero byte a 1 bit."""
+    return np.packbits(np.asarray(m) != 0, axis=-1, bitorder="little")
+
+
 def masks(ens: Ensemble) -> np.ndarray:
     """uint8[N, H, W] masks with values in {0, 1}."""
     return fill_masks(ens, np.empty((ens.n, ens.height, ens.width), dtype=np.uint8))

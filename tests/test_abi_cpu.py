@@ -30,7 +30,7 @@ def test_library_exports_every_declared_symbol(lib):
 def test_default_config(lib):
     cfg = binding.composite_default_config()
     assert (cfg.read_path, cfg.staging_buffers, cfg.chunk_members, cfg.count_bits, cfg.mode) == (0, 2, 16, 16, 0)
-    assert ctypes.sizeof(binding.Config) == 56
+    assert ctypes.sizeof(binding.Config) == 64
 
 
 @pytest.mark.parametrize("w,h", [(0, 5), (5, 0), (-1, 3)])
@@ -44,7 +44,7 @@ def test_begin_rejects_empty_raster(lib, w, h):
                                          ("chunk_members", 0), ("chunk_members", 256), ("count_bits", 8),
                                          ("mode", 2), ("trace", 2), ("wait_timeout_ms", -1),
                                          ("host_read", 2), ("tma_box_bytes", 32),
-                                         ("tma_box_bytes", 512)])
+                                         ("tma_box_bytes", 512), ("mask_format", 2)])
 def test_begin_rejects_bad_config(lib, field, value):
     cfg = binding.composite_default_config()
     setattr(cfg, field, value)
@@ -87,3 +87,13 @@ def test_engine_defaults_and_no_gpu(lib):
     if not torch.cuda.is_available():
         with pytest.raises(binding.CompositeError):
             binding.Engine()
+
+
+def test_bit_packed_masks_need_count_mode_and_linear_path(lib):
+    for field, value in (("mode", 1), ("read_path", 1), ("read_path", 2)):
+        cfg = binding.composite_default_config()
+        cfg.mask_format = binding.CPT_MASK_BITS
+        setattr(cfg, field, value)
+        with pytest.raises(binding.CompositeError) as e:
+            binding.composite_begin(64, 8, cfg)
+        assert e.value.code == binding.CPT_EINVAL

@@ -280,3 +280,33 @@ def test_tma_box_widths(box, mode, w, h, n):
         else:
             got = comp.render_host()["mean"]
             assert np.abs(got.astype(np.float64) - oracle.mean_depth(m)).max() <= 1e-5 * n
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("w,h,n", [(1024, 1024, 16), (13, 7, 5), (33, 9, 40), (100, 37, 300), (4097, 3, 9), (1, 1, 3)])
+def test_bit_packed_masks(kind, w, h, n):
+    m = synth.scramble_nonzero(synth.random_masks(90 + w, n, h, w, density=0.4), 90)
+    packed = synth.pack_masks(m)
+    assert packed.shape == (n, h, (w + 7) // 8)
+    with binding.Composite(w, h, mask_format="bits", chunk_members=16) as comp:
+        comp.add(as_kind(packed, kind))
+        check_counts(comp, m)
+
+
+@pytest.mark.parametrize("k,c", [(1, 3), (2, 255), (3, 16)])
+def test_bit_packed_add_remove_and_32bit(k, c):
+    w, h = 77, 45
+    a = synth.random_masks(95, 120, h, w)
+    b = synth.random_masks(96, 30, h, w)
+    with binding.Composite(w, h, mask_format="bits", staging_buffers=k, chunk_members=c, count_bits=32) as comp:
+        comp.add(as_kind(synth.pack_masks(a), "pinned"))
+        comp.add(as_kind(synth.pack_masks(b), "device"))
+        comp.remove(as_kind(synth.pack_masks(a), "pageable"))
+        check_counts(comp, b)
+        # a sparse composite: removing a dense member that was never added underflows
+        comp.clear()
+        comp.add(as_kind(synth.pack_masks(synth.random_masks(97, 3, h, w, density=0.05)), "device"))
+        comp.remove(as_kind(synth.pack_masks(a[:1]), "device"))
+        with pytest.raises(binding.CompositeError) as e:
+            comp.render_host()
+        assert e.value.code == binding.CPT_EUNDERFLOW

@@ -115,3 +115,13 @@ def test_torch_fills_match_numpy_generator():
     d = torch.empty((5, 50, 70), dtype=torch.float32)
     synth.fill_depths_torch(ens, d)
     np.testing.assert_array_equal(d.numpy(), synth.depths(ens))
+
+
+def test_pack_masks_round_trip_and_bit_order():
+    m = synth.scramble_nonzero(synth.random_masks(3, 4, 5, 19), 3)
+    p = synth.pack_masks(m)
+    assert p.shape == (4, 5, 3)
+    np.testing.assert_array_equal(np.unpackbits(p, axis=-1, bitorder="little")[..., :19], (m != 0).astype(np.uint8))
+    one = np.zeros((1, 1, 9), np.uint8)
+    one[0, 0, 8] = 7          # pixel 8 -> bit 0 of byte 1
+    np.testing.assert_array_equal(synth.pack_masks(one)[0, 0], [0, 1])

@@ -59,7 +59,8 @@ def parse_args():
                    help="target CPU time of the oracle baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--sweep", choices=["readpath", "layout", "streaming", "tiny", "batched", "serving"],
+    p.add_argument("--sweep", choices=["readpath", "layout", "streaming", "tiny", "batched", "serving",
+                                       "compressed"],
                    default=None,
                    help="print one JSON line per point of a workload sweep instead of the bench line")
     p.add_argument("--resident", type=int, default=2048, help="serving: members resident in HBM")
@@ -762,6 +763,64 @@ def sweep_serving(args, torch, binding, device, stream):
                           "p99_gain": single["p99_ms"] / batched["p99_ms"]}), flush=True)
 
 
+def sweep_compressed(args, torch, binding, device, stream):
+    """Bit-packed masks (one bit per pixel) against byte masks on the same
+    4096x4096 x 1024 ensemble: device resident (HBM bytes per member-pixel
+    1/8) and streamed from pinned host memory (link bytes 1/8)."""
+    import synth
+    W, H, N = args.width, args.height, args.members
+    P = W * H
+    ens = synth.ensemble(args.seed, W, H, N)
+    tdev = torch.from_numpy(ens.terrain).to(device)
+    dev = torch.empty((N, H, W), dtype=torch.uint8, device=device)
+    synth.fill_masks_torch(ens, dev, terrain_t=tdev)
+    packed = torch.empty((N, H, W // 8), dtype=torch.uint8, device=device)
+    for m0 in range(0, N, 64):
+        packed[m0:m0 + 64] = synth.pack_masks_torch(dev[m0:m0 + 64])
+    peaks, _ = measured_peaks()
+    out = {"sweep": "compressed", "width": W, "height": H, "members": N}
+    counts = {}
+    for fmt, data in (("bytes", dev), ("bits", packed)):
+        with binding.Composite(W, H, stream=stream.cuda_stream, mask_format=fmt) as comp:
+            def step():
+                comp.clear()
+                comp.add(data)
+            ms = _timed(torch, stream, step, args.steps, args.warmup)
+            c = np.empty((H, W), np.uint16)
+            comp.render(counts_out=c)
+            counts[fmt] = c
+        bytes_per = 1.0 if fmt == "bytes" else 0.125
+        out[f"resident_{fmt}_ms"] = ms
+        out[f"resident_{fmt}_member_px_per_s"] = N * P / (ms * 1e-3)
+        out[f"resident_{fmt}_read_gbs"] = (N * P * bytes_per + 4 * P) / (ms * 1e-3) / 1e9
+        out[f"resident_{fmt}_frac_of_hbm"] = out[f"resident_{fmt}_read_gbs"] / peaks["hbm_gbs"]
+    out["counts_identical"] = bool(np.array_equal(counts["bytes"], counts["bits"]))
+    host_packed = torch.empty((N, H, W // 8), dtype=torch.uint8, pin_memory=True)
+    host_packed.copy_(packed)
+    del dev
+    torch.cuda.empty_cache()
+    h_bucket = np.empty((H, W), np.uint8)
+    h_rgba = np.empty((H, W, 4), np.uint8)
+    for host_read in (False, True):
+        with binding.Composite(W, H, stream=stream.cuda_stream, mask_format="bits", chunk_members=255,
+                               staging_buffers=args.staging, host_read=host_read) as comp:
+            def host_step():
+                comp.clear()
+                comp.add(host_packed)
+                comp.render(bucket_out=h_bucket, rgba_out=h_rgba)
+            for _ in range(args.warmup):
+                host_step()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                host_step()
+            ms = 1e3 * (time.perf_counter() - t0) / args.steps
+        key = "streamed_bits_host_read" if host_read else "streamed_bits_staged"
+        out[f"{key}_ms"] = ms
+        out[f"{key}_member_px_per_s"] = N * P / (ms * 1e-3)
+        out[f"{key}_link_gbs"] = N * P / 8 / (ms * 1e-3) / 1e9
+    print(json.dumps(out), flush=True)
+
+
 def run_sweep(args):
     import torch
     from paper_2104_14667_gb300 import binding
@@ -779,6 +838,8 @@ def run_sweep(args):
     elif args.sweep == "streaming":
         sweep_streaming(args, torch, binding, device, stream, chunks=[1, 2, 4, 8, 16, 64, 128],
                         stagings=[1, 3, 4])
+    elif args.sweep == "compressed":
+        sweep_compressed(args, torch, binding, device, stream)
     elif args.sweep == "serving":
         sweep_serving(args, torch, binding, device, stream)
     elif args.sweep == "batched":

@@ -77,24 +77,57 @@ count_linear_kernel(RasterBatch b, Plane p, int sign, int *flags, int64_t groups
 
 // Bit-packed masks: pixel x of a row is bit (x & 7) of byte x >> 3 of the
 // row.  A thread owns one 32-pixel word of a composite row (a warp reads 128
-// contiguous bytes per member) and keeps the slab's counts bit-sliced: bit i
-// of counter word j is bit j of pixel i's count, so adding a member's word is
-// a ripple-carry over eight words (two logic operations per level), 32
-// pixels at a time.  Eight levels hold counts up to 255, one slab.
-__device__ __forceinline__ void bitslice_add(uint32_t (&c)[8], uint32_t m) {
+// contiguous bytes per member) and keeps the slab's counts bit-sliced, as
+// carry-save accumulators in the manner of the Harley-Seal population count:
+// bit i of `ones`, `twos`, `fours`, `eights` holds one bit of weight 1, 2, 4,
+// 8 of pixel i's count, and every 16 members the weight-16 carries ripple
+// into a 4-level counter `hi` (counts stay below 256, one slab).  Sixteen
+// members cost 15 carry-save adders (5 logic operations each) plus the
+// ripple, about 5 operations per word instead of 16 for a plain ripple-carry
+// counter.
+struct BitCounter {
+    uint32_t ones = 0, twos = 0, fours = 0, eights = 0;
+    uint32_t hi[4] = {0u, 0u, 0u, 0u};
+};
+
+// Carry-save adder: a + b + c = 2 * h + l, bitwise.
+__device__ __forceinline__ void csa(uint32_t &h, uint32_t &l, uint32_t a, uint32_t b, uint32_t c) {
+    const uint32_t u = a ^ b;
+    h = (a & b) | (u & c);
+    l = u ^ c;
+}
+
+__device__ __forceinline__ void bitcount_add16(BitCounter &s, const uint32_t (&w)[16]) {
+    uint32_t twos_a, twos_b, fours_a, fours_b, eights_a, eights_b, sixteens;
+    csa(twos_a, s.ones, s.ones, w[0], w[1]);
+    csa(twos_b, s.ones, s.ones, w[2], w[3]);
+    csa(fours_a, s.twos, s.twos, twos_a, twos_b);
+    csa(twos_a, s.ones, s.ones, w[4], w[5]);
+    csa(twos_b, s.ones, s.ones, w[6], w[7]);
+    csa(fours_b, s.twos, s.twos, twos_a, twos_b);
+    csa(eights_a, s.fours, s.fours, fours_a, fours_b);
+    csa(twos_a, s.ones, s.ones, w[8], w[9]);
+    csa(twos_b, s.ones, s.ones, w[10], w[11]);
+    csa(fours_a, s.twos, s.twos, twos_a, twos_b);
+    csa(twos_a, s.ones, s.ones, w[12], w[13]);
+    csa(twos_b, s.ones, s.ones, w[14], w[15]);
+    csa(fours_b, s.twos, s.twos, twos_a, twos_b);
+    csa(eights_b, s.fours, s.fours, fours_a, fours_b);
+    csa(sixteens, s.eights, s.eights, eights_a, eights_b);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const uint32_t carry = c[j] & m;
-        c[j] ^= m;
-        m = carry;
+    for (int j = 0; j < 4; ++j) {
+        const uint32_t carry = s.hi[j] & sixteens;
+        s.hi[j] ^= sixteens;
+        sixteens = carry;
     }
 }
 
-// Count of pixel i (0..31) from bit-sliced counters.
-__device__ __forceinline__ uint32_t bitslice_get(const uint32_t (&c)[8], int i) {
-    uint32_t v = 0;
+// Count of pixel i (0..31).
+__device__ __forceinline__ uint32_t bitcount_get(const BitCounter &s, int i) {
+    uint32_t v = ((s.ones >> i) & 1u) | (((s.twos >> i) & 1u) << 1) | (((s.fours >> i) & 1u) << 2) |
+                 (((s.eights >> i) & 1u) << 3);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) v |= ((c[j] >> i) & 1u) << j;
+    for (int j = 0; j < 4; ++j) v += ((s.hi[j] >> i) & 1u) << (4 + j);
     return v;
 }
 
@@ -116,31 +149,37 @@ count_bits_kernel(RasterBatch b, Plane p, int sign, int *flags, int64_t words, i
         const int m0 = sl * slab;
         const int m1 = min(b.n, m0 + slab);
         const uint8_t *q = static_cast<const uint8_t *>(b.base) + y * b.row_pitch + gx * 4 + (int64_t)m0 * stride;
-        uint32_t c[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
-        if (valid == 32) {
-#pragma unroll 8
-            for (int m = m0; m < m1; ++m) {
-                bitslice_add(c, __ldcs(reinterpret_cast<const uint32_t *>(q)));
-                q += stride;
+        const int nbytes = (valid + 7) / 8;
+        const uint32_t keep = valid == 32 ? 0xFFFFFFFFu : ((1u << valid) - 1u);
+        BitCounter acc;
+        for (int m = m0; m < m1; m += 16) {
+            uint32_t w[16];
+            const int take = min(16, m1 - m);
+            if (valid == 32) {
+#pragma unroll
+                for (int k = 0; k < 16; ++k)
+                    w[k] = k < take ? __ldcs(reinterpret_cast<const uint32_t *>(q + k * stride)) : 0u;
+            } else {
+                // ragged right edge: only the row's own bytes, bits past the width dropped
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    uint32_t v = 0;
+                    if (k < take)
+                        for (int i = 0; i < nbytes; ++i) v |= (uint32_t)q[k * stride + i] << (8 * i);
+                    w[k] = v & keep;
+                }
             }
-        } else {
-            // ragged right edge: only the row's own bytes, bits past the width dropped
-            const int nbytes = (valid + 7) / 8;
-            const uint32_t keep = valid == 32 ? 0xFFFFFFFFu : ((1u << valid) - 1u);
-            for (int m = m0; m < m1; ++m, q += stride) {
-                uint32_t w = 0;
-                for (int k = 0; k < nbytes; ++k) w |= (uint32_t)q[k] << (8 * k);
-                bitslice_add(c, w & keep);
-            }
+            bitcount_add16(acc, w);
+            q += 16 * stride;
         }
         CountT *dst = plane + (int64_t)y * p.pitch + x0;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {           // two 16-pixel groups
-            uint32_t wide[16];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) wide[j] = bitslice_get(c, 16 * h + j);
             const int v = min(16, valid - 16 * h);
             if (v <= 0) break;
+            uint32_t wide[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) wide[j] = bitcount_get(acc, 16 * h + j);
             if (slabs == 1)
                 apply_count_group<CountT>(dst + 16 * h, v, wide, sign, flags);
             else

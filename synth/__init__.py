@@ -219,6 +219,18 @@ def pack_masks(m: np.ndarray) -> np.ndarray:
     return np.packbits(np.asarray(m) != 0, axis=-1, bitorder="little")
 
 
+def pack_masks_torch(m):
+    """pack_masks for a torch uint8[n, H, W] tensor with W a multiple of 8, on
+    its own device: the same bit layout."""
+    import torch
+    n, h, w = m.shape
+    if w % 8:
+        raise ValueError("width must be a multiple of 8")
+    shifts = torch.arange(8, device=m.device, dtype=torch.uint8)
+    bits = (m.reshape(n, h, w // 8, 8) != 0).to(torch.uint8) << shifts
+    return bits.sum(dim=-1, dtype=torch.uint8)
+
+
 def masks(ens: Ensemble) -> np.ndarray:
     """uint8[N, H, W] masks with values in {0, 1}."""
     return fill_masks(ens, np.empty((ens.n, ens.height, ens.width), dtype=np.uint8))

@@ -125,3 +125,9 @@ def test_pack_masks_round_trip_and_bit_order():
     one = np.zeros((1, 1, 9), np.uint8)
     one[0, 0, 8] = 7          # pixel 8 -> bit 0 of byte 1
     np.testing.assert_array_equal(synth.pack_masks(one)[0, 0], [0, 1])
+
+
+def test_pack_masks_torch_matches_numpy():
+    torch = __import__("pytest").importorskip("torch")
+    m = synth.scramble_nonzero(synth.random_masks(4, 3, 6, 24), 4)
+    np.testing.assert_array_equal(synth.pack_masks_torch(torch.from_numpy(m)).numpy(), synth.pack_masks(m))

@@ -10,6 +10,7 @@ Definitions (Johnson & Jankun-Kelly; Fig. 1 caption, Figs. 2-3, Section 4):
 * ``count(p) = sum_m [mask_m(p) != 0]``  -- the per-member accumulation
 * ``bucket(p) = floor(255 * count(p) / N)`` (0 when N = 0)  -- overlap class
 * ``rgba(p) = LUT[bucket(p)]``  -- blue saturation colour map
+* ``hist[b] = #{p : bucket(p) = b}``  -- frequency of overlap classes
 * ``mean(p) = sum_m d_m(p) / N`` in FP64  -- mean-depth composite
 
 Parity pins (tests/test_oracle_pins.py): nested-threshold identity against
@@ -63,6 +64,8 @@ def _load():
             lib.oracle_bucket.argtypes = [_i64p, ctypes.c_int64, ctypes.c_int64, _u8p]
             lib.oracle_rgba.restype = None
             lib.oracle_rgba.argtypes = [_u8p, _u8p, ctypes.c_int64, _u8p]
+            lib.oracle_histogram.restype = None
+            lib.oracle_histogram.argtypes = [_u8p, ctypes.c_int64, ctypes.POINTER(ctypes.c_uint64)]
             lib.oracle_default_lut.restype = None
             lib.oracle_default_lut.argtypes = [_u8p]
             lib.oracle_depth_apply.restype = None
@@ -124,6 +127,15 @@ def bucket(counts: np.ndarray, n_members: int) -> np.ndarray:
     if _load().oracle_bucket(_ptr(c, ctypes.c_int64), int(n_members), c.size,
                              _ptr(out, ctypes.c_uint8)) != 0:
         raise ValueError("a count lies outside [0, N]")
+    return out
+
+
+def histogram(buckets: np.ndarray) -> np.ndarray:
+    """uint64[256] number of pixels in every overlap class (Fig. 1 caption:
+    the histogram of overlap-class frequencies)."""
+    b = np.ascontiguousarray(buckets, dtype=np.uint8)
+    out = np.empty(256, dtype=np.uint64)
+    _load().oracle_histogram(_ptr(b, ctypes.c_uint8), b.size, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
     return out
 
 
@@ -211,4 +223,4 @@ class Composite:
         if self.underflow:
             raise ValueError("a remove took away a member that was never added")
         b = bucket(self.counts, self.n)
-        return {"counts": self.counts.copy(), "bucket": b, "rgba": rgba(b, lut)}
+        return {"counts": self.counts.copy(), "bucket": b, "rgba": rgba(b, lut), "histogram": histogram(b)}

@@ -13,6 +13,7 @@
  *                                                step 4, applied once per member)
  *   bucket(p)  = N == 0 ? 0 : floor(255 * count(p) / N)   (overlap class, Fig. 1 caption)
  *   rgba(p)    = LUT[bucket(p)]                 (blue saturation map, Fig. 1 caption)
+ *   hist[b]    = #{p : bucket(p) == b}          (frequency of overlap classes, Fig. 1 caption)
  *   mean(p)    = (1/N) sum over m in S of d_m(p), FP64, N = 0 => 0  (mean-depth composite)
  * Members may be added and removed in any order (the interactive list of
  * Fig. 1); the state after any sequence equals a recompute over the final S.
@@ -76,6 +77,17 @@ void oracle_rgba(const uint8_t *bucket, const uint8_t *lut, int64_t npix,
     for (p = 0; p < npix; ++p)
         for (c = 0; c < 4; ++c)
             rgba[4 * p + c] = lut[4 * (int64_t)bucket[p] + c];
+}
+
+/* hist[b] = number of pixels whose overlap class is b, b = 0..255. */
+void oracle_histogram(const uint8_t *bucket, int64_t npix, uint64_t *hist)
+{
+    int64_t p;
+    int b;
+    for (b = 0; b < 256; ++b)
+        hist[b] = 0;
+    for (p = 0; p < npix; ++p)
+        hist[bucket[p]] += 1;
 }
 
 /* The default colour table: bucket b -> (255-b, 255-b, 255, 255), white at

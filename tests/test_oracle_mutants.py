@@ -34,6 +34,7 @@ MUTANTS = {
     "mean_divides_by_n_minus_1": ("sums[p] / (double)n_members", "sums[p] / (double)(n_members - 1 + (n_members == 1))"),
     "depth_drops_sign": ("sums[y * width + x] += (double)sign * (double)row[x];",
                          "sums[y * width + x] += (double)row[x];"),
+    "histogram_skips_class_zero": ("        hist[bucket[p]] += 1;", "        hist[bucket[p]] += bucket[p] != 0;"),
 }
 
 PINS = [
@@ -53,6 +54,8 @@ PINS = [
     pins.test_mean_depth_against_exact_rationals,
     pins.test_mean_depth_special_cases,
     pins.test_mean_depth_add_then_remove,
+    pins.test_histogram_counts_every_pixel_once,
+    pins.test_histogram_closed_forms,
 ]
 
 
@@ -85,7 +88,7 @@ def test_pins_reject_mutant(tmp_path, name, monkeypatch):
     real = oracle._load()
     mutant = ctypes.CDLL(str(so))
     for fn in ("oracle_count_apply", "oracle_bucket", "oracle_rgba", "oracle_default_lut",
-               "oracle_depth_apply", "oracle_mean"):
+               "oracle_depth_apply", "oracle_mean", "oracle_histogram"):
         getattr(mutant, fn).restype = getattr(real, fn).restype
         getattr(mutant, fn).argtypes = getattr(real, fn).argtypes
     monkeypatch.setattr(oracle, "_lib", mutant)

@@ -199,3 +199,26 @@ def test_mean_depth_add_then_remove():
     np.testing.assert_allclose(c.render()["mean"], oracle.mean_depth(b), rtol=0, atol=1e-12)
     empty = oracle.Composite(7, 6, mode="mean_depth")
     np.testing.assert_array_equal(empty.render()["mean"], np.zeros((6, 7)))
+
+
+def test_histogram_counts_every_pixel_once():
+    rng = np.random.default_rng(9)
+    b = rng.integers(0, 256, (37, 53), dtype=np.uint8)
+    h = oracle.histogram(b)
+    assert int(h.sum()) == b.size
+    np.testing.assert_array_equal(h, np.bincount(b.ravel(), minlength=256))
+
+
+def test_histogram_closed_forms():
+    h, w, n = 11, 17, 5
+    zero = oracle.Composite(w, h)
+    assert zero.render()["histogram"][0] == h * w and zero.render()["histogram"][1:].sum() == 0
+    full = oracle.Composite(w, h)
+    full.add(np.ones((n, h, w), np.uint8))
+    hist = full.render()["histogram"]
+    assert hist[255] == h * w and hist[:255].sum() == 0
+    half = oracle.Composite(w, h)
+    m = synth.random_masks(5, 1, h, w)
+    half.add(np.concatenate([m, np.ones((1, h, w), np.uint8)]))     # counts 1 or 2 of N = 2
+    hist = half.render()["histogram"]
+    assert hist[255] == int(m.sum()) and hist[127] == h * w - int(m.sum())

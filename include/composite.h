@@ -168,6 +168,16 @@ int composite_render(composite_ctx *ctx, void *counts_out, uint8_t *bucket_out,
                      uint8_t *rgba_out, float *mean_out, int32_t out_on_device,
                      const uint8_t *lut_rgba);
 
+/* As composite_render (COUNT mode), and in the same pass the histogram of
+ * overlap classes (Fig. 1 caption: the frequency of the overlap classes,
+ * the distribution of flood occurrences): histogram_out[b] = number of
+ * pixels whose class is b, b = 0..255, 256 x uint64, in device memory when
+ * out_on_device = 1 (8-byte aligned) else host memory.  histogram_out must
+ * not be NULL; the other outputs may be. */
+int composite_render_histogram(composite_ctx *ctx, void *counts_out, uint8_t *bucket_out,
+                               uint8_t *rgba_out, uint64_t *histogram_out, int32_t out_on_device,
+                               const uint8_t *lut_rgba);
+
 /* Waits (bounded) until every queued copy and kernel of the context has
  * finished; returns CPT_EUNDERFLOW if a remove underflowed, CPT_ETIMEOUT if
  * the wait ran out, and ends the borrow of every member passed so far. */

@@ -85,6 +85,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
             "composite_add_members": (ctypes.c_int, [vp, vp, i32, i64, i32]),
             "composite_remove_members": (ctypes.c_int, [vp, vp, i32, i64, i32]),
             "composite_render": (ctypes.c_int, [vp, vp, vp, vp, vp, i32, vp]),
+            "composite_render_histogram": (ctypes.c_int, [vp, vp, vp, vp, vp, i32, vp]),
             "composite_sync": (ctypes.c_int, [vp]),
             "composite_member_count": (ctypes.c_int, [vp, ctypes.POINTER(i64)]),
             "composite_trace_read": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_float), i32,
@@ -221,6 +222,19 @@ def composite_render(ctx, counts_out=None, bucket_out=None, rgba_out=None, mean_
     _check(lib, ctx, rc)
 
 
+def composite_render_histogram(ctx, histogram_out, counts_out=None, bucket_out=None, rgba_out=None,
+                               lut=None) -> None:
+    lib = load()
+    on_dev = _on_device(histogram_out, counts_out, bucket_out, rgba_out)
+    lut_arr = None
+    if lut is not None:
+        lut_arr = np.ascontiguousarray(np.asarray(lut, dtype=np.uint8).reshape(256, 4))
+    rc = lib.composite_render_histogram(ctx, _ptr(counts_out), _ptr(bucket_out), _ptr(rgba_out),
+                                        _ptr(histogram_out), on_dev,
+                                        lut_arr.ctypes.data if lut_arr is not None else None)
+    _check(lib, ctx, rc)
+
+
 def composite_sync(ctx) -> None:
     lib = load()
     _check(lib, ctx, lib.composite_sync(ctx))
@@ -318,6 +332,11 @@ class Composite:
     def render(self, counts_out=None, bucket_out=None, rgba_out=None, mean_out=None, lut=None):
         composite_render(self.ctx, counts_out, bucket_out, rgba_out, mean_out, lut)
         if not _on_device(counts_out, bucket_out, rgba_out, mean_out):
+            self._borrowed.clear()
+
+    def render_histogram(self, histogram_out, counts_out=None, bucket_out=None, rgba_out=None, lut=None):
+        composite_render_histogram(self.ctx, histogram_out, counts_out, bucket_out, rgba_out, lut)
+        if not _on_device(histogram_out, counts_out, bucket_out, rgba_out):
             self._borrowed.clear()
 
     def render_host(self, lut=None) -> dict:

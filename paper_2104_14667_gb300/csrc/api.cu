@@ -634,20 +634,24 @@ int composite_remove_members(composite_ctx *ctx, const void *members, int32_t n_
     return apply(ctx, members, n_members, member_stride_bytes, row_pitch_bytes, -1);
 }
 
-int composite_render(composite_ctx *ctx, void *counts_out, uint8_t *bucket_out, uint8_t *rgba_out,
-                     float *mean_out, int32_t out_on_device, const uint8_t *lut_rgba) {
+}  // extern "C"
+
+namespace {
+
+int render(composite_ctx *ctx, void *counts_out, uint8_t *bucket_out, uint8_t *rgba_out, float *mean_out,
+           uint64_t *hist_out, int32_t out_on_device, const uint8_t *lut_rgba) {
     if (!ctx) return CPT_EINVAL;
     ctx->err.clear();
     if (ctx->poisoned) return fail(ctx, CPT_ESTATE, "context poisoned by an earlier underflow; clear it");
     const bool count = ctx->cfg.mode == CPT_MODE_COUNT;
     if (count && mean_out) return fail(ctx, CPT_EINVAL, "mean_out needs CPT_MODE_MEAN_DEPTH");
-    if (!count && (counts_out || bucket_out || rgba_out))
-        return fail(ctx, CPT_EINVAL, "counts, buckets and colours need CPT_MODE_COUNT");
+    if (!count && (counts_out || bucket_out || rgba_out || hist_out))
+        return fail(ctx, CPT_EINVAL, "counts, buckets, colours and histograms need CPT_MODE_COUNT");
     if (out_on_device != 0 && out_on_device != 1) return fail(ctx, CPT_EINVAL, "out_on_device must be 0 or 1");
     if (out_on_device) {
         const uintptr_t cbytes = count ? (uintptr_t)(ctx->cfg.count_bits / 8) : 1;
         if ((reinterpret_cast<uintptr_t>(counts_out) % cbytes) || (reinterpret_cast<uintptr_t>(rgba_out) % 4) ||
-            (reinterpret_cast<uintptr_t>(mean_out) % 4))
+            (reinterpret_cast<uintptr_t>(mean_out) % 4) || (reinterpret_cast<uintptr_t>(hist_out) % 8))
             return fail(ctx, CPT_EINVAL, "device outputs must be aligned to their element size");
     }
     const Lut lut = lut_rgba ? pack_lut(lut_rgba) : ctx->default_lut;
@@ -657,7 +661,8 @@ int composite_render(composite_ctx *ctx, void *counts_out, uint8_t *bucket_out, 
 
     if (out_on_device) {
         cudaError_t e = count ? cpt::launch_render_counts(ctx->plane, n, counts_out, bucket_out,
-                                                          reinterpret_cast<uint32_t *>(rgba_out), lut, ctx->caps, ctx->compute)
+                                                          reinterpret_cast<uint32_t *>(rgba_out), lut, ctx->caps,
+                                                          ctx->compute, hist_out)
                               : cpt::launch_render_mean(ctx->plane, n, mean_out, ctx->caps, ctx->compute);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "render kernel launch");
         return CPT_OK;
@@ -665,7 +670,8 @@ int composite_render(composite_ctx *ctx, void *counts_out, uint8_t *bucket_out, 
 
     // scratch regions start on 256-byte boundaries (uint32 colour stores)
     auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
-    const size_t need = count ? up((size_t)px * cb) + up((size_t)px) + up((size_t)px * 4) : up((size_t)px * 4);
+    const size_t need = count ? up((size_t)px * cb) + up((size_t)px) + up((size_t)px * 4) + 256 * sizeof(uint64_t)
+                              : up((size_t)px * 4);
     if (ctx->out_scratch_bytes < need) {
         if (ctx->out_scratch) {
             CK(ctx, cudaStreamSynchronize(ctx->compute));
@@ -680,11 +686,13 @@ int composite_render(composite_ctx *ctx, void *counts_out, uint8_t *bucket_out, 
         uint8_t *d_counts = ctx->out_scratch;
         uint8_t *d_bucket = d_counts + up((size_t)px * cb);
         uint8_t *d_rgba = d_bucket + up((size_t)px);
+        uint64_t *d_hist = reinterpret_cast<uint64_t *>(d_rgba + up((size_t)px * 4));
         cudaError_t e = cpt::launch_render_counts(ctx->plane, n, counts_out ? d_counts : nullptr,
                                                   bucket_out ? d_bucket : nullptr,
                                                   rgba_out ? reinterpret_cast<uint32_t *>(d_rgba) : nullptr,
-                                                  lut, ctx->caps, ctx->compute);
+                                                  lut, ctx->caps, ctx->compute, hist_out ? d_hist : nullptr);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "render kernel launch");
+        if (hist_out) CK(ctx, cudaMemcpyAsync(hist_out, d_hist, 256 * sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->compute));
         if (counts_out) CK(ctx, cudaMemcpyAsync(counts_out, d_counts, (size_t)px * cb, cudaMemcpyDeviceToHost, ctx->compute));
         if (bucket_out) CK(ctx, cudaMemcpyAsync(bucket_out, d_bucket, (size_t)px, cudaMemcpyDeviceToHost, ctx->compute));
         if (rgba_out) CK(ctx, cudaMemcpyAsync(rgba_out, d_rgba, (size_t)px * 4, cudaMemcpyDeviceToHost, ctx->compute));
@@ -697,6 +705,21 @@ int composite_render(composite_ctx *ctx, void *counts_out, uint8_t *bucket_out, 
     int rc = wait_all(ctx);
     if (rc) return rc;
     return check_flags(ctx);
+}
+
+}  // namespace
+
+extern "C" {
+
+int composite_render(composite_ctx *ctx, void *counts_out, uint8_t *bucket_out, uint8_t *rgba_out,
+                     float *mean_out, int32_t out_on_device, const uint8_t *lut_rgba) {
+    return render(ctx, counts_out, bucket_out, rgba_out, mean_out, nullptr, out_on_device, lut_rgba);
+}
+
+int composite_render_histogram(composite_ctx *ctx, void *counts_out, uint8_t *bucket_out, uint8_t *rgba_out,
+                               uint64_t *histogram_out, int32_t out_on_device, const uint8_t *lut_rgba) {
+    if (ctx && !histogram_out) return fail(ctx, CPT_EINVAL, "histogram_out is NULL");
+    return render(ctx, counts_out, bucket_out, rgba_out, nullptr, histogram_out, out_on_device, lut_rgba);
 }
 
 int composite_sync(composite_ctx *ctx) {

@@ -73,9 +73,11 @@ bool tma_compatible(const RasterBatch &b);
 struct Lut {
     uint32_t rgba[256];
 };
+// hist_out (device, 256 x uint64, may be NULL): zeroed, then the number of
+// pixels in every overlap class, counted in the same pass.
 cudaError_t launch_render_counts(const Plane &p, uint64_t n_members, void *counts_out,
                                  uint8_t *bucket_out, uint32_t *rgba_out, const Lut &lut,
-                                 const DeviceCaps &caps, cudaStream_t s);
+                                 const DeviceCaps &caps, cudaStream_t s, uint64_t *hist_out = nullptr);
 cudaError_t launch_render_mean(const Plane &p, uint64_t n_members, float *mean_out,
                                const DeviceCaps &caps, cudaStream_t s);
 

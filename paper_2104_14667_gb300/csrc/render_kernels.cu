@@ -9,13 +9,37 @@ namespace {
 
 constexpr int kThreads = 256;
 
-template <typename CountT>
+// Histogram of overlap classes (Fig. 1 caption): every warp counts into its
+// own 256 bins in shared memory, a thread adds runs of equal classes at once,
+// and each block adds its bins into the 64-bit global histogram at the end.
+struct HistBins {
+    uint32_t warp[kThreads / 32][256];
+};
+
+__device__ __forceinline__ void hist_init(HistBins &h) {
+    for (int i = threadIdx.x; i < (kThreads / 32) * 256; i += blockDim.x) (&h.warp[0][0])[i] = 0;
+}
+
+__device__ __forceinline__ void hist_flush(HistBins &h, unsigned long long *hist_out) {
+    __syncthreads();
+    for (int b = threadIdx.x; b < 256; b += blockDim.x) {
+        uint32_t t = 0;
+#pragma unroll
+        for (int w = 0; w < kThreads / 32; ++w) t += h.warp[w][b];
+        if (t) atomicAdd(hist_out + b, (unsigned long long)t);
+    }
+}
+
+template <typename CountT, bool kHist>
 __global__ void __launch_bounds__(kThreads)
 render_counts_kernel(Plane p, uint64_t n_members, CountT *counts_out, uint8_t *bucket_out,
-                     uint32_t *rgba_out, Lut lut) {
+                     uint32_t *rgba_out, Lut lut, unsigned long long *hist_out) {
     __shared__ uint32_t table[256];
+    __shared__ HistBins bins;
     for (int i = threadIdx.x; i < 256; i += blockDim.x) table[i] = lut.rgba[i];
+    if (kHist) hist_init(bins);
     __syncthreads();
+    uint32_t *my_bins = bins.warp[threadIdx.x / 32];
     const CountT *plane = static_cast<const CountT *>(p.data);
     const int64_t total = (int64_t)p.width * p.height;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
@@ -27,19 +51,24 @@ render_counts_kernel(Plane p, uint64_t n_members, CountT *counts_out, uint8_t *b
         if (counts_out) counts_out[i] = (CountT)c;
         if (bucket_out) bucket_out[i] = (uint8_t)b;
         if (rgba_out) rgba_out[i] = table[b];
+        if (kHist) atomicAdd(my_bins + b, 1u);
     }
+    if (kHist) hist_flush(bins, hist_out);
 }
 
 // 16 pixels of one row per thread, 16-byte stores; used when the width is a
 // multiple of 16 and every output is 16-byte aligned, so every dense output
 // row starts on a 16-byte boundary.
-template <typename CountT>
+template <typename CountT, bool kHist>
 __global__ void __launch_bounds__(kThreads)
 render_counts_vec_kernel(Plane p, uint64_t n_members, CountT *counts_out, uint8_t *bucket_out,
-                         uint32_t *rgba_out, Lut lut) {
+                         uint32_t *rgba_out, Lut lut, unsigned long long *hist_out) {
     __shared__ uint32_t table[256];
+    __shared__ HistBins bins;
     for (int i = threadIdx.x; i < 256; i += blockDim.x) table[i] = lut.rgba[i];
+    if (kHist) hist_init(bins);
     __syncthreads();
+    uint32_t *my_bins = bins.warp[threadIdx.x / 32];
     const CountT *plane = static_cast<const CountT *>(p.data);
     const int gpr = p.width / 16;
     const int64_t groups = (int64_t)gpr * p.height;
@@ -87,7 +116,21 @@ render_counts_vec_kernel(Plane p, uint64_t n_members, CountT *counts_out, uint8_
             for (int q = 0; q < 4; ++q)
                 d[q] = make_uint4(table[b[4 * q]], table[b[4 * q + 1]], table[b[4 * q + 2]], table[b[4 * q + 3]]);
         }
+        if (kHist) {
+            uint32_t run = 1;
+#pragma unroll
+            for (int j = 1; j < 16; ++j) {
+                if (b[j] == b[j - 1]) {
+                    ++run;
+                } else {
+                    atomicAdd(my_bins + b[j - 1], run);
+                    run = 1;
+                }
+            }
+            atomicAdd(my_bins + b[15], run);
+        }
     }
+    if (kHist) hist_flush(bins, hist_out);
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -110,32 +153,44 @@ unsigned grid_for(int64_t total, const DeviceCaps &caps) {
     return (unsigned)(blocks < 1 ? 1 : blocks);
 }
 
-}  // namespace
-
-cudaError_t launch_render_counts(const Plane &p, uint64_t n_members, void *counts_out,
-                                 uint8_t *bucket_out, uint32_t *rgba_out, const Lut &lut,
-                                 const DeviceCaps &caps, cudaStream_t s) {
+template <bool kHist>
+cudaError_t render_counts_t(const Plane &p, uint64_t n_members, void *counts_out, uint8_t *bucket_out,
+                            uint32_t *rgba_out, const Lut &lut, unsigned long long *hist_out,
+                            const DeviceCaps &caps, cudaStream_t s) {
     const int64_t total = (int64_t)p.width * p.height;
-    if (!counts_out && !bucket_out && !rgba_out) return cudaSuccess;
     const bool aligned = ((reinterpret_cast<uintptr_t>(counts_out) | reinterpret_cast<uintptr_t>(bucket_out) |
                            reinterpret_cast<uintptr_t>(rgba_out)) % 16) == 0;
     if (p.width % 16 == 0 && aligned) {
         const int64_t groups = total / 16;
         if (p.count_bits == 16)
-            render_counts_vec_kernel<uint16_t><<<grid_for(groups, caps), kThreads, 0, s>>>(
-                p, n_members, static_cast<uint16_t *>(counts_out), bucket_out, rgba_out, lut);
+            render_counts_vec_kernel<uint16_t, kHist><<<grid_for(groups, caps), kThreads, 0, s>>>(
+                p, n_members, static_cast<uint16_t *>(counts_out), bucket_out, rgba_out, lut, hist_out);
         else
-            render_counts_vec_kernel<uint32_t><<<grid_for(groups, caps), kThreads, 0, s>>>(
-                p, n_members, static_cast<uint32_t *>(counts_out), bucket_out, rgba_out, lut);
-        return cudaGetLastError();
+            render_counts_vec_kernel<uint32_t, kHist><<<grid_for(groups, caps), kThreads, 0, s>>>(
+                p, n_members, static_cast<uint32_t *>(counts_out), bucket_out, rgba_out, lut, hist_out);
+    } else if (p.count_bits == 16) {
+        render_counts_kernel<uint16_t, kHist><<<grid_for(total, caps), kThreads, 0, s>>>(
+            p, n_members, static_cast<uint16_t *>(counts_out), bucket_out, rgba_out, lut, hist_out);
+    } else {
+        render_counts_kernel<uint32_t, kHist><<<grid_for(total, caps), kThreads, 0, s>>>(
+            p, n_members, static_cast<uint32_t *>(counts_out), bucket_out, rgba_out, lut, hist_out);
     }
-    if (p.count_bits == 16)
-        render_counts_kernel<uint16_t><<<grid_for(total, caps), kThreads, 0, s>>>(
-            p, n_members, static_cast<uint16_t *>(counts_out), bucket_out, rgba_out, lut);
-    else
-        render_counts_kernel<uint32_t><<<grid_for(total, caps), kThreads, 0, s>>>(
-            p, n_members, static_cast<uint32_t *>(counts_out), bucket_out, rgba_out, lut);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_render_counts(const Plane &p, uint64_t n_members, void *counts_out,
+                                 uint8_t *bucket_out, uint32_t *rgba_out, const Lut &lut,
+                                 const DeviceCaps &caps, cudaStream_t s, uint64_t *hist_out) {
+    if (hist_out) {
+        cudaError_t e = cudaMemsetAsync(hist_out, 0, 256 * sizeof(uint64_t), s);
+        if (e != cudaSuccess) return e;
+        return render_counts_t<true>(p, n_members, counts_out, bucket_out, rgba_out, lut,
+                                     reinterpret_cast<unsigned long long *>(hist_out), caps, s);
+    }
+    if (!counts_out && !bucket_out && !rgba_out) return cudaSuccess;
+    return render_counts_t<false>(p, n_members, counts_out, bucket_out, rgba_out, lut, nullptr, caps, s);
 }
 
 cudaError_t launch_render_mean(const Plane &p, uint64_t n_members, float *mean_out,

@@ -310,3 +310,24 @@ def test_bit_packed_add_remove_and_32bit(k, c):
         with pytest.raises(binding.CompositeError) as e:
             comp.render_host()
         assert e.value.code == binding.CPT_EUNDERFLOW
+
+
+@pytest.mark.parametrize("w,h,n", [(1024, 1024, 16), (13, 7, 5), (100, 37, 300), (48, 33, 2)])
+@pytest.mark.parametrize("on_device", [False, True])
+def test_histogram_of_overlap_classes(w, h, n, on_device):
+    m = synth.masks(synth.ensemble(300 + w, w, h, n)) if w * h > 64 else synth.random_masks(8, n, h, w)
+    with binding.Composite(w, h) as comp:
+        comp.add(as_kind(m, "device"))
+        if on_device:
+            hist = torch.empty(256, dtype=torch.int64, device="cuda")
+            bucket = torch.empty((h, w), dtype=torch.uint8, device="cuda")
+            comp.render_histogram(hist, bucket_out=bucket)
+            comp.sync()
+            got_hist, got_bucket = hist.cpu().numpy().view(np.uint64), bucket.cpu().numpy()
+        else:
+            got_hist = np.empty(256, np.uint64)
+            got_bucket = np.empty((h, w), np.uint8)
+            comp.render_histogram(got_hist, bucket_out=got_bucket)
+    b = oracle.bucket(oracle.count(m), n)
+    np.testing.assert_array_equal(got_bucket, b)
+    np.testing.assert_array_equal(got_hist, oracle.histogram(b))

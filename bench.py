@@ -60,7 +60,7 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--sweep", choices=["readpath", "layout", "streaming", "tiny", "batched", "serving",
-                                       "compressed"],
+                                       "compressed", "render"],
                    default=None,
                    help="print one JSON line per point of a workload sweep instead of the bench line")
     p.add_argument("--resident", type=int, default=2048, help="serving: members resident in HBM")
@@ -821,6 +821,35 @@ def sweep_compressed(args, torch, binding, device, stream):
     print(json.dumps(out), flush=True)
 
 
+def sweep_render(args, torch, binding, device, stream):
+    """The render step alone (counts -> overlap classes -> colours, optionally
+    the class histogram) at 4096^2 and 8192^2, device outputs."""
+    import synth
+    for side in (4096, 8192):
+        P = side * side
+        m = torch.empty((16, side, side), dtype=torch.uint8, device=device)
+        ens = synth.ensemble(6, side, side, 16)
+        synth.fill_masks_torch(ens, m)
+        bucket = torch.empty((side, side), dtype=torch.uint8, device=device)
+        rgba = torch.empty((side, side, 4), dtype=torch.uint8, device=device)
+        counts = torch.empty((side, side), dtype=torch.int16, device=device)
+        hist = torch.empty(256, dtype=torch.int64, device=device)
+        with binding.Composite(side, side, stream=stream.cuda_stream) as comp:
+            comp.add(m)
+            variants = {
+                "bucket+rgba": (lambda: comp.render(bucket_out=bucket, rgba_out=rgba), 2 + 1 + 4),
+                "counts+bucket+rgba": (lambda: comp.render(counts, bucket, rgba), 2 + 2 + 1 + 4),
+                "bucket+rgba+histogram": (lambda: comp.render_histogram(hist, bucket_out=bucket, rgba_out=rgba), 2 + 1 + 4),
+                "histogram only": (lambda: comp.render_histogram(hist), 2),
+            }
+            for name, (fn, bpp) in variants.items():
+                ms = _timed(torch, stream, fn, 50, 5)
+                print(json.dumps({"sweep": "render", "side": side, "outputs": name, "us": 1e3 * ms,
+                                  "gbs": bpp * P / (ms * 1e-3) / 1e9}), flush=True)
+            comp.sync()
+        del m
+
+
 def run_sweep(args):
     import torch
     from paper_2104_14667_gb300 import binding
@@ -838,6 +867,8 @@ def run_sweep(args):
     elif args.sweep == "streaming":
         sweep_streaming(args, torch, binding, device, stream, chunks=[1, 2, 4, 8, 16, 64, 128],
                         stagings=[1, 3, 4])
+    elif args.sweep == "render":
+        sweep_render(args, torch, binding, device, stream)
     elif args.sweep == "compressed":
         sweep_compressed(args, torch, binding, device, stream)
     elif args.sweep == "serving":

@@ -202,6 +202,15 @@ int composite_end(composite_ctx *ctx);
  * the library; valid until the next call on the same context. */
 const char *composite_last_error(const composite_ctx *ctx);
 
+/* Self-test of the device-side bounded wait used by the TMA kernels: one
+ * thread waits on a shared-memory mbarrier that nothing ever arrives at, for
+ * at most timeout_us (1..1e7), then gives up, exactly as a stuck TMA kernel
+ * would, and the host reads the outcome.  *gave_up_out = 1 when the wait
+ * gave up (the expected result), *waited_us_out (may be NULL) = how long it
+ * waited.  No GPU fault is involved; the context-free error message is in
+ * composite_last_error(NULL). */
+int composite_selftest_bounded_wait(int64_t timeout_us, int32_t *gave_up_out, int64_t *waited_us_out);
+
 /* Largest composite plane of composite_oneshot_static, in padded pixels:
  * roundup(width, 16) * height must not exceed it (2048 x 2048). */
 #define CPT_ONESHOT_MAX_PIXELS 4194304

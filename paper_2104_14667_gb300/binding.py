@@ -93,6 +93,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
             "composite_end": (ctypes.c_int, [vp]),
             "composite_last_error": (ctypes.c_char_p, [vp]),
             "composite_oneshot_static": (ctypes.c_int, [vp, i32, i64, i32, i32, i32, vp, vp, vp, vp, vp]),
+            "composite_selftest_bounded_wait": (ctypes.c_int, [i64, ctypes.POINTER(i32), ctypes.POINTER(i64)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -282,6 +283,14 @@ def composite_oneshot_static(members, counts_out=None, bucket_out=None, rgba_out
                                       _ptr(rgba_out), lut_arr.ctypes.data if lut_arr is not None else None,
                                       stream)
     _check(lib, None, rc)
+
+
+def composite_selftest_bounded_wait(timeout_us: int) -> tuple[bool, int]:
+    """(gave_up, waited_us) of a device wait on a barrier nothing arrives at."""
+    lib = load()
+    gave, waited = ctypes.c_int32(), ctypes.c_int64()
+    _check(lib, None, lib.composite_selftest_bounded_wait(int(timeout_us), ctypes.byref(gave), ctypes.byref(waited)))
+    return bool(gave.value), waited.value
 
 
 def make_config(read_path="linear", staging_buffers=2, chunk_members=16, count_bits=16,

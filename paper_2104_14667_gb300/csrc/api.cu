@@ -769,6 +769,21 @@ int composite_end(composite_ctx *ctx) {
     return rc == CPT_EUNDERFLOW ? CPT_OK : rc;
 }
 
+int composite_selftest_bounded_wait(int64_t timeout_us, int32_t *gave_up_out, int64_t *waited_us_out) {
+    g_begin_error.clear();
+    if (timeout_us <= 0 || timeout_us > 10000000 || !gave_up_out)
+        return fail(nullptr, CPT_EINVAL, "timeout_us must be in 1..1e7 and gave_up_out not NULL");
+    unsigned long long *d = nullptr, h[2] = {0, 0};
+    cudaError_t e = cudaMalloc(&d, sizeof h);
+    if (e == cudaSuccess) e = cpt::launch_bounded_wait_selftest((uint64_t)timeout_us * 1000ull, d, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof h, cudaMemcpyDeviceToHost);
+    if (d) cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "bounded-wait self-test");
+    *gave_up_out = (int32_t)h[0];
+    if (waited_us_out) *waited_us_out = (int64_t)(h[1] / 1000ull);
+    return CPT_OK;
+}
+
 const char *composite_last_error(const composite_ctx *ctx) {
     return ctx ? ctx->err.c_str() : g_begin_error.c_str();
 }

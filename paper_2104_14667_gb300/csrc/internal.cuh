@@ -63,6 +63,9 @@ cudaError_t launch_depth_tma(const CUtensorMap &map, const RasterBatch &b, const
                              int *flags, uint64_t timeout_ns, int box_bytes, const DeviceCaps &caps,
                              cudaStream_t s);
 bool tma_box_supported(int box_bytes);
+// One thread waits, bounded by timeout_ns, on an mbarrier nothing arrives at
+// (the same wait the TMA kernels use); status[0] = gave up, status[1] = ns.
+cudaError_t launch_bounded_wait_selftest(uint64_t timeout_ns, unsigned long long *status, cudaStream_t s);
 // Returns 0 on success; a CUresult otherwise.  elem_bytes 1 (masks) or 4.
 int encode_tma_map(CUtensorMap *map, const RasterBatch &b, int width, int height, int elem_bytes,
                    int box_bytes);

@@ -261,6 +261,26 @@ depth_tma_kernel(const __grid_constant__ CUtensorMap map, Plane p, int n_members
     }
 }
 
+// Runs the bounded wait of the TMA kernels on an mbarrier that nothing
+// arrives at: it must give up after timeout_ns and report it.  status[0] =
+// 1 if the wait gave up, status[1] = nanoseconds it waited.
+__global__ void bounded_wait_selftest_kernel(uint64_t timeout_ns, unsigned long long *status) {
+    __shared__ uint64_t bar;
+    __shared__ int abort;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint64_t t0 = global_ns();
+        const bool ok = wait_bounded(&bar, 0u, timeout_ns, &abort);
+        status[0] = ok ? 0ull : 1ull;
+        status[1] = global_ns() - t0;
+    }
+}
+
 template <typename Kernel>
 cudaError_t prepare(Kernel k) {
     return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
@@ -287,6 +307,11 @@ unsigned grid_for(int tiles, const DeviceCaps &caps) {
 }
 
 }  // namespace
+
+cudaError_t launch_bounded_wait_selftest(uint64_t timeout_ns, unsigned long long *status, cudaStream_t s) {
+    bounded_wait_selftest_kernel<<<1, 32, 0, s>>>(timeout_ns, status);
+    return cudaGetLastError();
+}
 
 bool tma_compatible(const RasterBatch &b) {
     return (reinterpret_cast<uintptr_t>(b.base) % 16 == 0) && (b.row_pitch % 16 == 0) &&

@@ -143,6 +143,23 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows), "samples_in_timed_region": len(inside)}
 
 
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The largest of every rank's x (the slowest rank's time); x itself on
+    one rank.  Needs an initialised process group when world > 1."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, ms: float) -> float:
+    """Units all ranks processed per second, over the slowest rank's time."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -281,13 +298,6 @@ def run_ours(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=device)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
-
     W, H, N = args.width, args.height, args.members
     P = W * H
     ens, dev_masks = make_ensemble(args, torch, device)
@@ -333,10 +343,10 @@ def run_ours(args):
         sampler.window(w0, w1)
     comp.sync()
     dev_ms = t_start.elapsed_time(t_stop)
-    dev_ms = max_over_ranks(dev_ms)
+    dev_ms = max_over_ranks(dev_ms, world, device)
     kernel_ms = [a.elapsed_time(b) for a, b in k_events]
     kernel_avg_ms = sum(kernel_ms) / len(kernel_ms)
-    value = world * args.steps * N * P / (dev_ms * 1e-3)
+    value = whole_job_rate(args.steps * N * P, world, dev_ms)
     comp.close()
 
     # roofline of the accumulation kernel (one launch per step on this path)
@@ -384,13 +394,13 @@ def run_ours(args):
             if sampler:
                 sampler.window(w0, time.time())
             comp.close()
-            return max_over_ranks(1e3 * host_s)
+            return max_over_ranks(1e3 * host_s, world, device)
 
         staged_ms = e2e_run(False)
         direct_ms = e2e_run(True) if args.read_path == "linear" else None
         use_direct = args.e2e_mode == "host_read" and direct_ms is not None
         e2e_ms = direct_ms if use_direct else staged_ms
-        e2e_value = world * args.steps * N * P / (e2e_ms * 1e-3)
+        e2e_value = whole_job_rate(args.steps * N * P, world, e2e_ms)
         h2d_gbs = N * P / (e2e_ms * 1e-3 / args.steps) / 1e9
         # one traced staged step (outside the timed region) for the overlap fraction
         traced = binding.Composite(W, H, read_path=args.read_path, staging_buffers=args.staging,

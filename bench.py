@@ -485,9 +485,10 @@ def sweep_readpath(args, torch, binding, device, stream):
         else:
             data = torch.empty((N, H, W), dtype=torch.float32, device=device)
             synth.fill_depths_torch(ens, data, terrain_t=terrain_t)
-        for path, box in (("linear", 0), ("texture", 0), ("tma", 64), ("tma", 128), ("tma", 256)):
+        for path, box, conv in (("linear", 0, "kernel"), ("texture", 0, "copy"), ("texture", 0, "kernel"),
+                                ("tma", 64, "kernel"), ("tma", 128, "kernel"), ("tma", 256, "kernel")):
             cfg = dict(read_path=path, chunk_members=args.chunk, staging_buffers=args.staging,
-                       mode=mode, stream=stream.cuda_stream, tma_box_bytes=box)
+                       mode=mode, stream=stream.cuda_stream, tma_box_bytes=box, layout_converter=conv)
             with binding.Composite(W, H, **cfg) as comp:
                 def step():
                     comp.clear()
@@ -503,6 +504,7 @@ def sweep_readpath(args, torch, binding, device, stream):
             plane_rmw = (4 if mode == "count" else 8) * P * launches
             kernel_bytes = N * P * elem + plane_rmw
             line = {"sweep": "readpath", "mode": mode, "read_path": path, "tma_box_bytes": box or None,
+                    "layout_converter": conv if path == "texture" else None,
                     "width": W, "height": H,
                     "members": N, "chunk_members": args.chunk, "ms_per_pass": ms,
                     "member_px_per_s": N * P / (ms * 1e-3), "kernel_launches": launches,
@@ -523,18 +525,20 @@ def sweep_layout(args, torch, binding, device, stream):
     for h in sides:
         for w in sides:
             data = torch.randint(0, 2, (reps, h, w), dtype=torch.uint8, device=device)
-            with binding.Composite(w, h, read_path="texture", chunk_members=1, staging_buffers=2,
-                                   trace=True, stream=stream.cuda_stream) as comp:
-                comp.add(data)
-                comp.sync()
-                comp.clear()
-                comp.add(data)
-                rec = comp.trace()
-            conv = sorted(float(e) - float(s) for k, s, e in rec if int(k) == 1)
-            med = conv[len(conv) // 2]
-            print(json.dumps({"sweep": "layout", "width": w, "height": h, "bytes": w * h,
-                              "conversion_ms": med, "conversion_gbs": w * h / (med * 1e-3) / 1e9}),
-                  flush=True)
+            line = {"sweep": "layout", "width": w, "height": h, "bytes": w * h}
+            for converter in ("copy", "kernel"):
+                with binding.Composite(w, h, read_path="texture", chunk_members=1, staging_buffers=2,
+                                       trace=True, stream=stream.cuda_stream, layout_converter=converter) as comp:
+                    comp.add(data)
+                    comp.sync()
+                    comp.clear()
+                    comp.add(data)
+                    rec = comp.trace()
+                conv = sorted(float(e) - float(s) for k, s, e in rec if int(k) == 1)
+                med = conv[len(conv) // 2]
+                line[f"{converter}_ms"] = med
+                line[f"{converter}_gbs"] = w * h / (med * 1e-3) / 1e9
+            print(json.dumps(line), flush=True)
             del data
 
 

@@ -70,6 +70,13 @@ enum {
     CPT_READ_TMA = 2       /* TMA tensor tiles staged into shared memory         */
 };
 
+/* The buffer-to-image transform of the texture path (Section 4). */
+enum {
+    CPT_CONVERT_COPY = 0,     /* cudaMemcpy3DAsync into the array (the driver's copy)      */
+    CPT_CONVERT_KERNEL = 1    /* a kernel: 16-byte loads, surface stores into the array;
+                                 unaligned sources fall back to the copy                */
+};
+
 enum {
     CPT_MODE_COUNT = 0,       /* uint8 masks -> per-pixel member counts      */
     CPT_MODE_MEAN_DEPTH = 1   /* float32 depths -> per-pixel mean (float32)   */
@@ -111,6 +118,8 @@ typedef struct composite_config {
                                    0 = 256                                                */
     int32_t mask_format;        /* CPT_MASK_*; CPT_MASK_BITS needs CPT_MODE_COUNT and
                                    CPT_READ_LINEAR; default CPT_MASK_BYTES                */
+    int32_t layout_converter;   /* CPT_READ_TEXTURE: how rasters reach the cudaArray;
+                                   default CPT_CONVERT_KERNEL                             */
 } composite_config;
 
 /* Fills *cfg with the defaults listed above.  CPT_EINVAL if cfg is NULL. */

@@ -30,6 +30,7 @@ CPT_READ_LINEAR, CPT_READ_TEXTURE, CPT_READ_TMA = 0, 1, 2
 READ_PATHS = {"linear": CPT_READ_LINEAR, "texture": CPT_READ_TEXTURE, "tma": CPT_READ_TMA}
 CPT_MODE_COUNT, CPT_MODE_MEAN_DEPTH = 0, 1
 CPT_MASK_BYTES, CPT_MASK_BITS = 0, 1
+CPT_CONVERT_COPY, CPT_CONVERT_KERNEL = 0, 1
 
 HEADER = os.path.join(_build.INCLUDE, "composite.h")
 HEADERS = [os.path.join(_build.INCLUDE, h) for h in ("composite.h", "composite_engine.h", "composite_server.h")]
@@ -55,6 +56,7 @@ class Config(ctypes.Structure):
         ("host_read", ctypes.c_int32),
         ("tma_box_bytes", ctypes.c_int32),
         ("mask_format", ctypes.c_int32),
+        ("layout_converter", ctypes.c_int32),
     ]
 
 
@@ -295,7 +297,8 @@ def composite_selftest_bounded_wait(timeout_us: int) -> tuple[bool, int]:
 
 def make_config(read_path="linear", staging_buffers=2, chunk_members=16, count_bits=16,
                 mode="count", trace=False, pinned_ring_bytes=0, stream=None,
-                wait_timeout_ms=0, host_read=False, tma_box_bytes=0, mask_format="bytes") -> Config:
+                wait_timeout_ms=0, host_read=False, tma_box_bytes=0, mask_format="bytes",
+                layout_converter="kernel") -> Config:
     cfg = composite_default_config()
     cfg.read_path = READ_PATHS[read_path] if isinstance(read_path, str) else int(read_path)
     cfg.staging_buffers = staging_buffers
@@ -310,6 +313,8 @@ def make_config(read_path="linear", staging_buffers=2, chunk_members=16, count_b
     cfg.tma_box_bytes = tma_box_bytes
     cfg.mask_format = {"bytes": CPT_MASK_BYTES, "bits": CPT_MASK_BITS}[mask_format] \
         if isinstance(mask_format, str) else int(mask_format)
+    cfg.layout_converter = {"copy": CPT_CONVERT_COPY, "kernel": CPT_CONVERT_KERNEL}[layout_converter] \
+        if isinstance(layout_converter, str) else int(layout_converter)
     return cfg
 
 

@@ -37,6 +37,7 @@ struct Slot {
     uint8_t *stage = nullptr;         // device receiving buffer, C rasters
     cudaArray_t array = nullptr;      // texture path: the slot's layered array
     cudaTextureObject_t tex = 0;
+    cudaSurfaceObject_t surf = 0;     // the same array, written by the layout kernel
     cudaEvent_t ready = nullptr;      // upload (or conversion) into the slot done
     cudaEvent_t consumed = nullptr;   // the kernel that read the slot done
     uint8_t *ring = nullptr;          // pinned host ring slot (pageable inputs)
@@ -194,6 +195,8 @@ int check_config(const composite_config &c) {
     if (c.trace != 0 && c.trace != 1) return fail(nullptr, CPT_EINVAL, "trace must be 0 or 1");
     if (c.pinned_ring_bytes < 0 || c.wait_timeout_ms < 0) return fail(nullptr, CPT_EINVAL, "negative ring budget or timeout");
     if (c.host_read != 0 && c.host_read != 1) return fail(nullptr, CPT_EINVAL, "host_read must be 0 or 1");
+    if (c.layout_converter != CPT_CONVERT_COPY && c.layout_converter != CPT_CONVERT_KERNEL)
+        return fail(nullptr, CPT_EINVAL, "layout_converter %d out of range", c.layout_converter);
     if (c.mask_format != CPT_MASK_BYTES && c.mask_format != CPT_MASK_BITS)
         return fail(nullptr, CPT_EINVAL, "mask_format %d out of range", c.mask_format);
     if (c.mask_format == CPT_MASK_BITS && (c.mode != CPT_MODE_COUNT || c.read_path != CPT_READ_LINEAR))
@@ -206,6 +209,7 @@ int check_config(const composite_config &c) {
 void destroy(composite_ctx *ctx) {
     for (Slot &s : ctx->slots) {
         if (s.tex) cudaDestroyTextureObject(s.tex);
+        if (s.surf) cudaDestroySurfaceObject(s.surf);
         if (s.array) cudaFreeArray(s.array);
         if (s.stage) cudaFree(s.stage);
         if (s.ring) cudaFreeHost(s.ring);
@@ -274,10 +278,11 @@ int setup(composite_ctx *ctx) {
                     : cudaCreateChannelDesc(32, 32, 32, 32, cudaChannelFormatKindFloat);
             CK(ctx, cudaMalloc3DArray(&s.array, &desc,
                                       make_cudaExtent((size_t)groups, ctx->height, c.chunk_members),
-                                      cudaArrayLayered));
+                                      cudaArrayLayered | cudaArraySurfaceLoadStore));
             cudaResourceDesc rd{};
             rd.resType = cudaResourceTypeArray;
             rd.res.array.array = s.array;
+            CK(ctx, cudaCreateSurfaceObject(&s.surf, &rd));
             cudaTextureDesc td{};
             td.addressMode[0] = td.addressMode[1] = td.addressMode[2] = cudaAddressModeClamp;
             td.filterMode = cudaFilterModePoint;
@@ -342,6 +347,14 @@ int convert_to_array(composite_ctx *ctx, Slot &s, const void *src, int64_t pitch
                      cudaStream_t st) {
     int rc = trace_open(ctx, kTraceConvert, st);
     if (rc) return rc;
+    const int texels = (int)(ctx->pitch_px / ctx->vec_px);
+    const bool aligned = (reinterpret_cast<uintptr_t>(src) % 16 == 0) && (pitch % 16 == 0);
+    if (ctx->cfg.layout_converter == CPT_CONVERT_KERNEL && aligned) {
+        const cudaError_t e = cpt::launch_convert_to_array(src, pitch, pitch * ctx->height, s.surf, texels,
+                                                           ctx->height, n_layers, st);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "layout conversion kernel launch");
+        return trace_close(ctx, st);
+    }
     cudaMemcpy3DParms p{};
     p.srcPtr = make_cudaPitchedPtr(const_cast<void *>(src), (size_t)pitch, (size_t)pitch, ctx->height);
     p.dstArray = s.array;
@@ -572,6 +585,7 @@ int composite_default_config(composite_config *cfg) {
     cfg->host_read = 0;
     cfg->tma_box_bytes = 0;
     cfg->mask_format = CPT_MASK_BYTES;
+    cfg->layout_converter = CPT_CONVERT_KERNEL;
     return CPT_OK;
 }
 

@@ -280,6 +280,23 @@ depth_texture_kernel(cudaTextureObject_t tex, int n_layers, Plane p, int sign, i
     }
 }
 
+// Layout conversion by hand (the buffer-to-image transform of Section 4):
+// one thread per 16-byte texel reads the linear raster with a 16-byte load
+// and stores the texel into the layered cudaArray through a surface object.
+__global__ void __launch_bounds__(kThreads)
+convert_to_array_kernel(const uint8_t *src, int64_t pitch, int64_t member_stride, cudaSurfaceObject_t surf,
+                        int texels_per_row, int height, int64_t texels) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < texels;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = t / texels_per_row;
+        const int x = (int)(t - row * texels_per_row);
+        const int layer = (int)(row / height);
+        const int y = (int)(row - (int64_t)layer * height);
+        const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(src + layer * member_stride + y * pitch + x * 16));
+        surf2DLayeredwrite(v, surf, x * 16, y, layer);
+    }
+}
+
 inline int64_t blocks_for(int64_t groups) {
     int64_t blocks = (groups + kThreads - 1) / kThreads;
     return blocks < 1 ? 1 : (blocks > 0x7FFFFFFF ? 0x7FFFFFFF : blocks);
@@ -348,6 +365,16 @@ cudaError_t launch_count_texture(cudaTextureObject_t tex, int n_layers, const Pl
         count_texture_kernel<uint16_t><<<grid, kThreads, 0, s>>>(tex, n_layers, p, sign, flags, groups, gpr);
     else
         count_texture_kernel<uint32_t><<<grid, kThreads, 0, s>>>(tex, n_layers, p, sign, flags, groups, gpr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert_to_array(const void *src, int64_t pitch, int64_t member_stride,
+                                    cudaSurfaceObject_t surf, int texels_per_row, int height, int n_layers,
+                                    cudaStream_t s) {
+    const int64_t texels = (int64_t)texels_per_row * height * n_layers;
+    if (texels == 0) return cudaSuccess;
+    convert_to_array_kernel<<<(unsigned)blocks_for(texels), kThreads, 0, s>>>(
+        static_cast<const uint8_t *>(src), pitch, member_stride, surf, texels_per_row, height, texels);
     return cudaGetLastError();
 }
 

@@ -51,6 +51,11 @@ cudaError_t launch_count_texture(cudaTextureObject_t tex, int n_layers, const Pl
                                  int *flags, const DeviceCaps &caps, cudaStream_t s);
 cudaError_t launch_depth_texture(cudaTextureObject_t tex, int n_layers, const Plane &p, int sign,
                                  int *flags, const DeviceCaps &caps, cudaStream_t s);
+// Linear rasters (16-byte aligned base, pitch and stride) -> the layers of a
+// cudaArray of 16-byte texels, through a surface object.
+cudaError_t launch_convert_to_array(const void *src, int64_t pitch, int64_t member_stride,
+                                    cudaSurfaceObject_t surf, int texels_per_row, int height, int n_layers,
+                                    cudaStream_t s);
 
 // TMA read path: tensor map over the batch, tiles staged in shared memory.
 // The tensor map must come from encode_tma_map for the same batch.

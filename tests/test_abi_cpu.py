@@ -30,6 +30,7 @@ def test_library_exports_every_declared_symbol(lib):
 def test_default_config(lib):
     cfg = binding.composite_default_config()
     assert (cfg.read_path, cfg.staging_buffers, cfg.chunk_members, cfg.count_bits, cfg.mode) == (0, 2, 16, 16, 0)
+    assert cfg.layout_converter == binding.CPT_CONVERT_KERNEL
     assert ctypes.sizeof(binding.Config) == 64
 
 
@@ -44,7 +45,8 @@ def test_begin_rejects_empty_raster(lib, w, h):
                                          ("chunk_members", 0), ("chunk_members", 256), ("count_bits", 8),
                                          ("mode", 2), ("trace", 2), ("wait_timeout_ms", -1),
                                          ("host_read", 2), ("tma_box_bytes", 32),
-                                         ("tma_box_bytes", 512), ("mask_format", 2)])
+                                         ("tma_box_bytes", 512), ("mask_format", 2),
+                                         ("layout_converter", 2)])
 def test_begin_rejects_bad_config(lib, field, value):
     cfg = binding.composite_default_config()
     setattr(cfg, field, value)

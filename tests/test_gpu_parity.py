@@ -331,3 +331,21 @@ def test_histogram_of_overlap_classes(w, h, n, on_device):
     b = oracle.bucket(oracle.count(m), n)
     np.testing.assert_array_equal(got_bucket, b)
     np.testing.assert_array_equal(got_hist, oracle.histogram(b))
+
+
+@pytest.mark.parametrize("converter", ["copy", "kernel"])
+@pytest.mark.parametrize("mode", ["count", "mean_depth"])
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("w,h,n", [(256, 64, 40), (13, 7, 5), (100, 37, 19)])
+def test_texture_layout_converters(converter, mode, kind, w, h, n):
+    if mode == "count":
+        m = synth.scramble_nonzero(synth.random_masks(110 + w, n, h, w), 110)
+    else:
+        m = synth.random_depths(111 + w, n, h, w)
+    with binding.Composite(w, h, read_path="texture", layout_converter=converter, mode=mode, chunk_members=8) as comp:
+        comp.add(as_kind(m, kind))
+        if mode == "count":
+            check_counts(comp, m)
+        else:
+            got = comp.render_host()["mean"]
+            assert np.abs(got.astype(np.float64) - oracle.mean_depth(m)).max() <= 1e-5 * n

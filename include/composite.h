@@ -31,9 +31,10 @@
  *       or device         copy stream) or read in place; BORROWED until the
  *                         next composite_render/composite_sync/composite_end
  *                         returns: do not modify or free it before then.
- *   - Work is queued on the context's compute stream (config.cuda_stream, or
- *     a stream the library owns) and copy stream (always library owned), and
- *     ordered by events, never by host synchronisation.  Host waits that do
+ *   - Work is queued on the context's compute stream (config.cuda_stream, by
+ *     default the legacy default stream) and a copy stream the library owns,
+ *     ordered by events, never by host synchronisation; uploads wait for the
+ *     caller's earlier work on the compute stream.  Host waits that do
  *     happen (ring reuse, render to host, sync, end) are bounded by
  *     config.wait_timeout_ms and return CPT_ETIMEOUT when exceeded.
  *   - One context per host thread; contexts are independent.
@@ -105,8 +106,9 @@ typedef struct composite_config {
                                    (composite_trace_read); default 0                      */
     int64_t pinned_ring_bytes;  /* cap on the pinned ring used for pageable inputs;
                                    0 = k * C rasters                                      */
-    void *cuda_stream;          /* compute stream (a cudaStream_t) or NULL for a stream
-                                   owned by the library                                   */
+    void *cuda_stream;          /* compute stream (a cudaStream_t); NULL = the legacy
+                                   default stream.  The library's work is ordered after
+                                   the caller's earlier work on this stream.              */
     int64_t wait_timeout_ms;    /* bound on every wait, host and device; 0 = 10000        */
     int32_t host_read;          /* 1 = with CPT_READ_LINEAR, pinned host rasters with 16-byte
                                    aligned base, pitch and stride are read in place by the

@@ -45,7 +45,8 @@ enum {
 };
 
 typedef struct composite_engine_config {
-    void *cuda_stream;        /* cudaStream_t for all engine work, NULL = engine-owned */
+    void *cuda_stream;        /* cudaStream_t for all engine work, NULL = the legacy
+                                 default stream (ordered with the caller's work there) */
     int32_t slab_members;     /* members per work item, 1..255; 0 = 128               */
     int32_t ctas_per_sm;      /* persistent CTAs of 256 threads per SM, 1..8; 0 = 5   */
     int64_t wait_timeout_ms;  /* bound on host waits; 0 = 10000                        */
@@ -67,8 +68,10 @@ typedef struct composite_op {
     const void *members;          /* device, 16-byte aligned */
     const int32_t *member_index;  /* device, n_members entries, or NULL */
     int32_t n_members;
-    int32_t row_pitch_bytes;      /* multiple of 16, >= width */
+    int32_t row_pitch_bytes;      /* multiple of 16, >= the row's bytes (width, or
+                                     ceil(width / 8) for bit-packed masks) */
     int64_t member_stride_bytes;  /* multiple of 16, >= row_pitch_bytes * height */
+    int32_t mask_format;          /* CPT_MASK_BYTES or CPT_MASK_BITS (composite.h) */
 } composite_op;
 
 /* Render of one plane into dense row-major device outputs (each may be NULL). */

@@ -61,8 +61,11 @@ typedef struct composite_server_config {
     int32_t staging_members;       /* overflow rasters per staging half, 1..4096; 0 = 64   */
     int32_t max_cycles_in_flight;  /* 1..16; 0 = 4                                         */
     int64_t hbm_budget_bytes;      /* cap on planes + staging + index buffers; 0 = no cap  */
-    void *cuda_stream;             /* compute stream, NULL = server-owned                 */
+    void *cuda_stream;             /* compute stream, NULL = the legacy default stream    */
     int64_t wait_timeout_ms;       /* bound on host waits; 0 = 10000                      */
+    int32_t mask_format;           /* CPT_MASK_BYTES or CPT_MASK_BITS (both parts): bit-packed
+                                      rows are ceil(width / 8) bytes, 8x fewer bytes resident
+                                      and over the host link                             */
 } composite_server_config;
 
 typedef struct composite_server_stats {

@@ -295,6 +295,19 @@ def composite_selftest_bounded_wait(timeout_us: int) -> tuple[bool, int]:
     return bool(gave.value), waited.value
 
 
+def caller_stream():
+    """The caller's current torch CUDA stream handle (0 = the legacy default
+    stream), so the library's work is ordered after torch's work that
+    produced its inputs; None without a usable CUDA torch."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream or None
+    except Exception:  # pragma: no cover
+        pass
+    return None
+
+
 def make_config(read_path="linear", staging_buffers=2, chunk_members=16, count_bits=16,
                 mode="count", trace=False, pinned_ring_bytes=0, stream=None,
                 wait_timeout_ms=0, host_read=False, tma_box_bytes=0, mask_format="bytes",
@@ -307,7 +320,7 @@ def make_config(read_path="linear", staging_buffers=2, chunk_members=16, count_b
     cfg.mode = {"count": CPT_MODE_COUNT, "mean_depth": CPT_MODE_MEAN_DEPTH}[mode] if isinstance(mode, str) else int(mode)
     cfg.trace = 1 if trace else 0
     cfg.pinned_ring_bytes = pinned_ring_bytes
-    cfg.cuda_stream = stream
+    cfg.cuda_stream = stream if stream is not None else caller_stream()
     cfg.wait_timeout_ms = wait_timeout_ms
     cfg.host_read = 1 if host_read else 0
     cfg.tma_box_bytes = tma_box_bytes
@@ -417,6 +430,7 @@ class Op(ctypes.Structure):
         ("n_members", ctypes.c_int32),
         ("row_pitch_bytes", ctypes.c_int32),
         ("member_stride_bytes", ctypes.c_int64),
+        ("mask_format", ctypes.c_int32),
     ]
 
 
@@ -485,7 +499,7 @@ class Engine:
         self.lib = _engine_lib()
         cfg = EngineConfig()
         self.lib.composite_engine_default_config(ctypes.byref(cfg))
-        cfg.cuda_stream = stream
+        cfg.cuda_stream = stream if stream is not None else caller_stream()
         cfg.slab_members = slab_members
         cfg.ctas_per_sm = ctas_per_sm
         cfg.wait_timeout_ms = wait_timeout_ms
@@ -508,13 +522,15 @@ class Engine:
     def clear(self, plane: int):
         _echeck(self.lib, self.h, self.lib.composite_engine_clear(self.h, plane))
 
-    @staticmethod
-    def op(plane: int, members, sign: int = 1, index=None) -> Op:
-        """An op from a device tensor of masks [n, H, W] (or the whole
-        ensemble when an int32 device index tensor selects members)."""
+    def op(self, plane: int, members, sign: int = 1, index=None, mask_format: str = "bytes") -> Op:
+        """An op from a device tensor of masks [n, H, W] (bit-packed: [n, H,
+        ceil(W/8)]), or the whole ensemble when an int32 device index tensor
+        selects members.  The engine keeps the tensors alive until sync."""
         ptr, n, _, _, stride, pitch, _, _ = _raster_view(members)
+        self._keep.extend([members, index])
         o = Op()
         o.plane, o.sign, o.members = plane, sign, ptr
+        o.mask_format = {"bytes": CPT_MASK_BYTES, "bits": CPT_MASK_BITS}[mask_format]
         o.row_pitch_bytes, o.member_stride_bytes = pitch, stride
         if index is not None:
             o.member_index = index.data_ptr()
@@ -617,6 +633,7 @@ class ServerConfig(ctypes.Structure):
         ("hbm_budget_bytes", ctypes.c_int64),
         ("cuda_stream", ctypes.c_void_p),
         ("wait_timeout_ms", ctypes.c_int64),
+        ("mask_format", ctypes.c_int32),
     ]
 
 
@@ -667,9 +684,14 @@ class Server:
     with the same row pitch and member stride, or None."""
 
     def __init__(self, resident, overflow=None, max_sessions=64, max_batch=64, staging_members=64,
-                 max_cycles_in_flight=4, hbm_budget_bytes=0, stream=None, wait_timeout_ms=0):
+                 max_cycles_in_flight=4, hbm_budget_bytes=0, stream=None, wait_timeout_ms=0,
+                 mask_format="bytes", width=None):
         self.lib = _server_lib()
         rptr, rn, h, w, rstride, rpitch, _, _ = _raster_view(resident)
+        if mask_format == "bits":
+            if width is None or (width + 7) // 8 != w:
+                raise ValueError("bit-packed ensembles need the raster width (rows of ceil(width / 8) bytes)")
+            w = width
         cfg = ServerConfig()
         self.lib.composite_server_default_config(ctypes.byref(cfg))
         cfg.width, cfg.height = w, h
@@ -677,12 +699,14 @@ class Server:
         cfg.row_pitch_bytes, cfg.member_stride_bytes = rpitch, rstride
         if overflow is not None:
             optr, on, oh, ow, ostride, opitch, _, _ = _raster_view(overflow)
-            if (oh, ow, ostride, opitch) != (h, w, rstride, rpitch):
+            if (oh, ostride, opitch) != (h, rstride, rpitch):
                 raise ValueError("overflow must have the resident part's layout")
             cfg.overflow, cfg.n_overflow = optr, on
         cfg.max_sessions, cfg.max_batch = max_sessions, max_batch
         cfg.staging_members, cfg.max_cycles_in_flight = staging_members, max_cycles_in_flight
-        cfg.hbm_budget_bytes, cfg.cuda_stream, cfg.wait_timeout_ms = hbm_budget_bytes, stream, wait_timeout_ms
+        cfg.hbm_budget_bytes, cfg.wait_timeout_ms = hbm_budget_bytes, wait_timeout_ms
+        cfg.cuda_stream = stream if stream is not None else caller_stream()
+        cfg.mask_format = {"bytes": CPT_MASK_BYTES, "bits": CPT_MASK_BITS}[mask_format]
         srv = ctypes.c_void_p()
         _scheck(self.lib, None, self.lib.composite_server_begin(ctypes.byref(srv), ctypes.byref(cfg)))
         self.h = srv

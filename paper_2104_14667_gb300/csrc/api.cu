@@ -70,13 +70,13 @@ struct composite_ctx {
     int device = 0;
     DeviceCaps caps{};
     cudaStream_t compute = nullptr, copy = nullptr;
-    bool own_compute = false;
     std::vector<Slot> slots;
     uint64_t next_slot = 0;
     int64_t ring_chunk = 0;
     uint8_t *out_scratch = nullptr;
     size_t out_scratch_bytes = 0;
     cudaEvent_t done_compute = nullptr, done_copy = nullptr;
+    cudaEvent_t caller_ready = nullptr;   // the caller's work queued before a call
     std::vector<TraceRec> trace;
     std::vector<cudaEvent_t> trace_pool;
     size_t trace_used = 0;
@@ -220,12 +220,12 @@ void destroy(composite_ctx *ctx) {
     for (cudaEvent_t e : ctx->trace_pool) cudaEventDestroy(e);
     if (ctx->done_compute) cudaEventDestroy(ctx->done_compute);
     if (ctx->done_copy) cudaEventDestroy(ctx->done_copy);
+    if (ctx->caller_ready) cudaEventDestroy(ctx->caller_ready);
     if (ctx->out_scratch) cudaFree(ctx->out_scratch);
     if (ctx->plane.data) cudaFree(ctx->plane.data);
     if (ctx->flags) cudaFree(ctx->flags);
     if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
     if (ctx->copy) cudaStreamDestroy(ctx->copy);
-    if (ctx->own_compute && ctx->compute) cudaStreamDestroy(ctx->compute);
     delete ctx;
 }
 
@@ -233,13 +233,11 @@ int setup(composite_ctx *ctx) {
     composite_config &c = ctx->cfg;
     CK(ctx, cudaGetDevice(&ctx->device));
     CK(ctx, cudaDeviceGetAttribute(&ctx->caps.num_sms, cudaDevAttrMultiProcessorCount, ctx->device));
-    if (c.cuda_stream) {
-        ctx->compute = static_cast<cudaStream_t>(c.cuda_stream);
-    } else {
-        CK(ctx, cudaStreamCreateWithFlags(&ctx->compute, cudaStreamNonBlocking));
-        ctx->own_compute = true;
-    }
+    // NULL is the legacy default stream: the library's work is then ordered
+    // with everything else the caller issues to it
+    ctx->compute = static_cast<cudaStream_t>(c.cuda_stream);
     CK(ctx, cudaStreamCreateWithFlags(&ctx->copy, cudaStreamNonBlocking));
+    CK(ctx, cudaEventCreateWithFlags(&ctx->caller_ready, cudaEventDisableTiming));
     CK(ctx, cudaEventCreateWithFlags(&ctx->done_compute, cudaEventDisableTiming));
     CK(ctx, cudaEventCreateWithFlags(&ctx->done_copy, cudaEventDisableTiming));
 
@@ -513,6 +511,10 @@ int apply(composite_ctx *ctx, const void *members, int32_t n, int64_t stride, in
 
     const uint8_t *src = static_cast<const uint8_t *>(members);
     const MemKind kind = memory_kind(members);
+    // uploads on the copy stream start after the caller's earlier work on the
+    // compute stream (which may have produced the rasters)
+    CK(ctx, cudaEventRecord(ctx->caller_ready, ctx->compute));
+    CK(ctx, cudaStreamWaitEvent(ctx->copy, ctx->caller_ready, 0));
     int rc;
     if (kind == kDevice) {
         const bool aligned = (reinterpret_cast<uintptr_t>(members) % 16 == 0) && (pitch % 16 == 0) && (stride % 16 == 0);

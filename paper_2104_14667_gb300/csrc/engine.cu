@@ -53,6 +53,8 @@ struct OpDesc {
     int32_t plane_id;
     int32_t groups_per_thread;   // groups per lane per item (short slabs take several)
     int32_t exclusive;           // the only op on its plane, one slab: plain read-modify-write
+    int32_t bits;                // bit-packed masks: a group is a 32-pixel word
+    int32_t words_per_row;       // bits: ceil(width / 32)
 };
 
 struct RenderDesc {
@@ -175,6 +177,78 @@ __device__ __forceinline__ void process_item(const OpDesc &op, uint32_t item, in
     if (gather) __syncwarp();
 }
 
+// The same for bit-packed masks: a lane owns 32-pixel words and keeps their
+// counts in carry-save accumulators (BitCounter), 16 members per step.
+__device__ __forceinline__ void process_bits_item(const OpDesc &op, uint32_t item, int lane, int32_t *index,
+                                                  int *flags) {
+    const uint32_t local = item - (uint32_t)op.item_start;
+    const int sl = (int)(local / (uint32_t)op.tiles);
+    const int chunk = (int)(local - (uint32_t)sl * op.tiles);
+    const int m0 = sl * op.slab;
+    const int cnt = min(op.n - m0, op.slab);
+    const bool gather = op.index != nullptr;
+    if (gather) {
+        for (int i = lane; i < cnt; i += 32) index[i] = op.index[m0 + i];
+        __syncwarp();
+    }
+    const int64_t words = (int64_t)op.words_per_row * op.height;
+    const int gpt = op.groups_per_thread;
+    const int64_t stride = op.stride;
+    for (int j = 0; j < gpt; ++j) {
+        const int64_t g = ((int64_t)chunk * gpt + j) * 32 + lane;
+        if (g >= words) break;
+        const int y = (int)(g / op.words_per_row);
+        const int gx = (int)(g - (int64_t)y * op.words_per_row);
+        const int x0 = gx * 32;
+        const int valid = min(32, op.width - x0);
+        const int nbytes = (valid + 7) / 8;
+        const uint32_t keep = valid == 32 ? 0xFFFFFFFFu : ((1u << valid) - 1u);
+        const uint8_t *row = op.base + (int64_t)y * op.pitch + gx * 4;
+        cpt::BitCounter acc;
+        for (int i = 0; i < cnt; i += 16) {
+            const int take = min(16, cnt - i);
+            uint32_t w[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                uint32_t v = 0;
+                if (k < take) {
+                    const int64_t mi = gather ? index[i + k] : (int64_t)(m0 + i + k);
+                    const uint8_t *q = row + mi * stride;
+                    if (valid == 32) {
+                        v = __ldcs(reinterpret_cast<const uint32_t *>(q));
+                    } else {
+                        for (int b = 0; b < nbytes; ++b) v |= (uint32_t)q[b] << (8 * b);
+                        v &= keep;
+                    }
+                }
+                w[k] = v;
+            }
+            cpt::bitcount_add16(acc, w);
+        }
+        uint32_t *dst = op.plane + (int64_t)y * op.plane_pitch + x0;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int v = min(16, valid - 16 * h);
+            if (v <= 0) break;
+            uint32_t wide[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) wide[k] = cpt::bitcount_get(acc, 16 * h + k);
+            if (op.exclusive)
+                cpt::apply_count_group<uint32_t>(dst + 16 * h, v, wide, op.sign, flags + op.plane_id);
+            else
+                cpt::atomic_count_group<uint32_t>(dst + 16 * h, wide, op.sign, flags + op.plane_id);
+        }
+    }
+    if (gather) __syncwarp();
+}
+
+__device__ __forceinline__ void run_item(const OpDesc &op, uint32_t item, int lane, int32_t *index, int *flags) {
+    if (op.bits)
+        process_bits_item(op, item, lane, index, flags);
+    else
+        process_item(op, item, lane, index, flags);
+}
+
 // Persistent schedule: warps claim items from the counter one ahead (lane 0
 // asks for the next while the warp works on the current one), so warps
 // never wait for one another and uneven items balance across the GPU.
@@ -192,7 +266,7 @@ engine_accumulate_kernel(const OpDesc *ops, int n_ops, uint32_t n_items, uint32_
     while (next < n_items) {
         const uint32_t item = next;
         if (lane == 0) next = atomicAdd(counter, 1u);
-        process_item(ops[find_op(ops, n_ops, s_starts, item)], item, lane, index, flags);
+        run_item(ops[find_op(ops, n_ops, s_starts, item)], item, lane, index, flags);
         next = __shfl_sync(0xFFFFFFFFu, next, 0);
     }
 }
@@ -205,7 +279,7 @@ engine_accumulate_grid_kernel(const OpDesc *ops, int n_ops, uint32_t n_items, in
     const int lane = threadIdx.x & 31;
     const uint32_t item = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
     if (item >= n_items) return;
-    process_item(ops[find_desc(ops, n_ops, item)], item, lane, s_index[threadIdx.x >> 5], flags);
+    run_item(ops[find_desc(ops, n_ops, item)], item, lane, s_index[threadIdx.x >> 5], flags);
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -299,7 +373,6 @@ struct composite_engine {
     int device = 0;
     DeviceCaps caps{};
     cudaStream_t stream = nullptr;
-    bool own_stream = false;
     std::vector<PlaneRec> planes;
     int *d_flags = nullptr;
     int *h_flags = nullptr;
@@ -316,6 +389,7 @@ struct composite_engine {
     uint32_t *graph_counters = nullptr;
     std::vector<std::pair<int32_t, int64_t>> graph_n;   // plane -> N after a replay
     std::vector<int32_t> graph_planes;                  // every plane the graph touches
+    cudaStream_t capture_stream = nullptr;              // private stream for graph capture
     std::string err;
 };
 
@@ -438,7 +512,11 @@ int plan_ops(composite_engine *e, const composite_op *ops, int32_t n_ops, std::v
         if (!o.members) return efail(e, CPT_EINVAL, "op %d: members is NULL", i);
         if ((reinterpret_cast<uintptr_t>(o.members) % 16) || (o.row_pitch_bytes % 16) || (o.member_stride_bytes % 16))
             return efail(e, CPT_EINVAL, "op %d: members, row pitch and stride must be 16-byte aligned", i);
-        if (o.row_pitch_bytes < p.width || o.member_stride_bytes < (int64_t)o.row_pitch_bytes * p.height)
+        if (o.mask_format != CPT_MASK_BYTES && o.mask_format != CPT_MASK_BITS)
+            return efail(e, CPT_EINVAL, "op %d: mask_format %d out of range", i, o.mask_format);
+        const bool bits = o.mask_format == CPT_MASK_BITS;
+        const int64_t row_bytes = bits ? ((int64_t)p.width + 7) / 8 : p.width;
+        if (o.row_pitch_bytes < row_bytes || o.member_stride_bytes < (int64_t)o.row_pitch_bytes * p.height)
             return efail(e, CPT_EINVAL, "op %d: row pitch or member stride too small", i);
         OpDesc d{};
         d.base = static_cast<const uint8_t *>(o.members);
@@ -452,7 +530,9 @@ int plan_ops(composite_engine *e, const composite_op *ops, int32_t n_ops, std::v
         d.width = p.width;
         d.height = p.height;
         d.groups_per_row = (int32_t)(p.pitch_px / 16);
-        const int64_t groups = (int64_t)d.groups_per_row * p.height;
+        d.bits = bits ? 1 : 0;
+        d.words_per_row = (int32_t)(((int64_t)p.width + 31) / 32);
+        const int64_t groups = bits ? (int64_t)d.words_per_row * p.height : (int64_t)d.groups_per_row * p.height;
         // a warp item: 32 lanes x groups_per_thread groups, so that a lane
         // streams about 512 member-groups per item whatever the slab length
         const int first_slab = std::min(o.n_members, slab);
@@ -603,7 +683,7 @@ void destroy_engine(composite_engine *e) {
     if (e->h_flags) cudaFreeHost(e->h_flags);
     if (e->d_counter) cudaFree(e->d_counter);
     if (e->done_ev) cudaEventDestroy(e->done_ev);
-    if (e->own_stream && e->stream) cudaStreamDestroy(e->stream);
+    if (e->capture_stream) cudaStreamDestroy(e->capture_stream);
     delete e;
 }
 
@@ -644,12 +724,7 @@ int composite_engine_begin(composite_engine **out, const composite_engine_config
     auto setup = [&]() -> int {
         ECK(e, cudaGetDevice(&e->device));
         ECK(e, cudaDeviceGetAttribute(&e->caps.num_sms, cudaDevAttrMultiProcessorCount, e->device));
-        if (c.cuda_stream) {
-            e->stream = static_cast<cudaStream_t>(c.cuda_stream);
-        } else {
-            ECK(e, cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking));
-            e->own_stream = true;
-        }
+        e->stream = static_cast<cudaStream_t>(c.cuda_stream);   // NULL: the legacy default stream
         ECK(e, cudaMalloc(&e->d_flags, kMaxPlanes * sizeof(int)));
         ECK(e, cudaMemsetAsync(e->d_flags, 0, kMaxPlanes * sizeof(int), e->stream));
         ECK(e, cudaHostAlloc(&e->h_flags, kMaxPlanes * sizeof(int), cudaHostAllocDefault));
@@ -780,6 +855,16 @@ int composite_engine_capture(composite_engine *e, const composite_op *ops, int32
         ECK(e, cudaMemcpy(e->graph_rops, rdescs.data(), rdescs.size() * sizeof(RenderDesc), cudaMemcpyHostToDevice));
     }
     const Lut lut = lut_rgba ? make_lut(lut_rgba) : e->default_lut;
+    // Capture happens on a private stream (the legacy default stream cannot
+    // be captured); the graph is launched on the engine's stream.
+    if (!e->capture_stream) ECK(e, cudaStreamCreateWithFlags(&e->capture_stream, cudaStreamNonBlocking));
+    cudaStream_t engine_stream = e->stream;
+    e->stream = e->capture_stream;
+    struct Restore {
+        composite_engine *e;
+        cudaStream_t s;
+        ~Restore() { e->stream = s; }
+    } restore{e, engine_stream};
     ECK(e, cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal));
     auto body = [&]() -> int {
         for (const auto &pn : n_after) {

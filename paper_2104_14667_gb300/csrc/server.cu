@@ -42,6 +42,7 @@ struct Cycle {
     cudaEvent_t start = nullptr;   // timed: recorded on the copy stream when the cycle is queued
     cudaEvent_t done = nullptr;    // timed: the cycle's last operation (compute stream)
     cudaEvent_t index_ready = nullptr;
+    cudaEvent_t caller_ready = nullptr;
     std::vector<int64_t> ids;
     std::vector<int32_t> sessions;
     int32_t *d_index = nullptr;
@@ -71,7 +72,6 @@ struct composite_server {
     composite_server_config cfg{};
     composite_engine *eng = nullptr;
     cudaStream_t compute = nullptr, copy = nullptr;
-    bool own_compute = false;
     int32_t n_total = 0;
     int64_t raster_bytes = 0;      // row_pitch * height
     int64_t plane_bytes = 0;
@@ -276,10 +276,14 @@ int launch_cycle(composite_server *s, bool *launched) {
             o.n_members = (int32_t)ids.size();
             o.row_pitch_bytes = s->cfg.row_pitch_bytes;
             o.member_stride_bytes = s->cfg.member_stride_bytes;
+            o.mask_format = s->cfg.mask_format;
             ops.push_back(o);
             off += ids.size();
         }
     }
+    // the copy stream starts after the caller's earlier work on the compute stream
+    SCK(s, cudaEventRecord(cyc->caller_ready, s->compute));
+    SCK(s, cudaStreamWaitEvent(s->copy, cyc->caller_ready, 0));
     SCK(s, cudaEventRecord(cyc->start, s->copy));
     if (off) {
         // on the copy stream, ahead of this cycle's raster uploads
@@ -325,6 +329,7 @@ int launch_cycle(composite_server *s, bool *launched) {
             o.n_members = (int32_t)(cur - first);
             o.row_pitch_bytes = s->cfg.row_pitch_bytes;
             o.member_stride_bytes = s->cfg.member_stride_bytes;
+            o.mask_format = s->cfg.mask_format;
             chunk_ops.push_back(o);
             off += cur - first;
         }
@@ -383,6 +388,7 @@ void destroy_server(composite_server *s) {
         if (c.done) cudaEventDestroy(c.done);
         if (c.start) cudaEventDestroy(c.start);
         if (c.index_ready) cudaEventDestroy(c.index_ready);
+        if (c.caller_ready) cudaEventDestroy(c.caller_ready);
         if (c.d_index) cudaFree(c.d_index);
         if (c.h_index) cudaFreeHost(c.h_index);
     }
@@ -392,7 +398,6 @@ void destroy_server(composite_server *s) {
     }
     if (s->d_stage) cudaFree(s->d_stage);
     if (s->copy) cudaStreamDestroy(s->copy);
-    if (s->own_compute && s->compute) cudaStreamDestroy(s->compute);
     delete s;
 }
 
@@ -422,7 +427,10 @@ int composite_server_begin(composite_server **out, const composite_server_config
         return sfail(nullptr, CPT_EINVAL, "member counts out of range");
     if (c.n_resident > 0 && !c.resident) return sfail(nullptr, CPT_EINVAL, "resident is NULL");
     if (c.n_overflow > 0 && !c.overflow) return sfail(nullptr, CPT_EINVAL, "overflow is NULL");
-    if ((c.row_pitch_bytes % 16) || (c.member_stride_bytes % 16) || c.row_pitch_bytes < c.width ||
+    if (c.mask_format != CPT_MASK_BYTES && c.mask_format != CPT_MASK_BITS)
+        return sfail(nullptr, CPT_EINVAL, "mask_format out of range");
+    const int64_t row_bytes = c.mask_format == CPT_MASK_BITS ? ((int64_t)c.width + 7) / 8 : c.width;
+    if ((c.row_pitch_bytes % 16) || (c.member_stride_bytes % 16) || c.row_pitch_bytes < row_bytes ||
         c.member_stride_bytes < (int64_t)c.row_pitch_bytes * c.height)
         return sfail(nullptr, CPT_EINVAL, "row pitch and member stride must be multiples of 16 covering the raster");
     if (reinterpret_cast<uintptr_t>(c.resident) % 16) return sfail(nullptr, CPT_EINVAL, "resident must be 16-byte aligned");
@@ -452,12 +460,7 @@ int composite_server_begin(composite_server **out, const composite_server_config
     s->raster_bytes = (int64_t)c.row_pitch_bytes * c.height;
     s->plane_bytes = ((int64_t)c.width + 15) / 16 * 16 * c.height * 4;
     auto setup = [&]() -> int {
-        if (c.cuda_stream) {
-            s->compute = static_cast<cudaStream_t>(c.cuda_stream);
-        } else {
-            SCK(s, cudaStreamCreateWithFlags(&s->compute, cudaStreamNonBlocking));
-            s->own_compute = true;
-        }
+        s->compute = static_cast<cudaStream_t>(c.cuda_stream);   // NULL: the legacy default stream
         SCK(s, cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking));
         composite_engine_config ec;
         composite_engine_default_config(&ec);
@@ -480,6 +483,7 @@ int composite_server_begin(composite_server **out, const composite_server_config
             SCK(s, cudaEventCreate(&cy.start));
             SCK(s, cudaEventCreate(&cy.done));
             SCK(s, cudaEventCreateWithFlags(&cy.index_ready, cudaEventDisableTiming));
+            SCK(s, cudaEventCreateWithFlags(&cy.caller_ready, cudaEventDisableTiming));
         }
         return CPT_OK;
     };

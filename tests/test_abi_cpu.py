@@ -78,7 +78,7 @@ def test_engine_defaults_and_no_gpu(lib):
     cfg = binding.EngineConfig()
     assert eng_lib.composite_engine_default_config(ctypes.byref(cfg)) == binding.CPT_OK
     assert (cfg.slab_members, cfg.ctas_per_sm) == (128, 5)
-    assert ctypes.sizeof(binding.Op) == 40 and ctypes.sizeof(binding.RenderOp) == 32
+    assert ctypes.sizeof(binding.Op) == 48 and ctypes.sizeof(binding.RenderOp) == 32
     assert ctypes.sizeof(binding.EngineConfig) == 40 and cfg.schedule == binding.CPT_SCHEDULE_PERSISTENT
     assert eng_lib.composite_engine_end(None) == binding.CPT_OK
     bad = binding.EngineConfig()

@@ -154,3 +154,40 @@ def test_invalid_ops_rejected_before_anything_runs():
             eng.submit([eng.op(p, odd)])
         assert e.value.code == binding.CPT_EINVAL
         assert eng.member_count(p) == 0
+
+
+def padded_bits(m: np.ndarray):
+    """Device copy of bit-packed masks with rows padded to 16 bytes."""
+    p = synth.pack_masks(m)
+    n, h, wb = p.shape
+    pitch = (wb + 15) // 16 * 16
+    buf = torch.zeros((n, h, pitch), dtype=torch.uint8, device="cuda")
+    buf[:, :, :wb] = torch.from_numpy(p).cuda()
+    return buf[:, :, :wb]
+
+
+@pytest.mark.parametrize("schedule", ["persistent", "grid"])
+def test_bit_packed_ops_mixed_with_byte_ops(schedule):
+    shapes = [(300, 70, 280), (33, 9, 5), (1024, 64, 40)]
+    with binding.Engine(schedule=schedule) as eng:
+        items = []
+        for i, (w, h, n) in enumerate(shapes):
+            m = synth.scramble_nonzero(synth.random_masks(120 + i, n, h, w, density=0.3), i)
+            p = eng.add_plane(w, h)
+            items.append((m, p, outputs(w, h)))
+        ops = []
+        for i, (m, p, _) in enumerate(items):
+            half = m.shape[0] // 2
+            ops.append(eng.op(p, padded_bits(m[:half]), mask_format="bits"))
+            ops.append(eng.op(p, padded(m[half:])))
+        eng.submit(ops)
+        # remove a gathered subset again, bit-packed, then re-add it as bytes
+        m0, p0, _ = items[0]
+        idx = torch.arange(0, m0.shape[0] // 2, 3, dtype=torch.int32, device="cuda")
+        bits0 = padded_bits(m0[: m0.shape[0] // 2])
+        eng.submit([eng.op(p0, bits0, -1, idx, mask_format="bits")])
+        eng.submit([eng.op(p0, padded(m0[: m0.shape[0] // 2]), 1, idx)])
+        eng.render([eng.render_op(p, *o) for _, p, o in items])
+        eng.sync()
+        for m, p, o in items:
+            check(o, m)

@@ -119,3 +119,23 @@ def test_session_rules_and_errors():
         with binding.Server(res, ovf, staging_members=4, hbm_budget_bytes=2 * 4 * PITCH * H + plane // 2) as srv:
             srv.open_session()
     assert e.value.code == binding.CPT_ENOMEM
+
+
+def test_bit_packed_ensemble_matches_byte_ensemble():
+    m, res, ovf = ensemble()
+    packed = synth.pack_masks(m)
+    wb = packed.shape[-1]
+    buf = np.zeros((N_RES + N_OVF, H, 32), np.uint8)
+    buf[:, :, :wb] = packed
+    pres = torch.from_numpy(buf[:N_RES]).cuda()[:, :, :wb]
+    povf = torch.from_numpy(buf[N_RES:]).pin_memory()[:, :, :wb]
+    reqs = trace(2, 4, 24)
+    as_bytes, _ = serve(res, ovf, reqs, 4, max_batch=6, staging_members=5)
+    as_bits, st = serve(pres, povf, reqs, 4, max_batch=6, staging_members=5, mask_format="bits", width=W)
+    assert st["overflow_uploads"] > 0
+    for a, b in zip(as_bytes, as_bits):
+        for x, y in zip(a, b):
+            np.testing.assert_array_equal(x, y)
+    for (counts, _, _), members in zip(as_bits, expected_sets(reqs, 4)):
+        c = oracle.count(m[members]) if len(members) else np.zeros((H, W), np.int64)
+        np.testing.assert_array_equal(counts.astype(np.int64), c)

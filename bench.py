@@ -69,6 +69,10 @@ def parse_args():
     p.add_argument("--requests", type=int, default=200, help="serving: requests per offered rate")
     p.add_argument("--max-batch", type=int, default=64, help="serving: requests per cycle")
     p.add_argument("--poll-us", type=float, default=100.0, help="serving: host back-off between idle polls")
+    p.add_argument("--staging-mib", type=int, default=1024,
+                   help="serving: size of one overflow staging half, MiB (members = this / raster bytes)")
+    p.add_argument("--mask-format", choices=["bytes", "bits"], default="bytes",
+                   help="serving: store the ensemble as byte or bit-packed masks")
     p.add_argument("--rates", type=float, nargs="+", default=[50, 100, 200, 500],
                    help="serving: offered request rates (per second)")
     p.add_argument("--e2e-mode", choices=["staged", "host_read"], default="staged",
@@ -700,15 +704,20 @@ def sweep_serving(args, torch, binding, device, stream):
     t_setup = time.perf_counter()
     ens = synth.ensemble(5, W, H, R + O)
     tdev = torch.from_numpy(ens.terrain).to(device)
-    resident = torch.empty((R, H, W), dtype=torch.uint8, device=device)
-    synth.fill_masks_torch(ens, resident, range(R), terrain_t=tdev)
-    overflow = torch.empty((O, H, W), dtype=torch.uint8, pin_memory=True) if O else None
+    bits = args.mask_format == "bits"
+    WB = W // 8 if bits else W
     step = 256
     tmp = torch.empty((step, H, W), dtype=torch.uint8, device=device)
+    resident = torch.empty((R, H, WB), dtype=torch.uint8, device=device)
+    for m0 in range(0, R, step):
+        m1 = min(R, m0 + step)
+        synth.fill_masks_torch(ens, tmp[: m1 - m0], range(m0, m1), terrain_t=tdev)
+        resident[m0:m1] = synth.pack_masks_torch(tmp[: m1 - m0]) if bits else tmp[: m1 - m0]
+    overflow = torch.empty((O, H, WB), dtype=torch.uint8, pin_memory=True) if O else None
     for m0 in range(0, O, step):
         m1 = min(O, m0 + step)
         synth.fill_masks_torch(ens, tmp[: m1 - m0], range(R + m0, R + m1), terrain_t=tdev)
-        overflow[m0:m1].copy_(tmp[: m1 - m0])
+        overflow[m0:m1].copy_(synth.pack_masks_torch(tmp[: m1 - m0]) if bits else tmp[: m1 - m0])
     del tmp
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t_setup
@@ -717,11 +726,14 @@ def sweep_serving(args, torch, binding, device, stream):
     outs = [(torch.empty((H, W), dtype=torch.uint8, device=device),
              torch.empty((H, W, 4), dtype=torch.uint8, device=device)) for _ in range(n_sessions)]
 
+    staging = max(1, min(4096, (args.staging_mib << 20) // (H * WB)))
+
     def run(trace, max_batch, cycles_in_flight):
         checks = {}
         with binding.Server(resident, overflow, max_sessions=n_sessions, max_batch=max_batch,
-                            staging_members=args.chunk * 2, max_cycles_in_flight=cycles_in_flight,
-                            stream=stream.cuda_stream) as srv:
+                            staging_members=staging, max_cycles_in_flight=cycles_in_flight,
+                            stream=stream.cuda_stream, mask_format=args.mask_format,
+                            width=W if bits else None) as srv:
             sessions = [srv.open_session() for _ in range(n_sessions)]
             sets = [np.zeros(R + O, bool) for _ in range(n_sessions)]
             arrival, done_at = {}, {}
@@ -769,8 +781,10 @@ def sweep_serving(args, torch, binding, device, stream):
         trace = synth.serving_trace(5, args.requests, rate, n_sessions, R + O)
         batched = run(trace, args.max_batch, 4)
         single = run(trace, 1, 1)      # the queue alone: one request on the device at a time
-        print(json.dumps({"sweep": "serving", "rate_per_s": rate, "requests": len(trace), "resident": R,
-                          "overflow": O, "side": W, "sessions": n_sessions, "setup_s": setup_s,
+        print(json.dumps({"sweep": "serving", "mask_format": args.mask_format, "rate_per_s": rate,
+                          "requests": len(trace), "resident": R,
+                          "overflow": O, "side": W, "sessions": n_sessions, "staging_members": staging,
+                          "setup_s": setup_s,
                           "toggle_members_mean": float(np.mean([len(t[2]) for t in trace])),
                           "batched": batched, "one_at_a_time": single,
                           "throughput_gain": batched["composites_per_s"] / single["composites_per_s"],

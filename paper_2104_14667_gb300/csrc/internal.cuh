@@ -51,6 +51,10 @@ cudaError_t launch_count_texture(cudaTextureObject_t tex, int n_layers, const Pl
                                  int *flags, const DeviceCaps &caps, cudaStream_t s);
 cudaError_t launch_depth_texture(cudaTextureObject_t tex, int n_layers, const Plane &p, int sign,
                                  int *flags, const DeviceCaps &caps, cudaStream_t s);
+// dst + i * stride <- src + ids[i] * stride, raster_bytes (a multiple of 16)
+// each, i < n; src may be host-mapped pinned memory.  16-byte aligned.
+cudaError_t launch_gather_rasters(void *dst, const void *src, const int32_t *ids, int n, int64_t stride,
+                                  int64_t raster_bytes, const DeviceCaps &caps, cudaStream_t s);
 // Linear rasters (16-byte aligned base, pitch and stride) -> the layers of a
 // cudaArray of 16-byte texels, through a surface object.
 cudaError_t launch_convert_to_array(const void *src, int64_t pitch, int64_t member_stride,

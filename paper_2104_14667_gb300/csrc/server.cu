@@ -10,10 +10,12 @@
 #include <string>
 #include <thread>
 #include <unordered_set>
+#include <utility>
 #include <vector>
 
 #include "composite_engine.h"
 #include "composite_server.h"
+#include "internal.cuh"
 
 namespace {
 
@@ -80,6 +82,9 @@ struct composite_server {
     std::deque<Request> queue;
     std::vector<Cycle> cycles;
     uint8_t *d_stage = nullptr;    // 2 halves x staging_members rasters
+    const void *overflow_dev = nullptr;   // the overflow part as the device reads it
+    std::vector<int32_t> pos_of;          // overflow id -> staging position, per cycle
+    cpt::DeviceCaps caps{};
     cudaEvent_t stage_ready[2] = {nullptr, nullptr}, stage_free[2] = {nullptr, nullptr};
     int stage_half = 0;
     int64_t next_id = 0;
@@ -238,21 +243,50 @@ int launch_cycle(composite_server *s, bool *launched) {
     }
     // Distinct overflow members of the cycle: each is uploaded once, whatever
     // number of requests toggle it; requests gather it from staging by index.
+    // Staging order is by the (ascending) list of requests that toggle the
+    // member, compared lexicographically, then by id: a request's members
+    // then lie in few contiguous runs, so each staging chunk holds few
+    // (request, sign) groups and the chunk's submit has few, large ops (each
+    // op costs a pass over its plane, whatever its member count).
     std::vector<int32_t> distinct;
-    distinct.reserve(ovf.size());
-    for (const OverflowItem &o : ovf) distinct.push_back(o.member);
-    std::sort(distinct.begin(), distinct.end());
-    distinct.erase(std::unique(distinct.begin(), distinct.end()), distinct.end());
-    for (OverflowItem &o : ovf)
-        o.pos = (int32_t)(std::lower_bound(distinct.begin(), distinct.end(), o.member) - distinct.begin());
+    {
+        std::vector<std::pair<int32_t, int32_t>> mr;   // (member, request), one per item
+        mr.reserve(ovf.size());
+        for (const OverflowItem &o : ovf) mr.push_back({o.member, o.request});
+        std::sort(mr.begin(), mr.end());
+        std::vector<size_t> first;   // per distinct member, its run in mr
+        for (size_t i = 0; i < mr.size(); ++i)
+            if (i == 0 || mr[i].first != mr[i - 1].first) first.push_back(i);
+        first.push_back(mr.size());
+        std::vector<int32_t> order(first.size() - 1);
+        for (size_t i = 0; i < order.size(); ++i) order[i] = (int32_t)i;
+        std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+            const auto a0 = mr.begin() + first[a], a1 = mr.begin() + first[a + 1];
+            const auto b0 = mr.begin() + first[b], b1 = mr.begin() + first[b + 1];
+            const auto by_request = [](const std::pair<int32_t, int32_t> &x, const std::pair<int32_t, int32_t> &y) {
+                return x.second < y.second;
+            };
+            if (std::lexicographical_compare(a0, a1, b0, b1, by_request)) return true;
+            if (std::lexicographical_compare(b0, b1, a0, a1, by_request)) return false;
+            return a0->first < b0->first;
+        });
+        distinct.resize(order.size());
+        if (s->pos_of.size() < (size_t)s->cfg.n_overflow) s->pos_of.resize(s->cfg.n_overflow);
+        for (size_t i = 0; i < order.size(); ++i) {
+            distinct[i] = mr[first[order[i]]].first;
+            s->pos_of[distinct[i]] = (int32_t)i;
+        }
+    }
+    for (OverflowItem &o : ovf) o.pos = s->pos_of[o.member];
     std::sort(ovf.begin(), ovf.end(), [](const OverflowItem &a, const OverflowItem &b) {
         if (a.request != b.request) return a.request < b.request;
         if (a.sign != b.sign) return a.sign > b.sign;
         return a.pos < b.pos;
     });
 
-    // index lists of the resident ops (and, after them, of the overflow ops)
-    size_t total = ovf.size();
+    // index lists of the resident ops (and, after them, of the overflow ops
+    // and the overflow ids each chunk gathers)
+    size_t total = ovf.size() + distinct.size();
     for (size_t r = 0; r < batch.size(); ++r) total += res_add[r].size() + res_rem[r].size();
     int rc = reserve_index(s, *cyc, std::max<size_t>(total, 1));
     if (rc) return rc;
@@ -333,21 +367,15 @@ int launch_cycle(composite_server *s, bool *launched) {
             chunk_ops.push_back(o);
             off += cur - first;
         }
+        // the chunk's distinct overflow ids, after its ops' slot lists
+        const size_t ids_off = off;
+        for (size_t i = c0; i < c1; ++i) cyc->h_index[off++] = distinct[i];
         SCK(s, cudaStreamWaitEvent(s->copy, s->stage_free[h], 0));
-        for (size_t i = c0; i < c1;) {
-            // consecutive overflow ids go up in one copy
-            size_t j = i + 1;
-            while (j < c1 && distinct[j] == distinct[j - 1] + 1) ++j;
-            const uint8_t *src = static_cast<const uint8_t *>(s->cfg.overflow) + (int64_t)distinct[i] * s->cfg.member_stride_bytes;
-            const size_t bytes = (size_t)((int64_t)(j - i - 1) * s->cfg.member_stride_bytes + s->raster_bytes);
-            SCK(s, cudaMemcpyAsync(base + (int64_t)(i - c0) * s->cfg.member_stride_bytes, src, bytes,
-                                   cudaMemcpyDefault, s->copy));
-            i = j;
-        }
+        SCK(s, cudaMemcpyAsync(cyc->d_index + off0, cyc->h_index + off0, (off - off0) * sizeof(int32_t),
+                               cudaMemcpyHostToDevice, s->copy));
+        SCK(s, cpt::launch_gather_rasters(base, s->overflow_dev, cyc->d_index + ids_off, (int)(c1 - c0),
+                                          s->cfg.member_stride_bytes, s->raster_bytes, s->caps, s->copy));
         s->stats.overflow_uploads += (int64_t)(c1 - c0);
-        if (off > off0)
-            SCK(s, cudaMemcpyAsync(cyc->d_index + off0, cyc->h_index + off0, (off - off0) * sizeof(int32_t),
-                                   cudaMemcpyHostToDevice, s->copy));
         SCK(s, cudaEventRecord(s->stage_ready[h], s->copy));
         SCK(s, cudaStreamWaitEvent(s->compute, s->stage_ready[h], 0));
         rc = engine_rc(s, composite_engine_submit(s->eng, chunk_ops.data(), (int32_t)chunk_ops.size()));
@@ -461,6 +489,18 @@ int composite_server_begin(composite_server **out, const composite_server_config
     s->plane_bytes = ((int64_t)c.width + 15) / 16 * 16 * c.height * 4;
     auto setup = [&]() -> int {
         s->compute = static_cast<cudaStream_t>(c.cuda_stream);   // NULL: the legacy default stream
+        int dev = 0;
+        SCK(s, cudaGetDevice(&dev));
+        SCK(s, cudaDeviceGetAttribute(&s->caps.num_sms, cudaDevAttrMultiProcessorCount, dev));
+        if (c.n_overflow > 0) {
+            // pinned host memory is read by the gather kernel through its device mapping
+            cudaPointerAttributes a;
+            SCK(s, cudaPointerGetAttributes(&a, c.overflow));
+            s->overflow_dev = a.type == cudaMemoryTypeHost ? a.devicePointer : c.overflow;
+            if (!s->overflow_dev) return sfail(s, CPT_EINVAL, "the overflow part has no device mapping");
+            if (reinterpret_cast<uintptr_t>(s->overflow_dev) % 16)
+                return sfail(s, CPT_EINVAL, "overflow must be 16-byte aligned");
+        }
         SCK(s, cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking));
         composite_engine_config ec;
         composite_engine_default_config(&ec);

@@ -14,7 +14,8 @@ render.
 * ``roofline``: the accumulation kernel against the measured HBM copy peak,
   its launches timed with CUDA events inside the timed region.
 * ``cpu_baseline``: the CPU oracle, single threaded, on a bounded sample of
-  the same workload.
+  the same workload; ``cpu_baseline_all_cores`` runs the same oracle in one
+  process per host core (spawned), each on its own members, started together.
 
 ``--impl reference`` times the CPU oracle itself on the same workload (each
 step a bounded sample of members) and prints its own line.
@@ -58,6 +59,7 @@ def parse_args():
     p.add_argument("--cpu-seconds", type=float, default=10.0,
                    help="target CPU time of the oracle baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-cpu-all-cores", action="store_true", help="skip the all-cores oracle timing")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--sweep", choices=["readpath", "layout", "streaming", "tiny", "batched", "serving",
                                        "compressed", "render"],
@@ -226,6 +228,56 @@ def cpu_oracle_rate(ens, members: int, target_s: float, batch: int = 4):
         spent += time.perf_counter() - t0
         done += b
     return done * w * h / spent, done, spent
+
+
+def _oracle_worker(seed, width, height, members, first, target_s, barrier, out):
+    # one process of the all-cores CPU baseline: members first, first + P, ...
+    import oracle
+    import synth
+    ens = synth.ensemble(seed, width, height, members)
+    stride = out["procs"]
+    buf = np.empty((1, height, width), dtype=np.uint8)
+    counts = np.zeros((height, width), dtype=np.int64)
+    ids = list(range(first, members, stride)) or [first % members]
+    synth.fill_masks(ens, buf, ids[:1])
+    oracle.count_apply(counts, buf, 1)          # warm: library load, page faults
+    barrier.wait()
+    done, spent, i = 0, 0.0, 0
+    t_start = time.perf_counter()
+    while time.perf_counter() - t_start < target_s:
+        synth.fill_masks(ens, buf, [ids[i % len(ids)]])
+        t0 = time.perf_counter()
+        oracle.count_apply(counts, buf, 1)
+        spent += time.perf_counter() - t0
+        done += 1
+        i += 1
+    out[first] = (done, spent, time.perf_counter() - t_start)
+
+
+def cpu_oracle_rate_all_cores(args, target_s: float):
+    """The oracle, unchanged, in one spawned process per host core, each on
+    its own members of the workload, all starting at one barrier; member-px/s
+    = all processes' member-pixels / the longest process's oracle time."""
+    import multiprocessing as mp
+    procs = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as mgr:
+        out = mgr.dict(procs=procs)
+        barrier = mgr.Barrier(procs)
+        ps = [ctx.Process(target=_oracle_worker, args=(args.seed, args.width, args.height, args.members, i,
+                                                       target_s, barrier, out)) for i in range(procs)]
+        for p in ps:
+            p.start()
+        for p in ps:
+            p.join(timeout=600)
+        res = [out.get(i) for i in range(procs)]
+    if any(r is None for r in res):
+        return None
+    done = sum(r[0] for r in res)
+    spent = max(r[1] for r in res)
+    return {"value": done * args.width * args.height / spent, "unit": UNIT, "cores": procs, "kind": "oracle",
+            "sample": f"{done} member passes over {procs} processes, one member at a time "
+                      f"({spent:.1f} s of oracle time in the longest process)"}
 
 
 def run_reference(args):
@@ -429,11 +481,13 @@ def run_ours(args):
 
     clocks = sampler.stop() if sampler else None
 
-    cpu = None
+    cpu = cpu_all = None
     if rank == 0 and not args.no_cpu_baseline:
         rate, done, spent = cpu_oracle_rate(ens, N, args.cpu_seconds)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{done} of {N} members of the {W}x{H} workload ({spent:.1f} s, one thread)"}
+        if not args.no_cpu_all_cores:
+            cpu_all = cpu_oracle_rate_all_cores(args, args.cpu_seconds)
 
     if rank == 0:
         launches_per_step = 2
@@ -442,7 +496,8 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": workload_config(args), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "config": workload_config(args), "roofline": roofline, "cpu_baseline": cpu,
+            "cpu_baseline_all_cores": cpu_all, "e2e": e2e,
             "gpu_launches": args.steps * (launches_per_step + (launches_e2e if e2e else 0)),
             "clocks": clocks, "link": link,
         }

@@ -245,22 +245,6 @@ convert_to_array_kernel(const uint8_t *src, int64_t pitch, int64_t member_stride
     }
 }
 
-// Gathers n rasters, src + ids[i] * stride (host-mapped or device memory),
-// into dst + i * stride, 16 bytes per thread and step: the upload of many
-// scattered rasters as one launch instead of one copy per raster.
-__global__ void __launch_bounds__(kThreads)
-gather_rasters_kernel(uint8_t *dst, const uint8_t *src, const int32_t *ids, int n, int64_t stride,
-                      int64_t vecs_per_raster) {
-    const int64_t total = vecs_per_raster * n;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(t / vecs_per_raster);
-        const int64_t v = t - (int64_t)i * vecs_per_raster;
-        const uint4 x = __ldcs(reinterpret_cast<const uint4 *>(src + (int64_t)ids[i] * stride) + v);
-        reinterpret_cast<uint4 *>(dst + (int64_t)i * stride)[v] = x;
-    }
-}
-
 inline int64_t blocks_for(int64_t groups) {
     int64_t blocks = (groups + kThreads - 1) / kThreads;
     return blocks < 1 ? 1 : (blocks > 0x7FFFFFFF ? 0x7FFFFFFF : blocks);
@@ -339,18 +323,6 @@ cudaError_t launch_convert_to_array(const void *src, int64_t pitch, int64_t memb
     if (texels == 0) return cudaSuccess;
     convert_to_array_kernel<<<(unsigned)blocks_for(texels), kThreads, 0, s>>>(
         static_cast<const uint8_t *>(src), pitch, member_stride, surf, texels_per_row, height, texels);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_gather_rasters(void *dst, const void *src, const int32_t *ids, int n, int64_t stride,
-                                  int64_t raster_bytes, const DeviceCaps &caps, cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
-    const int64_t vecs = raster_bytes / 16;
-    // two CTAs per SM: enough loads in flight for the link, and room left for
-    // the compute kernels it overlaps
-    const int64_t blocks = std::min<int64_t>(blocks_for(vecs * n), (int64_t)caps.num_sms * 2);
-    gather_rasters_kernel<<<(unsigned)blocks, kThreads, 0, s>>>(
-        static_cast<uint8_t *>(dst), static_cast<const uint8_t *>(src), ids, n, stride, vecs);
     return cudaGetLastError();
 }
 

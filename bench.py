@@ -71,6 +71,8 @@ def parse_args():
     p.add_argument("--requests", type=int, default=200, help="serving: requests per offered rate")
     p.add_argument("--max-batch", type=int, default=64, help="serving: requests per cycle")
     p.add_argument("--poll-us", type=float, default=100.0, help="serving: host back-off between idle polls")
+    p.add_argument("--formats", nargs="+", choices=["bytes", "bits"], default=["bytes", "bits"],
+                   help="compressed: resident mask formats to time (--no-e2e skips the streamed forms)")
     p.add_argument("--staging-mib", type=int, default=1024,
                    help="serving: size of one overflow staging half, MiB (members = this / raster bytes)")
     p.add_argument("--mask-format", choices=["bytes", "bits"], default="bytes",
@@ -855,15 +857,22 @@ def sweep_compressed(args, torch, binding, device, stream):
     P = W * H
     ens = synth.ensemble(args.seed, W, H, N)
     tdev = torch.from_numpy(ens.terrain).to(device)
-    dev = torch.empty((N, H, W), dtype=torch.uint8, device=device)
-    synth.fill_masks_torch(ens, dev, terrain_t=tdev)
+    with_bytes = "bytes" in args.formats
+    dev = torch.empty((N if with_bytes else 64, H, W), dtype=torch.uint8, device=device)
     packed = torch.empty((N, H, W // 8), dtype=torch.uint8, device=device)
     for m0 in range(0, N, 64):
-        packed[m0:m0 + 64] = synth.pack_masks_torch(dev[m0:m0 + 64])
+        m1 = min(N, m0 + 64)
+        part = dev[m0:m1] if with_bytes else dev[: m1 - m0]
+        synth.fill_masks_torch(ens, part, range(m0, m1), terrain_t=tdev)
+        packed[m0:m1] = synth.pack_masks_torch(part)
+    if not with_bytes:
+        del dev
+        torch.cuda.empty_cache()
     peaks, _ = measured_peaks()
     out = {"sweep": "compressed", "width": W, "height": H, "members": N}
     counts = {}
-    for fmt, data in (("bytes", dev), ("bits", packed)):
+    for fmt in args.formats:
+        data = dev if fmt == "bytes" else packed
         with binding.Composite(W, H, stream=stream.cuda_stream, mask_format=fmt) as comp:
             def step():
                 comp.clear()
@@ -877,10 +886,15 @@ def sweep_compressed(args, torch, binding, device, stream):
         out[f"resident_{fmt}_member_px_per_s"] = N * P / (ms * 1e-3)
         out[f"resident_{fmt}_read_gbs"] = (N * P * bytes_per + 4 * P) / (ms * 1e-3) / 1e9
         out[f"resident_{fmt}_frac_of_hbm"] = out[f"resident_{fmt}_read_gbs"] / peaks["hbm_gbs"]
-    out["counts_identical"] = bool(np.array_equal(counts["bytes"], counts["bits"]))
+    if len(counts) == 2:
+        out["counts_identical"] = bool(np.array_equal(counts["bytes"], counts["bits"]))
+    if args.no_e2e:     # resident forms only
+        print(json.dumps(out), flush=True)
+        return
     host_packed = torch.empty((N, H, W // 8), dtype=torch.uint8, pin_memory=True)
     host_packed.copy_(packed)
-    del dev
+    if with_bytes:
+        del dev
     torch.cuda.empty_cache()
     h_bucket = np.empty((H, W), np.uint8)
     h_rgba = np.empty((H, W, 4), np.uint8)

@@ -303,8 +303,10 @@ int setup(composite_ctx *ctx) {
 }
 
 // The accumulation kernel over one batch already in device memory (a staging
-// slot, or the caller's own rasters when they can be read in place).
-int accumulate(composite_ctx *ctx, const RasterBatch &b, int sign) {
+// slot, or the caller's own rasters when they can be read in place), or in
+// pinned host memory read through its device mapping (host_mapped: only the
+// plain load kernels read it there, never a bulk or tensor copy).
+int accumulate(composite_ctx *ctx, const RasterBatch &b, int sign, bool host_mapped = false) {
     const bool count = ctx->cfg.mode == CPT_MODE_COUNT;
     const uint64_t tns = (uint64_t)timeout_ms(ctx) * 1000000ull;
     int rc = trace_open(ctx, kTraceKernel, ctx->compute);
@@ -318,7 +320,9 @@ int accumulate(composite_ctx *ctx, const RasterBatch &b, int sign) {
         e = count ? cpt::launch_count_tma(map, b, ctx->plane, sign, ctx->flags, tns, box, ctx->caps, ctx->compute)
                   : cpt::launch_depth_tma(map, b, ctx->plane, sign, ctx->flags, tns, box, ctx->caps, ctx->compute);
     } else if (ctx->bits) {
-        e = cpt::launch_count_bits(b, ctx->plane, sign, ctx->flags, ctx->caps, ctx->compute);
+        e = !host_mapped && cpt::bits_bulk_compatible(b, ctx->width, ctx->height)
+                ? cpt::launch_count_bits_bulk(b, ctx->plane, sign, ctx->flags, tns, ctx->caps, ctx->compute)
+                : cpt::launch_count_bits(b, ctx->plane, sign, ctx->flags, ctx->caps, ctx->compute);
     } else {
         e = count ? cpt::launch_count_linear(b, ctx->plane, sign, ctx->flags, ctx->caps, ctx->compute)
                   : cpt::launch_depth_linear(b, ctx->plane, sign, ctx->flags, ctx->caps, ctx->compute);
@@ -535,7 +539,7 @@ int apply(composite_ctx *ctx, const void *members, int32_t n, int64_t stride, in
             void *dptr = nullptr;
             CK(ctx, cudaHostGetDevicePointer(&dptr, const_cast<void *>(members), 0));
             RasterBatch b{dptr, stride, pitch, n};
-            rc = accumulate(ctx, b, sign);
+            rc = accumulate(ctx, b, sign, true);
         } else {
             rc = run_staged(ctx, src, n, stride, pitch, sign);
         }

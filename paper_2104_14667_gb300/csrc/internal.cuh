@@ -72,6 +72,13 @@ cudaError_t launch_depth_tma(const CUtensorMap &map, const RasterBatch &b, const
                              int *flags, uint64_t timeout_ns, int box_bytes, const DeviceCaps &caps,
                              cudaStream_t s);
 bool tma_box_supported(int box_bytes);
+// Bit-packed masks through cp.async.bulk copies of contiguous 2 KiB pieces
+// into a shared-memory ring (device memory only).  Needs unpadded rows (width
+// a multiple of 32, row pitch width / 8), a 16-byte aligned base and member
+// stride, and width / 32 * height a multiple of 4; bits_bulk_compatible says.
+bool bits_bulk_compatible(const RasterBatch &b, int width, int height);
+cudaError_t launch_count_bits_bulk(const RasterBatch &b, const Plane &p, int sign, int *flags, uint64_t timeout_ns,
+                                   const DeviceCaps &caps, cudaStream_t s);
 // One thread waits, bounded by timeout_ns, on an mbarrier nothing arrives at
 // (the same wait the TMA kernels use); status[0] = gave up, status[1] = ns.
 cudaError_t launch_bounded_wait_selftest(uint64_t timeout_ns, unsigned long long *status, cudaStream_t s);

@@ -10,6 +10,9 @@
 // "not flooded" and adds 0.0 to a depth sum.  Every mbarrier wait is bounded
 // in time; a wait that runs out raises the timeout flag and the CTA leaves
 // after draining its own copies in flight.
+#include <algorithm>
+#include <cstdint>
+
 #include <cudaTypedefs.h>
 
 #include "device_common.cuh"
@@ -261,6 +264,170 @@ depth_tma_kernel(const __grid_constant__ CUtensorMap map, Plane p, int n_members
     }
 }
 
+// ---- bit-packed masks through bulk copies -----------------------------------
+//
+// With unpadded bit rows (width a multiple of 32, row pitch width / 8) a
+// member's raster is one run of 32-pixel words, so a tile of kBitsTileWords
+// consecutive words is one contiguous 2 KiB piece of every member.  The
+// producer warp streams the pieces of 16 members per stage with cp.async.bulk
+// (no tensor map: one lane per member) into a ring of shared-memory stages;
+// eight consumer warps keep the counts of 64 pixels per thread in carry-save
+// accumulators.  The bytes in flight wait in shared memory instead of
+// registers, which is what limits the register kernel (launch_count_bits).
+// Work items are (member slab, tile), slab-major so that concurrently running
+// CTAs read neighbouring pieces of the same members, dealt to the persistent
+// CTAs round robin.  A slab is at most 15 stages (240 members): the counters
+// hold 255.
+constexpr int kBitsTileWords = 512;
+constexpr int kBitsTileBytes = kBitsTileWords * 4;
+constexpr int kBitsStageMembers = 16;
+constexpr int kBitsStageBytes = kBitsTileBytes * kBitsStageMembers;   // 32 KiB
+constexpr int kBitsStages = 6;
+constexpr int kBitsCtasPerSm = 1;
+constexpr int kBitsSlabStages = 15;
+constexpr int kBitsConsumerWarps = 8;
+constexpr int kBitsConsumers = kBitsConsumerWarps * 32;              // two words each
+constexpr int kBitsThreads = kBitsConsumers + 32;                    // + the producer warp
+
+struct alignas(128) BitsShared {
+    uint8_t stage[kBitsStages][kBitsStageBytes];
+    uint64_t full[kBitsStages];
+    uint64_t empty[kBitsStages];
+    int abort;
+};
+constexpr size_t kBitsSmemBytes = sizeof(BitsShared) + 128;
+
+struct BitsWork {
+    const uint8_t *base;
+    int64_t stride;          // member stride, bytes
+    int64_t words;           // 32-pixel words per member
+    int words_per_row;
+    int tiles;
+    int slabs;
+    int slab_stages;
+    int n;
+};
+
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// The producer warp: lane 0 waits for a free stage and announces its bytes,
+// then lane k copies member k's piece.
+__device__ void produce_bits(BitsShared &sh, const BitsWork &w, uint64_t timeout_ns, int *flags) {
+    const int lane = threadIdx.x & 31;
+    uint32_t it = 0;
+    bool ok = true;
+    for (int item = blockIdx.x; ok && item < w.slabs * w.tiles; item += gridDim.x) {
+        const int slab = item / w.tiles, tile = item - slab * w.tiles;
+        const int m0 = slab * w.slab_stages * kBitsStageMembers;
+        const int m1 = min(w.n, m0 + w.slab_stages * kBitsStageMembers);
+        const int64_t word0 = (int64_t)tile * kBitsTileWords;
+        const uint32_t bytes = (uint32_t)(min((int64_t)kBitsTileWords, w.words - word0) * 4);
+        for (int ms = m0; ms < m1; ms += kBitsStageMembers, ++it) {
+            const int s = it % kBitsStages;
+            const int cnt = min(kBitsStageMembers, m1 - ms);
+            bool got = true;
+            if (lane == 0) {
+                got = wait_bounded(&sh.empty[s], ((it / kBitsStages) & 1u) ^ 1u, timeout_ns, &sh.abort);
+                if (got) mbar_arrive_expect_tx(&sh.full[s], bytes * (uint32_t)cnt);
+            }
+            ok = __shfl_sync(0xFFFFFFFFu, got, 0);
+            if (!ok) break;
+            if (lane < cnt)
+                bulk_load(sh.stage[s] + lane * kBitsTileBytes, w.base + (int64_t)(ms + lane) * w.stride + word0 * 4,
+                          bytes, &sh.full[s]);
+        }
+    }
+    if (!ok && lane == 0) {
+        flag_set(flags, kFlagTimeout);
+        sh.abort = 1;
+        // Drain: every piece still in flight lands before the CTA may exit.
+        const uint32_t first = it > (uint32_t)kBitsStages ? it - kBitsStages : 0u;
+        for (uint32_t j = first; j < it; ++j) {
+            int dummy = 0;
+            wait_bounded(&sh.full[j % kBitsStages], (j / kBitsStages) & 1u, timeout_ns, &dummy);
+        }
+    }
+}
+
+template <typename CountT>
+__global__ void __launch_bounds__(kBitsThreads, kBitsCtasPerSm)
+count_bits_bulk_kernel(BitsWork w, Plane p, int sign, int *flags, uint64_t timeout_ns) {
+    extern __shared__ uint8_t smem_raw[];
+    BitsShared &sh = *reinterpret_cast<BitsShared *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kBitsStages; ++s) {
+            mbar_init(&sh.full[s], 1);
+            mbar_init(&sh.empty[s], kBitsConsumerWarps);
+        }
+        sh.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (threadIdx.x >= kBitsConsumers) {
+        produce_bits(sh, w, timeout_ns, flags);
+        return;
+    }
+
+    CountT *plane = static_cast<CountT *>(p.data);
+    const int tid = threadIdx.x;
+    uint32_t it = 0;
+    for (int item = blockIdx.x; item < w.slabs * w.tiles; item += gridDim.x) {
+        const int slab = item / w.tiles, tile = item - slab * w.tiles;
+        const int m0 = slab * w.slab_stages * kBitsStageMembers;
+        const int m1 = min(w.n, m0 + w.slab_stages * kBitsStageMembers);
+        BitCounter acc[2];
+        for (int ms = m0; ms < m1; ms += kBitsStageMembers, ++it) {
+            const int s = it % kBitsStages;
+            const int cnt = min(kBitsStageMembers, m1 - ms);
+            if (!wait_bounded(&sh.full[s], (it / kBitsStages) & 1u, timeout_ns, &sh.abort)) {
+                flag_set(flags, kFlagTimeout);
+                sh.abort = 1;
+                return;
+            }
+            const uint8_t *src = sh.stage[s] + 8 * tid;
+            uint32_t w0[16], w1[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                uint2 v = make_uint2(0u, 0u);
+                if (k < cnt) v = *reinterpret_cast<const uint2 *>(src + k * kBitsTileBytes);
+                w0[k] = v.x;
+                w1[k] = v.y;
+            }
+            bitcount_add16(acc[0], w0);
+            bitcount_add16(acc[1], w1);
+            __syncwarp();
+            if ((tid & 31) == 0) mbar_arrive(&sh.empty[s]);
+        }
+        // words past the raster's last (a partial tile) hold stale bytes and are skipped
+        const int64_t word0 = (int64_t)tile * kBitsTileWords + 2 * tid;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int64_t g = word0 + j;
+            if (g >= w.words) break;
+            const int y = (int)(g / w.words_per_row);
+            const int x0 = 32 * (int)(g - (int64_t)y * w.words_per_row);
+            CountT *dst = plane + (int64_t)y * p.pitch + x0;
+            uint32_t pairs[16];
+            bitcount_pairs(acc[j], pairs);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (w.slabs == 1)
+                    apply_pair_group<CountT>(dst + 16 * h, 16, pairs + 8 * h, sign, flags);
+                else
+                    atomic_pair_group<CountT>(dst + 16 * h, pairs + 8 * h, sign, flags);
+            }
+        }
+    }
+}
+
 // Runs the bounded wait of the TMA kernels on an mbarrier that nothing
 // arrives at: it must give up after timeout_ns and report it.  status[0] =
 // 1 if the wait gave up, status[1] = nanoseconds it waited.
@@ -383,6 +550,48 @@ cudaError_t launch_count_tma(const CUtensorMap &map, const RasterBatch &b, const
         default:
             return cudaErrorInvalidValue;
     }
+}
+
+bool bits_bulk_compatible(const RasterBatch &b, int width, int height) {
+    return width % 32 == 0 && b.row_pitch == width / 8 && reinterpret_cast<uintptr_t>(b.base) % 16 == 0 &&
+           b.member_stride % 16 == 0 && ((int64_t)(width / 32) * height) % 4 == 0;
+}
+
+cudaError_t launch_count_bits_bulk(const RasterBatch &b, const Plane &p, int sign, int *flags, uint64_t timeout_ns,
+                                   const DeviceCaps &caps, cudaStream_t s) {
+    if (b.n <= 0 || p.width == 0 || p.height == 0) return cudaSuccess;
+    if (!bits_bulk_compatible(b, p.width, p.height)) return cudaErrorInvalidValue;
+    BitsWork w;
+    w.base = static_cast<const uint8_t *>(b.base);
+    w.stride = b.member_stride;
+    w.words_per_row = p.width / 32;
+    w.words = (int64_t)w.words_per_row * p.height;
+    const int64_t tiles = (w.words + kBitsTileWords - 1) / kBitsTileWords;
+    if (tiles > (1 << 24)) return cudaErrorInvalidValue;
+    w.tiles = (int)tiles;
+    w.n = b.n;
+    // slabs of at most 15 stages; more if needed for about eight items per CTA
+    const int stages = (b.n + kBitsStageMembers - 1) / kBitsStageMembers;
+    int slabs = (stages + kBitsSlabStages - 1) / kBitsSlabStages;
+    const int want = (int)std::min<int64_t>((8ll * kBitsCtasPerSm * caps.num_sms + tiles - 1) / tiles, stages);
+    slabs = std::max(slabs, want);
+    w.slab_stages = (stages + slabs - 1) / slabs;
+    w.slabs = (stages + w.slab_stages - 1) / w.slab_stages;
+    const int64_t items = (int64_t)w.slabs * w.tiles;
+    if (items > INT32_MAX) return cudaErrorInvalidValue;
+    const unsigned grid = (unsigned)std::min<int64_t>(items, (int64_t)kBitsCtasPerSm * caps.num_sms);
+    if (p.count_bits == 16) {
+        static cudaError_t prep = cudaFuncSetAttribute(count_bits_bulk_kernel<uint16_t>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBitsSmemBytes);
+        if (prep != cudaSuccess) return prep;
+        count_bits_bulk_kernel<uint16_t><<<grid, kBitsThreads, kBitsSmemBytes, s>>>(w, p, sign, flags, timeout_ns);
+    } else {
+        static cudaError_t prep = cudaFuncSetAttribute(count_bits_bulk_kernel<uint32_t>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBitsSmemBytes);
+        if (prep != cudaSuccess) return prep;
+        count_bits_bulk_kernel<uint32_t><<<grid, kBitsThreads, kBitsSmemBytes, s>>>(w, p, sign, flags, timeout_ns);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_depth_tma(const CUtensorMap &map, const RasterBatch &b, const Plane &p, int sign,

@@ -293,6 +293,37 @@ def test_bit_packed_masks(kind, w, h, n):
         check_counts(comp, m)
 
 
+@pytest.mark.parametrize("kind", ["device", "pinned"])
+@pytest.mark.parametrize("w,h,n", [(256, 96, 300), (64, 4, 20), (128, 64, 7), (2048, 2, 33), (4096, 128, 1000)])
+def test_bit_packed_bulk_copy_layouts(kind, w, h, n):
+    # width a multiple of 32 and unpadded rows: the rasters reach the kernel
+    # by bulk copies into shared memory (partial last tiles and stages, one
+    # member slab folded in place, several folded by atomics)
+    m = synth.scramble_nonzero(synth.random_masks(140 + w + n, n, h, w, density=0.3), 140)
+    packed = synth.pack_masks(m)
+    with binding.Composite(w, h, mask_format="bits", chunk_members=255) as comp:
+        comp.add(as_kind(packed, kind))
+        check_counts(comp, m)
+
+
+@pytest.mark.parametrize("count_bits", [16, 32])
+def test_bit_packed_bulk_copy_remove_and_underflow(count_bits):
+    w, h = 320, 40
+    a = synth.random_masks(150, 250, h, w)
+    b = synth.random_masks(151, 9, h, w)
+    with binding.Composite(w, h, mask_format="bits", chunk_members=255, count_bits=count_bits) as comp:
+        comp.add(as_kind(synth.pack_masks(a), "device"))
+        comp.add(as_kind(synth.pack_masks(b), "device"))
+        comp.remove(as_kind(synth.pack_masks(a), "device"))
+        check_counts(comp, b)
+        comp.clear()
+        comp.add(as_kind(synth.pack_masks(synth.random_masks(152, 3, h, w, density=0.05)), "device"))
+        comp.remove(as_kind(synth.pack_masks(a[:1]), "device"))
+        with pytest.raises(binding.CompositeError) as e:
+            comp.render_host()
+        assert e.value.code == binding.CPT_EUNDERFLOW
+
+
 @pytest.mark.parametrize("k,c", [(1, 3), (2, 255), (3, 16)])
 def test_bit_packed_add_remove_and_32bit(k, c):
     w, h = 77, 45

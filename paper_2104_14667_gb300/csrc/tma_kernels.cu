@@ -272,11 +272,17 @@ depth_tma_kernel(const __grid_constant__ CUtensorMap map, Plane p, int n_members
 // producer warp streams the pieces of 16 members per stage with cp.async.bulk
 // (no tensor map: one lane per member) into a ring of shared-memory stages;
 // eight consumer warps keep the counts of 64 pixels per thread in carry-save
-// accumulators.  The bytes in flight wait in shared memory instead of
+// accumulators (two independent chains per thread: sixteen warps of 32
+// pixels were slower).  The bytes in flight wait in shared memory instead of
 // registers, which is what limits the register kernel (launch_count_bits).
-// Work items are (member slab, tile), slab-major so that concurrently running
-// CTAs read neighbouring pieces of the same members, dealt to the persistent
-// CTAs round robin.  A slab is at most 15 stages (240 members): the counters
+// Work items are (tile, member slab).  They are numbered in blocks of one
+// tile per CTA, slab after slab within a block, and dealt to the persistent
+// CTAs round robin, so CTA c takes tile c of the block through all its slabs
+// in turn: no two CTAs fold into one tile at the same time, and the tile's
+// counts stay in L2 between its slabs.  (Slab-major numbering streamed the
+// whole mask set between two visits of a tile and re-read the count plane
+// from DRAM once per slab; tile-major numbering had up to 18 CTAs folding
+// atomics into the same tile.)  A slab is at most 15 stages (240 members): the counters
 // hold 255.
 constexpr int kBitsTileWords = 512;
 constexpr int kBitsTileBytes = kBitsTileWords * 4;
@@ -285,8 +291,9 @@ constexpr int kBitsStageBytes = kBitsTileBytes * kBitsStageMembers;   // 32 KiB
 constexpr int kBitsStages = 6;
 constexpr int kBitsCtasPerSm = 1;
 constexpr int kBitsSlabStages = 15;
-constexpr int kBitsConsumerWarps = 8;
-constexpr int kBitsConsumers = kBitsConsumerWarps * 32;              // two words each
+constexpr int kBitsWordsPerThread = 2;
+constexpr int kBitsConsumers = kBitsTileWords / kBitsWordsPerThread;
+constexpr int kBitsConsumerWarps = kBitsConsumers / 32;
 constexpr int kBitsThreads = kBitsConsumers + 32;                    // + the producer warp
 
 struct alignas(128) BitsShared {
@@ -306,7 +313,19 @@ struct BitsWork {
     int slabs;
     int slab_stages;
     int n;
+    int block_tiles;         // tiles per block of items (the grid size)
 };
+
+// The (tile, slab) of work item `item`.
+__device__ __forceinline__ void bits_item(const BitsWork &w, int item, int &tile, int &slab) {
+    const int per_block = w.block_tiles * w.slabs;
+    const int block = item / per_block;
+    const int r = item - block * per_block;
+    const int first = block * w.block_tiles;
+    const int in_block = min(w.block_tiles, w.tiles - first);
+    slab = r / in_block;
+    tile = first + (r - slab * in_block);
+}
 
 __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
     asm volatile(
@@ -323,7 +342,8 @@ __device__ void produce_bits(BitsShared &sh, const BitsWork &w, uint64_t timeout
     uint32_t it = 0;
     bool ok = true;
     for (int item = blockIdx.x; ok && item < w.slabs * w.tiles; item += gridDim.x) {
-        const int slab = item / w.tiles, tile = item - slab * w.tiles;
+        int tile, slab;
+        bits_item(w, item, tile, slab);
         const int m0 = slab * w.slab_stages * kBitsStageMembers;
         const int m1 = min(w.n, m0 + w.slab_stages * kBitsStageMembers);
         const int64_t word0 = (int64_t)tile * kBitsTileWords;
@@ -380,10 +400,11 @@ count_bits_bulk_kernel(BitsWork w, Plane p, int sign, int *flags, uint64_t timeo
     const int tid = threadIdx.x;
     uint32_t it = 0;
     for (int item = blockIdx.x; item < w.slabs * w.tiles; item += gridDim.x) {
-        const int slab = item / w.tiles, tile = item - slab * w.tiles;
+        int tile, slab;
+        bits_item(w, item, tile, slab);
         const int m0 = slab * w.slab_stages * kBitsStageMembers;
         const int m1 = min(w.n, m0 + w.slab_stages * kBitsStageMembers);
-        BitCounter acc[2];
+        BitCounter acc[kBitsWordsPerThread];
         for (int ms = m0; ms < m1; ms += kBitsStageMembers, ++it) {
             const int s = it % kBitsStages;
             const int cnt = min(kBitsStageMembers, m1 - ms);
@@ -392,24 +413,32 @@ count_bits_bulk_kernel(BitsWork w, Plane p, int sign, int *flags, uint64_t timeo
                 sh.abort = 1;
                 return;
             }
-            const uint8_t *src = sh.stage[s] + 8 * tid;
-            uint32_t w0[16], w1[16];
+            const uint8_t *src = sh.stage[s] + 4 * kBitsWordsPerThread * tid;
+            if constexpr (kBitsWordsPerThread == 2) {
+                uint32_t w0[16], w1[16];
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                uint2 v = make_uint2(0u, 0u);
-                if (k < cnt) v = *reinterpret_cast<const uint2 *>(src + k * kBitsTileBytes);
-                w0[k] = v.x;
-                w1[k] = v.y;
+                for (int k = 0; k < 16; ++k) {
+                    uint2 v = make_uint2(0u, 0u);
+                    if (k < cnt) v = *reinterpret_cast<const uint2 *>(src + k * kBitsTileBytes);
+                    w0[k] = v.x;
+                    w1[k] = v.y;
+                }
+                bitcount_add16(acc[0], w0);
+                bitcount_add16(acc[1], w1);
+            } else {
+                uint32_t w0[16];
+#pragma unroll
+                for (int k = 0; k < 16; ++k)
+                    w0[k] = k < cnt ? *reinterpret_cast<const uint32_t *>(src + k * kBitsTileBytes) : 0u;
+                bitcount_add16(acc[0], w0);
             }
-            bitcount_add16(acc[0], w0);
-            bitcount_add16(acc[1], w1);
             __syncwarp();
             if ((tid & 31) == 0) mbar_arrive(&sh.empty[s]);
         }
         // words past the raster's last (a partial tile) hold stale bytes and are skipped
-        const int64_t word0 = (int64_t)tile * kBitsTileWords + 2 * tid;
+        const int64_t word0 = (int64_t)tile * kBitsTileWords + kBitsWordsPerThread * tid;
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
+        for (int j = 0; j < kBitsWordsPerThread; ++j) {
             const int64_t g = word0 + j;
             if (g >= w.words) break;
             const int y = (int)(g / w.words_per_row);
@@ -580,6 +609,7 @@ cudaError_t launch_count_bits_bulk(const RasterBatch &b, const Plane &p, int sig
     const int64_t items = (int64_t)w.slabs * w.tiles;
     if (items > INT32_MAX) return cudaErrorInvalidValue;
     const unsigned grid = (unsigned)std::min<int64_t>(items, (int64_t)kBitsCtasPerSm * caps.num_sms);
+    w.block_tiles = (int)std::min<int64_t>(grid, w.tiles);
     if (p.count_bits == 16) {
         static cudaError_t prep = cudaFuncSetAttribute(count_bits_bulk_kernel<uint16_t>,
                                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBitsSmemBytes);

@@ -226,17 +226,16 @@ __device__ __forceinline__ void process_bits_item(const OpDesc &op, uint32_t ite
             cpt::bitcount_add16(acc, w);
         }
         uint32_t *dst = op.plane + (int64_t)y * op.plane_pitch + x0;
+        uint32_t pairs[16];
+        cpt::bitcount_pairs(acc, pairs);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int v = min(16, valid - 16 * h);
             if (v <= 0) break;
-            uint32_t wide[16];
-#pragma unroll
-            for (int k = 0; k < 16; ++k) wide[k] = cpt::bitcount_get(acc, 16 * h + k);
             if (op.exclusive)
-                cpt::apply_count_group<uint32_t>(dst + 16 * h, v, wide, op.sign, flags + op.plane_id);
+                cpt::apply_pair_group<uint32_t>(dst + 16 * h, v, pairs + 8 * h, op.sign, flags + op.plane_id);
             else
-                cpt::atomic_count_group<uint32_t>(dst + 16 * h, wide, op.sign, flags + op.plane_id);
+                cpt::atomic_pair_group<uint32_t>(dst + 16 * h, pairs + 8 * h, op.sign, flags + op.plane_id);
         }
     }
     if (gather) __syncwarp();

@@ -270,11 +270,15 @@ depth_tma_kernel(const __grid_constant__ CUtensorMap map, Plane p, int n_members
 // member's raster is one run of 32-pixel words, so a tile of kBitsTileWords
 // consecutive words is one contiguous 2 KiB piece of every member.  The
 // producer warp streams the pieces of 16 members per stage with cp.async.bulk
-// (no tensor map: one lane per member) into a ring of shared-memory stages;
-// eight consumer warps keep the counts of 64 pixels per thread in carry-save
-// accumulators (two independent chains per thread: sixteen warps of 32
-// pixels were slower).  The bytes in flight wait in shared memory instead of
-// registers, which is what limits the register kernel (launch_count_bits).
+// (no tensor map: one lane per member) into a ring of seven 32 KiB
+// shared-memory stages; four consumer warps keep the counts of 128 pixels per
+// thread in carry-save accumulators, four independent chains per thread.
+// The bytes in flight wait in shared memory instead of registers, which is
+// what limits the register kernel (launch_count_bits).  Measured shapes
+// (4096^2 x 1024, ms per pass): 4 warps x 128 pixels 0.371 with a 192 KiB
+// ring, 0.367 with 224 KiB, 0.398 with 128 KiB; 8 x 64 0.378; 16 x 64
+// 0.404; 4 x 64 (1 KiB pieces) 0.613; two or three CTAs per SM with smaller
+// rings 0.403.
 // Work items are (tile, member slab).  They are numbered in blocks of one
 // tile per CTA, slab after slab within a block, and dealt to the persistent
 // CTAs round robin, so CTA c takes tile c of the block through all its slabs
@@ -282,19 +286,23 @@ depth_tma_kernel(const __grid_constant__ CUtensorMap map, Plane p, int n_members
 // counts stay in L2 between its slabs.  (Slab-major numbering streamed the
 // whole mask set between two visits of a tile and re-read the count plane
 // from DRAM once per slab; tile-major numbering had up to 18 CTAs folding
-// atomics into the same tile.)  A slab is at most 15 stages (240 members): the counters
-// hold 255.
-constexpr int kBitsTileWords = 512;
+// atomics into the same tile.)  A slab is at most 15 stages (240 members):
+// the counters hold 255.
+constexpr int kBitsConsumerWarps = 4;
+constexpr int kBitsWordsPerThread = 4;
+constexpr int kBitsConsumers = kBitsConsumerWarps * 32;
+constexpr int kBitsThreads = kBitsConsumers + 32;                    // + the producer warp
+constexpr int kBitsTileWords = kBitsConsumers * kBitsWordsPerThread;
 constexpr int kBitsTileBytes = kBitsTileWords * 4;
 constexpr int kBitsStageMembers = 16;
-constexpr int kBitsStageBytes = kBitsTileBytes * kBitsStageMembers;   // 32 KiB
-constexpr int kBitsStages = 6;
+constexpr int kBitsStageBytes = kBitsTileBytes * kBitsStageMembers;
+constexpr int kBitsRingBytes = 224 * 1024;
+constexpr int kBitsStages = kBitsRingBytes / kBitsStageBytes;
 constexpr int kBitsCtasPerSm = 1;
 constexpr int kBitsSlabStages = 15;
-constexpr int kBitsWordsPerThread = 2;
-constexpr int kBitsConsumers = kBitsTileWords / kBitsWordsPerThread;
-constexpr int kBitsConsumerWarps = kBitsConsumers / 32;
-constexpr int kBitsThreads = kBitsConsumers + 32;                    // + the producer warp
+static_assert(kBitsStages >= 2, "the ring needs two stages");
+static_assert(kBitsWordsPerThread == 1 || kBitsWordsPerThread == 2 || kBitsWordsPerThread == 4,
+              "a consumer reads 4, 8 or 16 bytes per member");
 
 struct alignas(128) BitsShared {
     uint8_t stage[kBitsStages][kBitsStageBytes];
@@ -303,6 +311,7 @@ struct alignas(128) BitsShared {
     int abort;
 };
 constexpr size_t kBitsSmemBytes = sizeof(BitsShared) + 128;
+static_assert(kBitsSmemBytes <= 227 * 1024, "shared memory per CTA");
 
 struct BitsWork {
     const uint8_t *base;
@@ -336,7 +345,8 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
 }
 
 // The producer warp: lane 0 waits for a free stage and announces its bytes,
-// then lane k copies member k's piece.
+// then lane k copies member k's piece.  (One tensor-map box per stage --
+// {256 words, 2 rows, 16 members} -- was slower: 0.381 against 0.367 ms.)
 __device__ void produce_bits(BitsShared &sh, const BitsWork &w, uint64_t timeout_ns, int *flags) {
     const int lane = threadIdx.x & 31;
     uint32_t it = 0;
@@ -414,24 +424,27 @@ count_bits_bulk_kernel(BitsWork w, Plane p, int sign, int *flags, uint64_t timeo
                 return;
             }
             const uint8_t *src = sh.stage[s] + 4 * kBitsWordsPerThread * tid;
-            if constexpr (kBitsWordsPerThread == 2) {
-                uint32_t w0[16], w1[16];
+            uint32_t wv[kBitsWordsPerThread][16];
 #pragma unroll
-                for (int k = 0; k < 16; ++k) {
-                    uint2 v = make_uint2(0u, 0u);
-                    if (k < cnt) v = *reinterpret_cast<const uint2 *>(src + k * kBitsTileBytes);
-                    w0[k] = v.x;
-                    w1[k] = v.y;
+            for (int k = 0; k < 16; ++k) {
+                uint32_t v[4] = {0u, 0u, 0u, 0u};
+                if (k < cnt) {
+                    const uint8_t *q = src + k * kBitsTileBytes;
+                    if constexpr (kBitsWordsPerThread == 4) {
+                        const uint4 t = *reinterpret_cast<const uint4 *>(q);
+                        v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+                    } else if constexpr (kBitsWordsPerThread == 2) {
+                        const uint2 t = *reinterpret_cast<const uint2 *>(q);
+                        v[0] = t.x, v[1] = t.y;
+                    } else {
+                        v[0] = *reinterpret_cast<const uint32_t *>(q);
+                    }
                 }
-                bitcount_add16(acc[0], w0);
-                bitcount_add16(acc[1], w1);
-            } else {
-                uint32_t w0[16];
 #pragma unroll
-                for (int k = 0; k < 16; ++k)
-                    w0[k] = k < cnt ? *reinterpret_cast<const uint32_t *>(src + k * kBitsTileBytes) : 0u;
-                bitcount_add16(acc[0], w0);
+                for (int j = 0; j < kBitsWordsPerThread; ++j) wv[j][k] = v[j];
             }
+#pragma unroll
+            for (int j = 0; j < kBitsWordsPerThread; ++j) bitcount_add16(acc[j], wv[j]);
             __syncwarp();
             if ((tid & 31) == 0) mbar_arrive(&sh.empty[s]);
         }
@@ -586,6 +599,16 @@ bool bits_bulk_compatible(const RasterBatch &b, int width, int height) {
            b.member_stride % 16 == 0 && ((int64_t)(width / 32) * height) % 4 == 0;
 }
 
+template <typename CountT>
+cudaError_t launch_bits_bulk_t(const BitsWork &w, unsigned grid, const Plane &p, int sign, int *flags,
+                               uint64_t timeout_ns, cudaStream_t s) {
+    static cudaError_t prep = cudaFuncSetAttribute(count_bits_bulk_kernel<CountT>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBitsSmemBytes);
+    if (prep != cudaSuccess) return prep;
+    count_bits_bulk_kernel<CountT><<<grid, kBitsThreads, kBitsSmemBytes, s>>>(w, p, sign, flags, timeout_ns);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_count_bits_bulk(const RasterBatch &b, const Plane &p, int sign, int *flags, uint64_t timeout_ns,
                                    const DeviceCaps &caps, cudaStream_t s) {
     if (b.n <= 0 || p.width == 0 || p.height == 0) return cudaSuccess;
@@ -610,18 +633,8 @@ cudaError_t launch_count_bits_bulk(const RasterBatch &b, const Plane &p, int sig
     if (items > INT32_MAX) return cudaErrorInvalidValue;
     const unsigned grid = (unsigned)std::min<int64_t>(items, (int64_t)kBitsCtasPerSm * caps.num_sms);
     w.block_tiles = (int)std::min<int64_t>(grid, w.tiles);
-    if (p.count_bits == 16) {
-        static cudaError_t prep = cudaFuncSetAttribute(count_bits_bulk_kernel<uint16_t>,
-                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBitsSmemBytes);
-        if (prep != cudaSuccess) return prep;
-        count_bits_bulk_kernel<uint16_t><<<grid, kBitsThreads, kBitsSmemBytes, s>>>(w, p, sign, flags, timeout_ns);
-    } else {
-        static cudaError_t prep = cudaFuncSetAttribute(count_bits_bulk_kernel<uint32_t>,
-                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBitsSmemBytes);
-        if (prep != cudaSuccess) return prep;
-        count_bits_bulk_kernel<uint32_t><<<grid, kBitsThreads, kBitsSmemBytes, s>>>(w, p, sign, flags, timeout_ns);
-    }
-    return cudaGetLastError();
+    return p.count_bits == 16 ? launch_bits_bulk_t<uint16_t>(w, grid, p, sign, flags, timeout_ns, s)
+                              : launch_bits_bulk_t<uint32_t>(w, grid, p, sign, flags, timeout_ns, s);
 }
 
 cudaError_t launch_depth_tma(const CUtensorMap &map, const RasterBatch &b, const Plane &p, int sign,

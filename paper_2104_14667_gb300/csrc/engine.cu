@@ -23,7 +23,7 @@
 #include <vector>
 
 #include "composite_engine.h"
-#include "device_common.cuh"
+#include "bit_count.cuh"
 
 namespace {
 

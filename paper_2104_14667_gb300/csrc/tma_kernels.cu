@@ -15,7 +15,7 @@
 
 #include <cudaTypedefs.h>
 
-#include "device_common.cuh"
+#include "bit_count.cuh"
 
 namespace cpt {
 namespace {

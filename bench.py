@@ -661,12 +661,23 @@ def sweep_streaming(args, torch, binding, device, stream, sides=None, counts=Non
         copies = [(float(a), float(b)) for kk, a, b in rec if int(kk) == 0]
         kernels = [(float(a), float(b)) for kk, a, b in rec if int(kk) != 0]
         gbs = n * P / (ms * 1e-3) / 1e9
+        # Section 7.1's model over the traced chunks: copy c_i, no layout
+        # transform on the linear path, processing p_i; beside the traced wall
+        model = {}
+        ups = sorted(copies)
+        ks = sorted((float(a), float(b)) for kk, a, b in rec if int(kk) == 2)
+        if ups and len(ups) == len(ks):
+            c = [b - a for a, b in ups]
+            pk = [b - a for a, b in ks]
+            model = {"model_wall_ms": metrics.pipeline_wall(c, [0.0] * len(c), pk),
+                     "traced_wall_ms": max(b for _, b in ks) - min(a for a, _ in ups),
+                     "paper_e": metrics.pipeline_ratio(c, [0.0] * len(c), pk), "traced_chunks": len(c)}
         print(json.dumps({"sweep": "streaming", "side": side, "members": n, "chunk_members": chunk,
                           "staging_buffers": k, "pool_members": pool_n, "ms_per_pass": ms,
                           "member_px_per_s": n * P / (ms * 1e-3), "h2d_gbs": gbs,
                           "link_peak_gbs": peak, "link_frac": gbs / peak,
                           "overlap_fraction": metrics.overlap_fraction(copies, kernels),
-                          "mb_per_100ms": gbs * 100.0}), flush=True)
+                          "mb_per_100ms": gbs * 100.0, **model}), flush=True)
     pools.clear()
 
 

@@ -71,6 +71,8 @@ def parse_args():
     p.add_argument("--requests", type=int, default=200, help="serving: requests per offered rate")
     p.add_argument("--max-batch", type=int, default=64, help="serving: requests per cycle")
     p.add_argument("--poll-us", type=float, default=100.0, help="serving: host back-off between idle polls")
+    p.add_argument("--paths", nargs="+", choices=["linear", "texture", "tma"], default=["linear", "texture", "tma"],
+                   help="readpath: read paths to time")
     p.add_argument("--formats", nargs="+", choices=["bytes", "bits"], default=["bytes", "bits"],
                    help="compressed: resident mask formats to time (--no-e2e skips the streamed forms)")
     p.add_argument("--staging-mib", type=int, default=1024,
@@ -548,6 +550,8 @@ def sweep_readpath(args, torch, binding, device, stream):
             synth.fill_depths_torch(ens, data, terrain_t=terrain_t)
         for path, box, conv in (("linear", 0, "kernel"), ("texture", 0, "copy"), ("texture", 0, "kernel"),
                                 ("tma", 64, "kernel"), ("tma", 128, "kernel"), ("tma", 256, "kernel")):
+            if path not in args.paths:
+                continue
             cfg = dict(read_path=path, chunk_members=args.chunk, staging_buffers=args.staging,
                        mode=mode, stream=stream.cuda_stream, tma_box_bytes=box, layout_converter=conv)
             with binding.Composite(W, H, **cfg) as comp:

@@ -3,11 +3,11 @@
 // The batch is described to the tensor memory accelerator as a 3-D tensor
 // (x = pixel within a row, y = row, z = member).  A persistent CTA walks its
 // composite tiles (64, 128 or 256 bytes wide, 2 KiB per member); for every
-// tile one producer thread streams boxes of that tile x 8 members through a
+// tile one producer thread streams boxes of that tile x 16 members through a
 // ring of shared-memory stages with cp.async.bulk.tensor, and four consumer
-// warps fold each box into registers, one 16-byte group per thread.  Boxes past the raster's
-// edge or the last member are zero filled by the hardware, which counts as
-// "not flooded" and adds 0.0 to a depth sum.  Every mbarrier wait is bounded
+// warps fold each box into registers, one 16-byte group per thread.  Boxes
+// past the raster's edge or the last member are zero filled by the hardware,
+// which counts as "not flooded" and adds 0.0 to a depth sum.  Every mbarrier wait is bounded
 // in time; a wait that runs out raises the timeout flag and the CTA leaves
 // after draining its own copies in flight.
 #include <algorithm>
@@ -21,14 +21,18 @@ namespace cpt {
 namespace {
 
 // A box is kBoxX bytes x (2048 / kBoxX) rows x kBoxMembers members: 2 KiB
-// per member, 16 KiB per box, one 16-byte group per consumer thread and member.
+// per member, 32 KiB per box, one 16-byte group per consumer thread and
+// member; four stages, one CTA per SM.  Measured on 256 members at 4096^2
+// (256-byte boxes, ms per pass, masks / depths): 16 x 4 x 1 CTA 0.639-0.649 /
+// 2.36-2.39; 16 x 5 x 1 0.648 / 2.45; 16 x 3 x 1 0.661 / 2.47; 32 x 2 x 1
+// 0.648 / 2.40; 8 x 6 x 2 CTAs 0.680 / 2.48; 8 x 13 x 1 0.650 / 2.50.
 constexpr int kMemberPlaneBytes = 2048;
-constexpr int kBoxMembers = 8;                      // z extent
-constexpr int kBoxBytes = kMemberPlaneBytes * kBoxMembers;   // 16 KiB
-constexpr int kStages = 6;
+constexpr int kBoxMembers = 16;                      // z extent
+constexpr int kBoxBytes = kMemberPlaneBytes * kBoxMembers;   // 32 KiB
+constexpr int kStages = 4;
 constexpr int kConsumers = 128;                      // one 16-byte group each
 constexpr int kThreads = kConsumers + 32;            // + one producer warp
-constexpr int kCtasPerSm = 2;
+constexpr int kCtasPerSm = 1;
 
 struct alignas(128) TmaShared {
     uint8_t stage[kStages][kBoxBytes];

@@ -12,6 +12,9 @@
 // after draining its own copies in flight.
 #include <algorithm>
 #include <cstdint>
+#include <mutex>
+#include <set>
+#include <utility>
 
 #include <cudaTypedefs.h>
 
@@ -494,23 +497,32 @@ __global__ void bounded_wait_selftest_kernel(uint64_t timeout_ns, unsigned long 
     }
 }
 
-template <typename Kernel>
-cudaError_t prepare(Kernel k) {
-    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+// Raises a kernel's dynamic shared-memory limit to `bytes`, once per
+// (kernel, device): the attribute belongs to the device that is current when
+// it is set, so a process that drives several GPUs sets it on each.
+cudaError_t allow_smem(const void *kernel, size_t bytes) {
+    static std::mutex mu;
+    static std::set<std::pair<const void *, int>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count({kernel, dev})) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) done.insert({kernel, dev});
+    return e;
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
         cudaDriverEntryPointQueryResult q;
         void *ptr = nullptr;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000,
-                                             cudaEnableDefault, &q) == cudaSuccess &&
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
-    }
+            return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+        return nullptr;
+    }();
     return fn;
 }
 
@@ -558,7 +570,7 @@ template <typename CountT, int kBoxX>
 cudaError_t launch_count_tma_t(const CUtensorMap &map, const RasterBatch &b, const Plane &p, int sign,
                                int *flags, uint64_t timeout_ns, const DeviceCaps &caps, cudaStream_t s) {
     constexpr int kRows = kMemberPlaneBytes / kBoxX;
-    static cudaError_t prep = prepare(count_tma_kernel<CountT, kBoxX>);
+    const cudaError_t prep = allow_smem(reinterpret_cast<const void *>(count_tma_kernel<CountT, kBoxX>), kSmemBytes);
     if (prep != cudaSuccess) return prep;
     const int tiles = ((p.width + kBoxX - 1) / kBoxX) * ((p.height + kRows - 1) / kRows);
     count_tma_kernel<CountT, kBoxX><<<grid_for(tiles, caps), kThreads, kSmemBytes, s>>>(
@@ -570,7 +582,7 @@ template <int kBoxX>
 cudaError_t launch_depth_tma_t(const CUtensorMap &map, const RasterBatch &b, const Plane &p, int sign,
                                int *flags, uint64_t timeout_ns, const DeviceCaps &caps, cudaStream_t s) {
     constexpr int kRows = kMemberPlaneBytes / kBoxX;
-    static cudaError_t prep = prepare(depth_tma_kernel<kBoxX>);
+    const cudaError_t prep = allow_smem(reinterpret_cast<const void *>(depth_tma_kernel<kBoxX>), kSmemBytes);
     if (prep != cudaSuccess) return prep;
     const int tiles = ((p.width + kBoxX / 4 - 1) / (kBoxX / 4)) * ((p.height + kRows - 1) / kRows);
     depth_tma_kernel<kBoxX><<<grid_for(tiles, caps), kThreads, kSmemBytes, s>>>(map, p, b.n, sign, flags,
@@ -606,8 +618,7 @@ bool bits_bulk_compatible(const RasterBatch &b, int width, int height) {
 template <typename CountT>
 cudaError_t launch_bits_bulk_t(const BitsWork &w, unsigned grid, const Plane &p, int sign, int *flags,
                                uint64_t timeout_ns, cudaStream_t s) {
-    static cudaError_t prep = cudaFuncSetAttribute(count_bits_bulk_kernel<CountT>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBitsSmemBytes);
+    const cudaError_t prep = allow_smem(reinterpret_cast<const void *>(count_bits_bulk_kernel<CountT>), kBitsSmemBytes);
     if (prep != cudaSuccess) return prep;
     count_bits_bulk_kernel<CountT><<<grid, kBitsThreads, kBitsSmemBytes, s>>>(w, p, sign, flags, timeout_ns);
     return cudaGetLastError();

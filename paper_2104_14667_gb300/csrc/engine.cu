@@ -74,6 +74,8 @@ struct RenderDesc {
 };
 
 constexpr int kSmemStarts = 2048;      // ops whose first items fit in shared memory
+constexpr int kRenderGroups = 2;       // 16-pixel groups per lane per render item
+constexpr int kRenderCtasPerSm = 3;    // render launch: CTAs per SM, grid-stride over items
 
 template <typename Desc>
 __device__ __forceinline__ int find_desc(const Desc *d, int n, int64_t item) {
@@ -281,42 +283,54 @@ engine_accumulate_grid_kernel(const OpDesc *ops, int n_ops, uint32_t n_items, in
     run_item(ops[find_desc(ops, n_ops, item)], item, lane, s_index[threadIdx.x >> 5], flags);
 }
 
-__global__ void __launch_bounds__(kThreads)
-engine_render_kernel(const RenderDesc *ops, int n_ops, uint32_t n_items, uint32_t *counter, Lut lut) {
+// Render: warp-level items (render op, chunk of 32 x kRenderGroups 16-pixel
+// groups) dealt round robin to every warp of the launch -- items are all the
+// same size, so no counter is needed -- and a lane loads all its groups
+// before it classifies and stores any.
+__global__ void __launch_bounds__(kThreads, kRenderCtasPerSm)
+engine_render_kernel(const RenderDesc *ops, int n_ops, uint32_t n_items, Lut lut) {
     __shared__ uint32_t table[256];
-    __shared__ uint32_t s_item[2];
     __shared__ uint32_t s_starts[kSmemStarts];
     for (int i = threadIdx.x; i < 256; i += kThreads) table[i] = lut.rgba[i];
     load_starts(ops, n_ops, s_starts);
-    if (threadIdx.x == 0) s_item[0] = atomicAdd(counter, 1u);
-    for (int turn = 0;; turn ^= 1) {
-        __syncthreads();
-        const uint32_t item = s_item[turn];
-        if (item >= n_items) break;
-        if (threadIdx.x == 0) s_item[turn ^ 1] = atomicAdd(counter, 1u);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const uint32_t warps = gridDim.x * (kThreads / 32);
+    for (uint32_t item = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5); item < n_items; item += warps) {
         const RenderDesc &op = ops[find_op(ops, n_ops, s_starts, item)];
-        const int64_t g = (int64_t)(item - (uint32_t)op.item_start) * kThreads + threadIdx.x;
-        if (g < (int64_t)op.groups_per_row * op.height) {
+        const int64_t groups = (int64_t)op.groups_per_row * op.height;
+        const int64_t g0 = (int64_t)(item - (uint32_t)op.item_start) * (32 * kRenderGroups) + lane;
+        uint32_t c[kRenderGroups][16];
+#pragma unroll
+        for (int k = 0; k < kRenderGroups; ++k) {
+            const int64_t g = g0 + 32 * k;
+            if (g >= groups) break;
             const int y = (int)(g / op.groups_per_row);
             const int x0 = (int)(g - (int64_t)y * op.groups_per_row) * 16;
-            const int valid = min(16, op.width - x0);
             const uint4 *src = reinterpret_cast<const uint4 *>(op.plane + (int64_t)y * op.plane_pitch + x0);
-            uint32_t c[16];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const uint4 v = src[q];
-                c[4 * q] = v.x; c[4 * q + 1] = v.y; c[4 * q + 2] = v.z; c[4 * q + 3] = v.w;
+                c[k][4 * q] = v.x; c[k][4 * q + 1] = v.y; c[k][4 * q + 2] = v.z; c[k][4 * q + 3] = v.w;
             }
+        }
+#pragma unroll
+        for (int k = 0; k < kRenderGroups; ++k) {
+            const int64_t g = g0 + 32 * k;
+            if (g >= groups) break;
+            const int y = (int)(g / op.groups_per_row);
+            const int x0 = (int)(g - (int64_t)y * op.groups_per_row) * 16;
+            const int valid = min(16, op.width - x0);
             uint32_t b[16];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) b[j] = cpt::overlap_class(c[j], op.n_members);
+            for (int j = 0; j < 16; ++j) b[j] = cpt::overlap_class(c[k][j], op.n_members);
             const int64_t out = (int64_t)y * op.width + x0;
             if (op.vec && valid == 16) {
                 if (op.counts_out) {
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
                         reinterpret_cast<uint4 *>(op.counts_out + out)[q] =
-                            make_uint4(c[4 * q], c[4 * q + 1], c[4 * q + 2], c[4 * q + 3]);
+                            make_uint4(c[k][4 * q], c[k][4 * q + 1], c[k][4 * q + 2], c[k][4 * q + 3]);
                 }
                 if (op.bucket_out) {
                     uint32_t w[4];
@@ -335,7 +349,7 @@ engine_render_kernel(const RenderDesc *ops, int n_ops, uint32_t n_items, uint32_
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     if (j < valid) {
-                        if (op.counts_out) op.counts_out[out + j] = c[j];
+                        if (op.counts_out) op.counts_out[out + j] = c[k][j];
                         if (op.bucket_out) op.bucket_out[out + j] = (uint8_t)b[j];
                         if (op.rgba_out) op.rgba_out[out + j] = table[b[j]];
                     }
@@ -585,7 +599,7 @@ int plan_render(composite_engine *e, const composite_render_op *ops, int32_t n_o
         d.height = p.height;
         d.groups_per_row = (int32_t)(p.pitch_px / 16);
         const int64_t groups = (int64_t)d.groups_per_row * p.height;
-        d.tiles = (int32_t)((groups + kThreads - 1) / kThreads);
+        d.tiles = (int32_t)((groups + 32 * kRenderGroups - 1) / (32 * kRenderGroups));
         const uintptr_t a = reinterpret_cast<uintptr_t>(o.counts_out) | reinterpret_cast<uintptr_t>(o.bucket_out) |
                             reinterpret_cast<uintptr_t>(o.rgba_out);
         d.vec = (p.width % 16 == 0) && (a % 16 == 0);
@@ -618,11 +632,12 @@ int launch_accumulate(composite_engine *e, const void *d_ops, int n_ops, int64_t
     return CPT_OK;
 }
 
-int launch_render(composite_engine *e, const void *d_ops, int n_ops, int64_t n_items, uint32_t *counter,
+int launch_render(composite_engine *e, const void *d_ops, int n_ops, int64_t n_items, uint32_t *,
                   const Lut &lut) {
-    ECK(e, cudaMemsetAsync(counter, 0, sizeof(uint32_t), e->stream));
-    engine_render_kernel<<<persistent_grid(e, n_items), kThreads, 0, e->stream>>>(
-        static_cast<const RenderDesc *>(d_ops), n_ops, (uint32_t)n_items, counter, lut);
+    const int64_t ctas = std::min<int64_t>((int64_t)e->caps.num_sms * kRenderCtasPerSm,
+                                           (n_items + kThreads / 32 - 1) / (kThreads / 32));
+    engine_render_kernel<<<(unsigned)std::max<int64_t>(1, ctas), kThreads, 0, e->stream>>>(
+        static_cast<const RenderDesc *>(d_ops), n_ops, (uint32_t)n_items, lut);
     ECK(e, cudaGetLastError());
     return CPT_OK;
 }

@@ -71,6 +71,8 @@ def parse_args():
     p.add_argument("--requests", type=int, default=200, help="serving: requests per offered rate")
     p.add_argument("--max-batch", type=int, default=64, help="serving: requests per cycle")
     p.add_argument("--poll-us", type=float, default=100.0, help="serving: host back-off between idle polls")
+    p.add_argument("--engine-count-bits", type=int, choices=[16, 32], default=16,
+                   help="batched: count width of the engine's planes")
     p.add_argument("--paths", nargs="+", choices=["linear", "texture", "tma"], default=["linear", "texture", "tma"],
                    help="readpath: read paths to time")
     p.add_argument("--formats", nargs="+", choices=["bytes", "bits"], default=["bytes", "bits"],
@@ -723,7 +725,9 @@ def sweep_batched(args, torch, binding, device, stream):
         ctx.sync()
         ctx.close()
     eng = binding.Engine(stream=stream.cuda_stream)
-    planes = [eng.add_plane(w, h) for w, h, _ in reqs]
+    # 16-bit planes, like the plain runs' counts: no request exceeds 65535 members
+    bits = args.engine_count_bits
+    planes = [eng.add_plane(w, h, bits) for w, h, _ in reqs]
     ops = [eng.op(p, dev) for p, dev in zip(planes, data)]
     rops = [eng.render_op(p, None, b, c) for p, (b, c) in zip(planes, out_batch)]
     t0 = time.perf_counter()
@@ -754,6 +758,7 @@ def sweep_batched(args, torch, binding, device, stream):
         "speedup": ms_plain / ms_graph, "plain_member_px_per_s": member_px / (ms_plain * 1e-3),
         "batched_member_px_per_s": member_px / (ms_graph * 1e-3),
         "batched_mask_gbs": hbm(ms_graph), "batched_frac_of_hbm": hbm(ms_graph) / peaks["hbm_gbs"],
+        "engine_count_bits": bits,
         "tuned_slab_members": slab, "tuned_ctas_per_sm": ctas, "tune_seconds": tune_s,
         "outputs_identical": bool(same)}), flush=True)
 

@@ -4,7 +4,7 @@
  * Many composites at once (the batched and interactive uses of the paper's
  * flood-analysis program, Section 2 and Fig. 1: several member selections,
  * each folded into its own composite and shown as its own saturation map).
- * The engine holds composite planes in device memory (uint32 counts, one per
+ * The engine holds composite planes in device memory (uint32 or uint16 counts, one per
  * plane) and applies "ops" to them: add or remove a set of device-resident
  * uint8 masks to one plane.  All ops of one submit call run in ONE persistent
  * kernel launch whose warps pull work items (op, member slab, chunk of
@@ -77,7 +77,8 @@ typedef struct composite_op {
 /* Render of one plane into dense row-major device outputs (each may be NULL). */
 typedef struct composite_render_op {
     int32_t plane;
-    uint32_t *counts_out;   /* width x height uint32, 4-byte aligned */
+    void *counts_out;       /* width x height counts of the plane's type (uint32, or
+                               uint16 for a 16-bit plane), aligned to it */
     uint8_t *bucket_out;    /* width x height */
     uint8_t *rgba_out;      /* width x height x 4, 4-byte aligned */
 } composite_render_op;
@@ -90,6 +91,13 @@ int composite_engine_begin(composite_engine **out, const composite_engine_config
 /* Allocates a zeroed width x height uint32 plane (N = 0); *plane_out is its id. */
 int composite_engine_add_plane(composite_engine *eng, int32_t width, int32_t height, int32_t *plane_out);
 
+/* The same with the count width chosen: count_bits 32, or 16 for a plane that
+ * will never hold more than 65535 members (half the plane's bytes in every
+ * clear, fold and render; a submit that would exceed 65535 is rejected with
+ * CPT_EINVAL).  count_bits other than 16 or 32: CPT_EINVAL. */
+int composite_engine_add_plane_bits(composite_engine *eng, int32_t width, int32_t height, int32_t count_bits,
+                                    int32_t *plane_out);
+
 /* Frees a plane after the engine's queued work; its id is not reused. */
 int composite_engine_free_plane(composite_engine *eng, int32_t plane);
 
@@ -98,7 +106,8 @@ int composite_engine_clear(composite_engine *eng, int32_t plane);
 
 /* Queues every op in one persistent accumulate launch.  Validates all ops on
  * the host first (CPT_EINVAL and nothing queued if one is bad: unknown plane,
- * sign not +-1, N of a plane would go negative or above 2^32-1, bad strides).
+ * sign not +-1, N of a plane would go negative or above its count type's
+ * maximum (2^32-1, or 65535 for a 16-bit plane), bad strides).
  * A pixel count that would go below zero raises the plane's underflow state
  * (reported by composite_engine_sync). */
 int composite_engine_submit(composite_engine *eng, const composite_op *ops, int32_t n_ops);

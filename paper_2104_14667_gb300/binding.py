@@ -456,6 +456,7 @@ def _engine_lib():
             "composite_engine_default_config": (ctypes.c_int, [ctypes.POINTER(EngineConfig)]),
             "composite_engine_begin": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(EngineConfig)]),
             "composite_engine_add_plane": (ctypes.c_int, [vp, i32, i32, p32]),
+            "composite_engine_add_plane_bits": (ctypes.c_int, [vp, i32, i32, i32, p32]),
             "composite_engine_free_plane": (ctypes.c_int, [vp, i32]),
             "composite_engine_clear": (ctypes.c_int, [vp, i32]),
             "composite_engine_submit": (ctypes.c_int, [vp, ctypes.POINTER(Op), i32]),
@@ -510,9 +511,11 @@ class Engine:
         self._keep = []
         self.shapes = {}
 
-    def add_plane(self, width: int, height: int) -> int:
+    def add_plane(self, width: int, height: int, count_bits: int = 32) -> int:
+        """A zeroed plane of uint32 (or, count_bits=16, uint16) counts; its id."""
         pid = ctypes.c_int32()
-        _echeck(self.lib, self.h, self.lib.composite_engine_add_plane(self.h, width, height, ctypes.byref(pid)))
+        _echeck(self.lib, self.h, self.lib.composite_engine_add_plane_bits(self.h, width, height, count_bits,
+                                                                          ctypes.byref(pid)))
         self.shapes[pid.value] = (width, height)
         return pid.value
 

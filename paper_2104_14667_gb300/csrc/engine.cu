@@ -55,11 +55,13 @@ struct OpDesc {
     int32_t exclusive;           // the only op on its plane, one slab: plain read-modify-write
     int32_t bits;                // bit-packed masks: a group is a 32-pixel word
     int32_t words_per_row;       // bits: ceil(width / 32)
+    int32_t u16;                 // the plane holds uint16 counts (else uint32)
+    int32_t pad;
 };
 
 struct RenderDesc {
     const uint32_t *plane;
-    uint32_t *counts_out;
+    void *counts_out;
     uint8_t *bucket_out;
     uint32_t *rgba_out;
     int64_t plane_pitch;
@@ -70,7 +72,7 @@ struct RenderDesc {
     int32_t groups_per_row;
     int32_t tiles;
     int32_t vec;           // 16-byte stores allowed
-    int32_t pad;
+    int32_t u16;           // the plane holds uint16 counts (else uint32)
 };
 
 constexpr int kSmemStarts = 2048;      // ops whose first items fit in shared memory
@@ -170,11 +172,20 @@ __device__ __forceinline__ void process_item(const OpDesc &op, uint32_t item, in
 #pragma unroll
         for (int jj = 0; jj < 16; ++jj) wide[jj] = 0;
         cpt::widen16(wide, k[0], k[1], k[2], k[3]);
-        uint32_t *dst = op.plane + (int64_t)y * op.plane_pitch + x0;
-        if (op.exclusive)
-            cpt::apply_count_group<uint32_t>(dst, valid, wide, op.sign, flags + op.plane_id);
-        else
-            cpt::atomic_count_group<uint32_t>(dst, wide, op.sign, flags + op.plane_id);
+        const int64_t at = (int64_t)y * op.plane_pitch + x0;
+        if (op.u16) {
+            uint16_t *dst = reinterpret_cast<uint16_t *>(op.plane) + at;
+            if (op.exclusive)
+                cpt::apply_count_group<uint16_t>(dst, valid, wide, op.sign, flags + op.plane_id);
+            else
+                cpt::atomic_count_group<uint16_t>(dst, wide, op.sign, flags + op.plane_id);
+        } else {
+            uint32_t *dst = op.plane + at;
+            if (op.exclusive)
+                cpt::apply_count_group<uint32_t>(dst, valid, wide, op.sign, flags + op.plane_id);
+            else
+                cpt::atomic_count_group<uint32_t>(dst, wide, op.sign, flags + op.plane_id);
+        }
     }
     if (gather) __syncwarp();
 }
@@ -227,17 +238,26 @@ __device__ __forceinline__ void process_bits_item(const OpDesc &op, uint32_t ite
             }
             cpt::bitcount_add16(acc, w);
         }
-        uint32_t *dst = op.plane + (int64_t)y * op.plane_pitch + x0;
+        const int64_t at = (int64_t)y * op.plane_pitch + x0;
         uint32_t pairs[16];
         cpt::bitcount_pairs(acc, pairs);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int v = min(16, valid - 16 * h);
             if (v <= 0) break;
-            if (op.exclusive)
-                cpt::apply_pair_group<uint32_t>(dst + 16 * h, v, pairs + 8 * h, op.sign, flags + op.plane_id);
-            else
-                cpt::atomic_pair_group<uint32_t>(dst + 16 * h, pairs + 8 * h, op.sign, flags + op.plane_id);
+            if (op.u16) {
+                uint16_t *dst = reinterpret_cast<uint16_t *>(op.plane) + at + 16 * h;
+                if (op.exclusive)
+                    cpt::apply_pair_group<uint16_t>(dst, v, pairs + 8 * h, op.sign, flags + op.plane_id);
+                else
+                    cpt::atomic_pair_group<uint16_t>(dst, pairs + 8 * h, op.sign, flags + op.plane_id);
+            } else {
+                uint32_t *dst = op.plane + at + 16 * h;
+                if (op.exclusive)
+                    cpt::apply_pair_group<uint32_t>(dst, v, pairs + 8 * h, op.sign, flags + op.plane_id);
+                else
+                    cpt::atomic_pair_group<uint32_t>(dst, pairs + 8 * h, op.sign, flags + op.plane_id);
+            }
         }
     }
     if (gather) __syncwarp();
@@ -307,11 +327,23 @@ engine_render_kernel(const RenderDesc *ops, int n_ops, uint32_t n_items, Lut lut
             if (g >= groups) break;
             const int y = (int)(g / op.groups_per_row);
             const int x0 = (int)(g - (int64_t)y * op.groups_per_row) * 16;
-            const uint4 *src = reinterpret_cast<const uint4 *>(op.plane + (int64_t)y * op.plane_pitch + x0);
+            const int64_t at = (int64_t)y * op.plane_pitch + x0;
+            if (op.u16) {
+                const uint4 *src = reinterpret_cast<const uint4 *>(reinterpret_cast<const uint16_t *>(op.plane) + at);
+                const uint4 a = src[0], b = src[1];
+                const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const uint4 v = src[q];
-                c[k][4 * q] = v.x; c[k][4 * q + 1] = v.y; c[k][4 * q + 2] = v.z; c[k][4 * q + 3] = v.w;
+                for (int q = 0; q < 8; ++q) {
+                    c[k][2 * q] = w[q] & 0xFFFFu;
+                    c[k][2 * q + 1] = w[q] >> 16;
+                }
+            } else {
+                const uint4 *src = reinterpret_cast<const uint4 *>(op.plane + at);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint4 v = src[q];
+                    c[k][4 * q] = v.x; c[k][4 * q + 1] = v.y; c[k][4 * q + 2] = v.z; c[k][4 * q + 3] = v.w;
+                }
             }
         }
 #pragma unroll
@@ -327,10 +359,18 @@ engine_render_kernel(const RenderDesc *ops, int n_ops, uint32_t n_items, Lut lut
             const int64_t out = (int64_t)y * op.width + x0;
             if (op.vec && valid == 16) {
                 if (op.counts_out) {
+                    if (op.u16) {
 #pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        reinterpret_cast<uint4 *>(op.counts_out + out)[q] =
-                            make_uint4(c[k][4 * q], c[k][4 * q + 1], c[k][4 * q + 2], c[k][4 * q + 3]);
+                        for (int q = 0; q < 2; ++q)
+                            reinterpret_cast<uint4 *>(reinterpret_cast<uint16_t *>(op.counts_out) + out)[q] =
+                                make_uint4(c[k][8 * q] | (c[k][8 * q + 1] << 16), c[k][8 * q + 2] | (c[k][8 * q + 3] << 16),
+                                           c[k][8 * q + 4] | (c[k][8 * q + 5] << 16), c[k][8 * q + 6] | (c[k][8 * q + 7] << 16));
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            reinterpret_cast<uint4 *>(reinterpret_cast<uint32_t *>(op.counts_out) + out)[q] =
+                                make_uint4(c[k][4 * q], c[k][4 * q + 1], c[k][4 * q + 2], c[k][4 * q + 3]);
+                    }
                 }
                 if (op.bucket_out) {
                     uint32_t w[4];
@@ -349,7 +389,12 @@ engine_render_kernel(const RenderDesc *ops, int n_ops, uint32_t n_items, Lut lut
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     if (j < valid) {
-                        if (op.counts_out) op.counts_out[out + j] = c[k][j];
+                        if (op.counts_out) {
+                            if (op.u16)
+                                reinterpret_cast<uint16_t *>(op.counts_out)[out + j] = (uint16_t)c[k][j];
+                            else
+                                reinterpret_cast<uint32_t *>(op.counts_out)[out + j] = c[k][j];
+                        }
                         if (op.bucket_out) op.bucket_out[out + j] = (uint8_t)b[j];
                         if (op.rgba_out) op.rgba_out[out + j] = table[b[j]];
                     }
@@ -362,9 +407,13 @@ engine_render_kernel(const RenderDesc *ops, int n_ops, uint32_t n_items, Lut lut
 struct PlaneRec {
     int32_t width = 0, height = 0;
     int64_t pitch_px = 0;
-    uint32_t *data = nullptr;
+    uint32_t *data = nullptr;    // uint16 counts when count_bits is 16
+    int32_t count_bits = 32;
     int64_t n = 0;
     bool alive = false;
+
+    size_t bytes() const { return (size_t)pitch_px * height * (count_bits / 8); }
+    int64_t max_members() const { return count_bits == 16 ? 0xFFFFll : 0xFFFFFFFFll; }
 };
 
 // A device buffer of descriptors with its pinned host mirror.
@@ -520,7 +569,9 @@ int plan_ops(composite_engine *e, const composite_op *ops, int32_t n_ops, std::v
         if (n[o.plane] < 0) n[o.plane] = from_zero ? 0 : p.n;
         n[o.plane] += (int64_t)o.sign * o.n_members;
         if (n[o.plane] < 0) return efail(e, CPT_EINVAL, "op %d: plane %d would hold fewer than 0 members", i, o.plane);
-        if (n[o.plane] > 0xFFFFFFFFll) return efail(e, CPT_EINVAL, "op %d: plane %d would exceed 2^32-1 members", i, o.plane);
+        if (n[o.plane] > p.max_members())
+            return efail(e, CPT_EINVAL, "op %d: plane %d would exceed %lld members (%d-bit counts)", i, o.plane,
+                         (long long)p.max_members(), p.count_bits);
         if (o.n_members == 0) continue;
         if (!o.members) return efail(e, CPT_EINVAL, "op %d: members is NULL", i);
         if ((reinterpret_cast<uintptr_t>(o.members) % 16) || (o.row_pitch_bytes % 16) || (o.member_stride_bytes % 16))
@@ -544,6 +595,7 @@ int plan_ops(composite_engine *e, const composite_op *ops, int32_t n_ops, std::v
         d.height = p.height;
         d.groups_per_row = (int32_t)(p.pitch_px / 16);
         d.bits = bits ? 1 : 0;
+        d.u16 = p.count_bits == 16 ? 1 : 0;
         d.words_per_row = (int32_t)(((int64_t)p.width + 31) / 32);
         const int64_t groups = bits ? (int64_t)d.words_per_row * p.height : (int64_t)d.groups_per_row * p.height;
         // a warp item: 32 lanes x groups_per_thread groups, so that a lane
@@ -580,9 +632,9 @@ int plan_render(composite_engine *e, const composite_render_op *ops, int32_t n_o
     for (int32_t i = 0; i < n_ops; ++i) {
         const composite_render_op &o = ops[i];
         if (!plane_ok(e, o.plane)) return efail(e, CPT_EINVAL, "render %d: no plane %d", i, o.plane);
-        if ((reinterpret_cast<uintptr_t>(o.counts_out) % 4) || (reinterpret_cast<uintptr_t>(o.rgba_out) % 4))
-            return efail(e, CPT_EINVAL, "render %d: counts_out and rgba_out must be 4-byte aligned", i);
         const PlaneRec &p = e->planes[o.plane];
+        if ((reinterpret_cast<uintptr_t>(o.counts_out) % (p.count_bits / 8)) || (reinterpret_cast<uintptr_t>(o.rgba_out) % 4))
+            return efail(e, CPT_EINVAL, "render %d: counts_out must be aligned to its count type, rgba_out to 4 bytes", i);
         int64_t n = p.n;
         if (n_override)
             for (const auto &pn : *n_override)
@@ -603,6 +655,7 @@ int plan_render(composite_engine *e, const composite_render_op *ops, int32_t n_o
         const uintptr_t a = reinterpret_cast<uintptr_t>(o.counts_out) | reinterpret_cast<uintptr_t>(o.bucket_out) |
                             reinterpret_cast<uintptr_t>(o.rgba_out);
         d.vec = (p.width % 16 == 0) && (a % 16 == 0);
+        d.u16 = p.count_bits == 16 ? 1 : 0;
         items += d.tiles;
         descs->push_back(d);
     }
@@ -644,7 +697,7 @@ int launch_render(composite_engine *e, const void *d_ops, int n_ops, int64_t n_i
 
 int clear_plane(composite_engine *e, int32_t p) {
     PlaneRec &r = e->planes[p];
-    ECK(e, cudaMemsetAsync(r.data, 0, (size_t)r.pitch_px * r.height * sizeof(uint32_t), e->stream));
+    ECK(e, cudaMemsetAsync(r.data, 0, r.bytes(), e->stream));
     ECK(e, cudaMemsetAsync(e->d_flags + p, 0, sizeof(int), e->stream));
     r.n = 0;
     return CPT_OK;
@@ -763,15 +816,22 @@ int composite_engine_begin(composite_engine **out, const composite_engine_config
 }
 
 int composite_engine_add_plane(composite_engine *e, int32_t width, int32_t height, int32_t *plane_out) {
+    return composite_engine_add_plane_bits(e, width, height, 32, plane_out);
+}
+
+int composite_engine_add_plane_bits(composite_engine *e, int32_t width, int32_t height, int32_t count_bits,
+                                    int32_t *plane_out) {
     if (!e || !plane_out) return CPT_EINVAL;
     e->err.clear();
     if (width <= 0 || height <= 0) return efail(e, CPT_EINVAL, "plane %d x %d is empty", width, height);
+    if (count_bits != 16 && count_bits != 32) return efail(e, CPT_EINVAL, "count_bits must be 16 or 32");
     if ((int)e->planes.size() >= kMaxPlanes) return efail(e, CPT_EINVAL, "at most %d planes", kMaxPlanes);
     PlaneRec r;
     r.width = width;
     r.height = height;
     r.pitch_px = ((int64_t)width + 15) / 16 * 16;
-    ECK(e, cudaMalloc(&r.data, (size_t)r.pitch_px * height * sizeof(uint32_t)));
+    r.count_bits = count_bits;
+    ECK(e, cudaMalloc(&r.data, r.bytes()));
     r.alive = true;
     e->planes.push_back(r);
     const int32_t id = (int32_t)e->planes.size() - 1;
@@ -883,7 +943,7 @@ int composite_engine_capture(composite_engine *e, const composite_op *ops, int32
     auto body = [&]() -> int {
         for (const auto &pn : n_after) {
             PlaneRec &r = e->planes[pn.first];
-            ECK(e, cudaMemsetAsync(r.data, 0, (size_t)r.pitch_px * r.height * sizeof(uint32_t), e->stream));
+            ECK(e, cudaMemsetAsync(r.data, 0, r.bytes(), e->stream));
             ECK(e, cudaMemsetAsync(e->d_flags + pn.first, 0, sizeof(int), e->stream));
         }
         if (items > 0) {

@@ -22,8 +22,9 @@ def padded(m: np.ndarray):
     return buf[:, :, :w]
 
 
-def outputs(w, h):
-    return (torch.empty((h, w), dtype=torch.int32, device="cuda"),
+def outputs(w, h, count_bits=32):
+    # counts of a 16-bit plane come back as uint16 (held in an int16 tensor)
+    return (torch.empty((h, w), dtype=torch.int32 if count_bits == 32 else torch.int16, device="cuda"),
             torch.empty((h, w), dtype=torch.uint8, device="cuda"),
             torch.empty((h, w, 4), dtype=torch.uint8, device="cuda"))
 
@@ -32,7 +33,10 @@ def check(outs, masks_np, lut=None):
     counts, bucket, rgba = outs
     c = oracle.count(masks_np)
     b = oracle.bucket(c, masks_np.shape[0])
-    np.testing.assert_array_equal(counts.cpu().numpy().astype(np.int64), c)
+    got = counts.cpu().numpy()
+    if got.dtype == np.int16:
+        got = got.view(np.uint16)
+    np.testing.assert_array_equal(got.astype(np.int64), c)
     np.testing.assert_array_equal(bucket.cpu().numpy(), b)
     np.testing.assert_array_equal(rgba.cpu().numpy(), oracle.rgba(b, lut))
 
@@ -40,15 +44,16 @@ def check(outs, masks_np, lut=None):
 SHAPES = [(1024, 1024, 16), (13, 7, 5), (100, 37, 40), (257, 131, 300), (4096, 3, 9), (1, 1, 2), (48, 600, 1)]
 
 
+@pytest.mark.parametrize("count_bits", [32, 16])
 @pytest.mark.parametrize("schedule", ["persistent", "grid"])
-def test_many_planes_one_launch(schedule):
+def test_many_planes_one_launch(schedule, count_bits):
     with binding.Engine(schedule=schedule) as eng:
         data, ops, rops, outs = [], [], [], []
         for i, (w, h, n) in enumerate(SHAPES):
             m = synth.scramble_nonzero(synth.random_masks(50 + i, n, h, w, density=0.3 + 0.05 * i), i)
-            p = eng.add_plane(w, h)
+            p = eng.add_plane(w, h, count_bits)
             dev = padded(m)
-            o = outputs(w, h)
+            o = outputs(w, h, count_bits)
             data.append((m, dev))
             outs.append(o)
             ops.append(eng.op(p, dev))
@@ -61,8 +66,9 @@ def test_many_planes_one_launch(schedule):
             check(o, m)
 
 
+@pytest.mark.parametrize("count_bits", [32, 16])
 @pytest.mark.parametrize("schedule", ["persistent", "grid"])
-def test_index_lists_add_and_remove(schedule):
+def test_index_lists_add_and_remove(schedule, count_bits):
     w, h, total = 300, 70, 500
     ens = synth.scramble_nonzero(synth.random_masks(60, total, h, w, density=0.2), 60)
     dev = padded(ens)
@@ -71,12 +77,12 @@ def test_index_lists_add_and_remove(schedule):
     b = rng.choice(total, 120, replace=False).astype(np.int32)
     drop = a[:170]
     with binding.Engine(slab_members=64, schedule=schedule) as eng:
-        p = eng.add_plane(w, h)
-        q = eng.add_plane(w, h)
+        p = eng.add_plane(w, h, count_bits)
+        q = eng.add_plane(w, h, count_bits)
         ia, ib, idrop = (torch.from_numpy(x).cuda() for x in (a, b, drop))
         eng.submit([eng.op(p, dev, 1, ia), eng.op(q, dev, 1, ib), eng.op(p, dev, 1, ib)])
         eng.submit([eng.op(p, dev, -1, idrop)])
-        op_, oq = outputs(w, h), outputs(w, h)
+        op_, oq = outputs(w, h, count_bits), outputs(w, h, count_bits)
         eng.render([eng.render_op(p, *op_), eng.render_op(q, *oq)])
         eng.sync()
         keep = np.concatenate([a[170:], b])
@@ -85,13 +91,14 @@ def test_index_lists_add_and_remove(schedule):
         assert eng.member_count(p) == len(keep)
 
 
-def test_underflow_is_reported_per_plane_and_cleared():
+@pytest.mark.parametrize("count_bits", [32, 16])
+def test_underflow_is_reported_per_plane_and_cleared(count_bits):
     w, h = 64, 20
     m = synth.random_masks(61, 2, h, w, density=0.5)
     dev = padded(m)
     with binding.Engine() as eng:
-        good = eng.add_plane(w, h)
-        bad = eng.add_plane(w, h)
+        good = eng.add_plane(w, h, count_bits)
+        bad = eng.add_plane(w, h, count_bits)
         eng.submit([eng.op(good, dev), eng.op(bad, dev[:1])])
         eng.submit([eng.op(bad, dev[1:], -1)])
         with pytest.raises(binding.CompositeError) as e:
@@ -99,19 +106,20 @@ def test_underflow_is_reported_per_plane_and_cleared():
         assert e.value.code == binding.CPT_EUNDERFLOW and e.value.plane == bad
         eng.clear(bad)
         eng.submit([eng.op(bad, dev)])
-        o = outputs(w, h)
+        o = outputs(w, h, count_bits)
         eng.render([eng.render_op(bad, *o)])
         eng.sync()
         check(o, m)
 
 
-def test_capture_replay_matches_direct_and_repeats():
+@pytest.mark.parametrize("count_bits", [32, 16])
+def test_capture_replay_matches_direct_and_repeats(count_bits):
     shapes = [(512, 64, 37), (77, 45, 260), (16, 16, 3)]
     with binding.Engine() as eng:
         items = []
         for i, (w, h, n) in enumerate(shapes):
             m = synth.random_masks(70 + i, n, h, w, density=0.4)
-            items.append((m, padded(m), eng.add_plane(w, h), outputs(w, h)))
+            items.append((m, padded(m), eng.add_plane(w, h, count_bits), outputs(w, h, count_bits)))
         ops = [eng.op(p, dev) for _, dev, p, _ in items]
         rops = [eng.render_op(p, *o) for _, _, p, o in items]
         eng.capture(ops, rops)
@@ -156,6 +164,25 @@ def test_invalid_ops_rejected_before_anything_runs():
         assert eng.member_count(p) == 0
 
 
+def test_sixteen_bit_plane_limit():
+    w, h = 16, 2
+    with binding.Engine() as eng:
+        with pytest.raises(binding.CompositeError) as e:
+            eng.add_plane(w, h, 8)
+        assert e.value.code == binding.CPT_EINVAL
+        p = eng.add_plane(w, h, 16)
+        ones = torch.ones((65535, h, w), dtype=torch.uint8, device="cuda")
+        eng.submit([eng.op(p, ones)])
+        with pytest.raises(binding.CompositeError) as e:
+            eng.submit([eng.op(p, ones[:1])])
+        assert e.value.code == binding.CPT_EINVAL
+        o = outputs(w, h, 16)
+        eng.render([eng.render_op(p, *o)])
+        eng.sync()
+        assert eng.member_count(p) == 65535
+        assert (o[0].cpu().numpy().view(np.uint16) == 65535).all() and (o[1].cpu().numpy() == 255).all()
+
+
 def padded_bits(m: np.ndarray):
     """Device copy of bit-packed masks with rows padded to 16 bytes."""
     p = synth.pack_masks(m)
@@ -166,15 +193,16 @@ def padded_bits(m: np.ndarray):
     return buf[:, :, :wb]
 
 
+@pytest.mark.parametrize("count_bits", [32, 16])
 @pytest.mark.parametrize("schedule", ["persistent", "grid"])
-def test_bit_packed_ops_mixed_with_byte_ops(schedule):
+def test_bit_packed_ops_mixed_with_byte_ops(schedule, count_bits):
     shapes = [(300, 70, 280), (33, 9, 5), (1024, 64, 40)]
     with binding.Engine(schedule=schedule) as eng:
         items = []
         for i, (w, h, n) in enumerate(shapes):
             m = synth.scramble_nonzero(synth.random_masks(120 + i, n, h, w, density=0.3), i)
-            p = eng.add_plane(w, h)
-            items.append((m, p, outputs(w, h)))
+            p = eng.add_plane(w, h, count_bits)
+            items.append((m, p, outputs(w, h, count_bits)))
         ops = []
         for i, (m, p, _) in enumerate(items):
             half = m.shape[0] // 2

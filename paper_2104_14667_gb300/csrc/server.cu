@@ -507,6 +507,11 @@ int composite_server_begin(composite_server **out, const composite_server_config
         ec.cuda_stream = s->compute;
         ec.wait_timeout_ms = c.wait_timeout_ms;
         ec.slab_members = 255;
+        // four persistent CTAs per SM, not five: the overflow gather kernel on
+        // the copy stream then fits beside the engine's launch (registers) and
+        // the uploads overlap the folds instead of taking turns with them
+        // (byte masks at 500 req/s: 52.8 against 50.7 composites/s)
+        ec.ctas_per_sm = 4;
         ec.upload_stream = s->copy;
         int rc = composite_engine_begin(&s->eng, &ec);
         if (rc) return sfail(s, rc, "engine: %s", composite_engine_last_error(nullptr));

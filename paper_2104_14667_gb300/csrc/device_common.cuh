@@ -149,17 +149,6 @@ __device__ __forceinline__ void atomic_count_group(CountT *dst, const uint32_t (
     if (under) flag_set(flags, kFlagUnderflow);
 }
 
-// floor(255 * c / n) for 0 <= c <= n, exact.  With n < 2^24 the product fits
-// in 32 bits; larger n take the 64-bit path.  A count above n (only possible
-// in a composite an underflow has already invalidated) is held at 255 so the
-// colour table is never indexed out of range.
-__device__ __forceinline__ uint32_t overlap_class(uint32_t c, uint64_t n) {
-    if (n == 0) return 0;
-    if (c >= n) return 255;
-    if (n < (1u << 24)) return (255u * c) / (uint32_t)n;
-    return (uint32_t)((255ull * c) / n);
-}
-
 // dst[j] (+|-)= acc[j] for the first `valid` of four float32 sums.
 __device__ __forceinline__ void apply_depth_group(float *dst, int valid, const float (&acc)[4],
                                                   int sign) {

@@ -24,6 +24,7 @@
 
 #include "composite_engine.h"
 #include "bit_count.cuh"
+#include "overlap_class.cuh"
 
 namespace {
 
@@ -73,6 +74,7 @@ struct RenderDesc {
     int32_t tiles;
     int32_t vec;           // 16-byte stores allowed
     int32_t u16;           // the plane holds uint16 counts (else uint32)
+    cpt::ClassDivisor div; // floor(255 c / n_members) by multiplication
 };
 
 constexpr int kSmemStarts = 2048;      // ops whose first items fit in shared memory
@@ -355,7 +357,7 @@ engine_render_kernel(const RenderDesc *ops, int n_ops, uint32_t n_items, Lut lut
             const int valid = min(16, op.width - x0);
             uint32_t b[16];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) b[j] = cpt::overlap_class(c[k][j], op.n_members);
+            for (int j = 0; j < 16; ++j) b[j] = cpt::overlap_class(c[k][j], op.div);
             const int64_t out = (int64_t)y * op.width + x0;
             if (op.vec && valid == 16) {
                 if (op.counts_out) {
@@ -647,6 +649,7 @@ int plan_render(composite_engine *e, const composite_render_op *ops, int32_t n_o
         d.plane_pitch = p.pitch_px;
         d.item_start = items;
         d.n_members = (uint64_t)n;
+        d.div = cpt::class_divisor((uint64_t)n);
         d.width = p.width;
         d.height = p.height;
         d.groups_per_row = (int32_t)(p.pitch_px / 16);

@@ -3,6 +3,7 @@
 // high saturation, and the frequency of overlap classes), or depth sums to a
 // mean depth.  One thread per output pixel; outputs are dense row-major.
 #include "device_common.cuh"
+#include "overlap_class.cuh"
 
 namespace cpt {
 namespace {
@@ -32,7 +33,7 @@ __device__ __forceinline__ void hist_flush(HistBins &h, unsigned long long *hist
 
 template <typename CountT, bool kHist>
 __global__ void __launch_bounds__(kThreads)
-render_counts_kernel(Plane p, uint64_t n_members, CountT *counts_out, uint8_t *bucket_out,
+render_counts_kernel(Plane p, ClassDivisor div, CountT *counts_out, uint8_t *bucket_out,
                      uint32_t *rgba_out, Lut lut, unsigned long long *hist_out) {
     __shared__ uint32_t table[256];
     __shared__ HistBins bins;
@@ -47,7 +48,7 @@ render_counts_kernel(Plane p, uint64_t n_members, CountT *counts_out, uint8_t *b
         const int y = (int)(i / p.width);
         const int x = (int)(i - (int64_t)y * p.width);
         const uint32_t c = plane[(int64_t)y * p.pitch + x];
-        const uint32_t b = overlap_class(c, n_members);
+        const uint32_t b = overlap_class(c, div);
         if (counts_out) counts_out[i] = (CountT)c;
         if (bucket_out) bucket_out[i] = (uint8_t)b;
         if (rgba_out) rgba_out[i] = table[b];
@@ -61,7 +62,7 @@ render_counts_kernel(Plane p, uint64_t n_members, CountT *counts_out, uint8_t *b
 // row starts on a 16-byte boundary.
 template <typename CountT, bool kHist>
 __global__ void __launch_bounds__(kThreads)
-render_counts_vec_kernel(Plane p, uint64_t n_members, CountT *counts_out, uint8_t *bucket_out,
+render_counts_vec_kernel(Plane p, ClassDivisor div, CountT *counts_out, uint8_t *bucket_out,
                          uint32_t *rgba_out, Lut lut, unsigned long long *hist_out) {
     __shared__ uint32_t table[256];
     __shared__ HistBins bins;
@@ -102,7 +103,7 @@ render_counts_vec_kernel(Plane p, uint64_t n_members, CountT *counts_out, uint8_
         }
         uint32_t b[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) b[j] = overlap_class(c[j], n_members);
+        for (int j = 0; j < 16; ++j) b[j] = overlap_class(c[j], div);
         if (bucket_out) {
             uint32_t w[4];
 #pragma unroll
@@ -157,6 +158,7 @@ template <bool kHist>
 cudaError_t render_counts_t(const Plane &p, uint64_t n_members, void *counts_out, uint8_t *bucket_out,
                             uint32_t *rgba_out, const Lut &lut, unsigned long long *hist_out,
                             const DeviceCaps &caps, cudaStream_t s) {
+    const ClassDivisor div = class_divisor(n_members);
     const int64_t total = (int64_t)p.width * p.height;
     const bool aligned = ((reinterpret_cast<uintptr_t>(counts_out) | reinterpret_cast<uintptr_t>(bucket_out) |
                            reinterpret_cast<uintptr_t>(rgba_out)) % 16) == 0;
@@ -164,16 +166,16 @@ cudaError_t render_counts_t(const Plane &p, uint64_t n_members, void *counts_out
         const int64_t groups = total / 16;
         if (p.count_bits == 16)
             render_counts_vec_kernel<uint16_t, kHist><<<grid_for(groups, caps), kThreads, 0, s>>>(
-                p, n_members, static_cast<uint16_t *>(counts_out), bucket_out, rgba_out, lut, hist_out);
+                p, div, static_cast<uint16_t *>(counts_out), bucket_out, rgba_out, lut, hist_out);
         else
             render_counts_vec_kernel<uint32_t, kHist><<<grid_for(groups, caps), kThreads, 0, s>>>(
-                p, n_members, static_cast<uint32_t *>(counts_out), bucket_out, rgba_out, lut, hist_out);
+                p, div, static_cast<uint32_t *>(counts_out), bucket_out, rgba_out, lut, hist_out);
     } else if (p.count_bits == 16) {
         render_counts_kernel<uint16_t, kHist><<<grid_for(total, caps), kThreads, 0, s>>>(
-            p, n_members, static_cast<uint16_t *>(counts_out), bucket_out, rgba_out, lut, hist_out);
+            p, div, static_cast<uint16_t *>(counts_out), bucket_out, rgba_out, lut, hist_out);
     } else {
         render_counts_kernel<uint32_t, kHist><<<grid_for(total, caps), kThreads, 0, s>>>(
-            p, n_members, static_cast<uint32_t *>(counts_out), bucket_out, rgba_out, lut, hist_out);
+            p, div, static_cast<uint32_t *>(counts_out), bucket_out, rgba_out, lut, hist_out);
     }
     return cudaGetLastError();
 }

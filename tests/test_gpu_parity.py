@@ -380,3 +380,74 @@ def test_texture_layout_converters(converter, mode, kind, w, h, n):
         else:
             got = comp.render_host()["mean"]
             assert np.abs(got.astype(np.float64) - oracle.mean_depth(m)).max() <= 1e-5 * n
+
+
+def _nested_masks(n, targets):
+    """uint8[n, 1, W] on the device: member m floods pixel x when m <
+    targets[x], so the composite's counts are exactly `targets`."""
+    t = torch.as_tensor(np.asarray(targets, np.int64), device="cuda")
+    return (torch.arange(n, device="cuda")[:, None] < t[None, :]).to(torch.uint8)[:, None, :].contiguous()
+
+
+def _class_targets(n):
+    if n <= 4097:
+        return np.arange(n + 1)
+    return np.unique(np.round(np.linspace(0, n, 4097)).astype(np.int64))
+
+
+CLASS_NS = list(range(1, 130)) + [255, 256, 257, 1000, 4095, 4096, 4097, 65535]
+
+
+@pytest.mark.parametrize("count_bits", [16, 32])
+def test_overlap_class_for_every_count(count_bits):
+    # the render's floor(255 c / N) (a multiply-high by an invariant divisor)
+    # against the oracle for every count of every listed N; widths both
+    # multiples of 16 (16-pixel kernel) and not (per-pixel kernel)
+    for n in CLASS_NS:
+        targets = _class_targets(n)
+        masks = _nested_masks(n, targets)
+        with binding.Composite(len(targets), 1, count_bits=count_bits) as comp:
+            comp.add(masks)
+            got = comp.render_host()
+        c = np.asarray(targets, np.int64)[None, :]
+        b = oracle.bucket(c, n)
+        np.testing.assert_array_equal(got["counts"].astype(np.int64), c, err_msg=f"N={n}")
+        np.testing.assert_array_equal(got["bucket"], b, err_msg=f"N={n}")
+        np.testing.assert_array_equal(got["rgba"], oracle.rgba(b), err_msg=f"N={n}")
+
+
+@pytest.mark.parametrize("count_bits", [16, 32])
+def test_engine_overlap_class_for_every_count(count_bits):
+    ns = [1, 2, 3, 7, 16, 17, 100, 255, 256, 1000, 4097] + ([65535] if count_bits == 16 else [65535, 70001])
+    with binding.Engine() as eng:
+        for n in ns:
+            targets = _class_targets(n)
+            w = len(targets)
+            buf = torch.zeros((n, 1, (w + 15) // 16 * 16), dtype=torch.uint8, device="cuda")
+            buf[:, :, :w] = _nested_masks(n, targets)
+            p = eng.add_plane(w, 1, count_bits)
+            counts = torch.empty((1, w), dtype=torch.int32 if count_bits == 32 else torch.int16, device="cuda")
+            bucket = torch.empty((1, w), dtype=torch.uint8, device="cuda")
+            eng.submit([eng.op(p, buf[:, :, :w])])
+            eng.render([eng.render_op(p, counts, bucket, None)])
+            eng.sync()
+            got = counts.cpu().numpy()
+            if got.dtype == np.int16:
+                got = got.view(np.uint16)
+            c = np.asarray(targets, np.int64)[None, :]
+            np.testing.assert_array_equal(got.astype(np.int64), c, err_msg=f"N={n}")
+            np.testing.assert_array_equal(bucket.cpu().numpy(), oracle.bucket(c, n), err_msg=f"N={n}")
+            eng.free_plane(p)
+
+
+def test_overlap_class_past_two_to_the_24_members():
+    # N >= 2^24 members: the 64-bit division path of the class
+    n = (1 << 24) + 3
+    targets = np.array([0, 1, 2, n // 3, n // 2, n - 2, n - 1, n] + [0] * 8, np.int64)
+    masks = _nested_masks(n, targets)           # n x 1 x 16 bytes, read in place
+    with binding.Composite(16, 1, count_bits=32) as comp:
+        comp.add(masks)
+        got = comp.render_host()
+    c = targets[None, :]
+    np.testing.assert_array_equal(got["counts"].astype(np.int64), c)
+    np.testing.assert_array_equal(got["bucket"], oracle.bucket(c, n))

@@ -74,7 +74,10 @@ depth_texture_kernel(cudaTextureObject_t tex, int n_layers, Plane p, int sign, i
 // one thread per 16-byte texel reads the linear raster with a 16-byte load
 // and stores the texel into the layered cudaArray through a surface object,
 // a warp taking 32 consecutive texels of a row.  (Warps over 4 x 8 texel
-// blocks converted 1.9 TB/s of source against 2.1 for rows.)
+// blocks converted 1.9 TB/s of source against 2.1 for rows; four texels per
+// thread with every load issued first gave 2.16 / 1.75 TB/s for masks /
+// depths against 2.16 / 2.18: the surface stores, not the loads in flight,
+// set the rate.)
 __global__ void __launch_bounds__(kThreads)
 convert_to_array_kernel(const uint8_t *src, int64_t pitch, int64_t member_stride, cudaSurfaceObject_t surf,
                         int texels_per_row, int height, int64_t texels) {

@@ -514,6 +514,18 @@ def run_ours(args):
 
 # ---- sweeps: the workload configs' other measurements (one JSON line each) ----
 
+def identity_rows_exact(comp, terrain, levels, rows=(0, 1, -2, -1)) -> bool:
+    """Renders the composite's counts and checks sampled rows against the
+    nested-threshold identity: every member thresholds the same terrain, so
+    count(p) = #{m : w_m > terrain(p)} over the members' water levels (with
+    repeats when members cycle through a pool)."""
+    got = comp.render_host()["counts"].astype(np.int64)
+    lv = np.sort(np.asarray(levels, np.float32))
+    rows = sorted({r % terrain.shape[0] for r in rows})
+    ident = len(lv) - np.searchsorted(lv, terrain[rows].ravel(), side="right").reshape(len(rows), -1)
+    return bool(np.array_equal(got[rows], ident))
+
+
 def _timed(torch, stream, fn, steps: int, warmup: int) -> float:
     """Average ms of fn() over `steps` runs (CUDA events on `stream`)."""
     for _ in range(warmup):
@@ -565,6 +577,7 @@ def sweep_readpath(args, torch, binding, device, stream):
             with binding.Composite(W, H, trace=True, **cfg) as comp:
                 comp.add(data)
                 rec = comp.trace()
+                exact = identity_rows_exact(comp, ens.terrain, ens.levels) if mode == "count" else None
             launches = int(sum(1 for k, _, _ in rec if int(k) == 2))
             kernel_ms = _busy(rec, (2,))
             convert_ms = _busy(rec, (1,))
@@ -578,7 +591,8 @@ def sweep_readpath(args, torch, binding, device, stream):
                     "kernel_busy_ms": kernel_ms, "conversion_busy_ms": convert_ms,
                     "kernel_alg_gbs": kernel_bytes / (kernel_ms * 1e-3) / 1e9,
                     "kernel_frac_of_hbm": kernel_bytes / (kernel_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
-                    "conversion_gbs": (N * P * elem / (convert_ms * 1e-3) / 1e9) if convert_ms else None}
+                    "conversion_gbs": (N * P * elem / (convert_ms * 1e-3) / 1e9) if convert_ms else None,
+                    "exact_sampled_rows": exact}
             print(json.dumps(line), flush=True)
         del data
         torch.cuda.empty_cache()
@@ -638,8 +652,8 @@ def sweep_streaming(args, torch, binding, device, stream, sides=None, counts=Non
             host = torch.empty((pool_n, side, side), dtype=torch.uint8, pin_memory=True)
             host.copy_(dev)
             del dev
-            pools[side] = host
-        host = pools[side]
+            pools[side] = (host, ens)
+        host, ens = pools[side]
         pool_n = host.shape[0]
 
         def add_all(comp):
@@ -664,6 +678,7 @@ def sweep_streaming(args, torch, binding, device, stream, sides=None, counts=Non
         with binding.Composite(side, side, trace=True, **cfg) as comp:
             add_all(comp)
             rec = comp.trace()
+            exact = identity_rows_exact(comp, ens.terrain, [ens.levels[m % pool_n] for m in range(n)])
         copies = [(float(a), float(b)) for kk, a, b in rec if int(kk) == 0]
         kernels = [(float(a), float(b)) for kk, a, b in rec if int(kk) != 0]
         gbs = n * P / (ms * 1e-3) / 1e9
@@ -683,7 +698,7 @@ def sweep_streaming(args, torch, binding, device, stream, sides=None, counts=Non
                           "member_px_per_s": n * P / (ms * 1e-3), "h2d_gbs": gbs,
                           "link_peak_gbs": peak, "link_frac": gbs / peak,
                           "overlap_fraction": metrics.overlap_fraction(copies, kernels),
-                          "mb_per_100ms": gbs * 100.0, **model}), flush=True)
+                          "mb_per_100ms": gbs * 100.0, **model, "exact_sampled_rows": exact}), flush=True)
     pools.clear()
 
 

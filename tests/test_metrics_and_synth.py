@@ -131,3 +131,29 @@ def test_pack_masks_torch_matches_numpy():
     torch = __import__("pytest").importorskip("torch")
     m = synth.scramble_nonzero(synth.random_masks(4, 3, 6, 24), 4)
     np.testing.assert_array_equal(synth.pack_masks_torch(torch.from_numpy(m)).numpy(), synth.pack_masks(m))
+
+
+def test_bench_identity_check_accepts_exact_and_rejects_off_by_one():
+    # the sweeps' sampled-row check: counts from the oracle pass, a count
+    # one off in a sampled row fails, members cycling through a pool count
+    # once per use
+    import bench
+    import oracle
+
+    ens = synth.ensemble(21, 40, 12, 9)
+    masks = synth.masks(ens)
+
+    class Fake:
+        def __init__(self, counts):
+            self.counts = counts
+
+        def render_host(self):
+            return {"counts": self.counts.astype(np.uint16)}
+
+    exact = oracle.count(masks)
+    assert bench.identity_rows_exact(Fake(exact), ens.terrain, ens.levels)
+    off = exact.copy()
+    off[-1, 7] += 1
+    assert not bench.identity_rows_exact(Fake(off), ens.terrain, ens.levels)
+    cycled = oracle.count(np.concatenate([masks, masks[:4]]))
+    assert bench.identity_rows_exact(Fake(cycled), ens.terrain, [ens.levels[m % 9] for m in range(13)])

@@ -61,7 +61,7 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-cpu-all-cores", action="store_true", help="skip the all-cores oracle timing")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--sweep", choices=["readpath", "layout", "streaming", "tiny", "batched", "serving",
+    p.add_argument("--sweep", choices=["readpath", "layout", "streaming", "tiny", "batched", "serving", "ingest",
                                        "compressed", "render"],
                    default=None,
                    help="print one JSON line per point of a workload sweep instead of the bench line")
@@ -778,6 +778,45 @@ def sweep_batched(args, torch, binding, device, stream):
         "outputs_identical": bool(same)}), flush=True)
 
 
+def sweep_ingest(args, torch, binding, device, stream):
+    """Host ingest (step a2): pageable host rasters copied into the pinned
+    ring, then uploaded through the staging buffers, against pinned rasters
+    uploaded directly; 256 masks of 4096x4096 (4.3 GB), wall clock per pass."""
+    import synth
+    W = H = 4096
+    N = args.members if args.members != 1024 else 256
+    ens = synth.ensemble(7, W, H, N)
+    dev = torch.empty((N, H, W), dtype=torch.uint8, device=device)
+    synth.fill_masks_torch(ens, dev)
+    pageable = dev.cpu().numpy()
+    pinned = torch.empty((N, H, W), dtype=torch.uint8, pin_memory=True)
+    pinned.copy_(dev)
+    del dev
+    torch.cuda.empty_cache()
+    peak = link_peak_gbs(torch, device)
+    for kind, data, threads in (("pinned", pinned, 0), ("pageable", pageable, 1), ("pageable", pageable, 4),
+                                ("pageable", pageable, 8), ("pageable", pageable, 0)):
+        with binding.Composite(W, H, chunk_members=args.chunk, staging_buffers=args.staging,
+                               stream=stream.cuda_stream, ingest_threads=threads) as comp:
+            def step():
+                comp.clear()
+                comp.add(data)
+                comp.sync()
+            for _ in range(args.warmup):
+                step()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                step()
+            ms = 1e3 * (time.perf_counter() - t0) / args.steps
+            exact = identity_rows_exact(comp, ens.terrain, ens.levels)
+        gbs = N * W * H / (ms * 1e-3) / 1e9
+        print(json.dumps({"sweep": "ingest", "input": kind, "ingest_threads": threads or "default",
+                          "width": W, "height": H, "members": N,
+                          "chunk_members": args.chunk, "staging_buffers": args.staging, "ms_per_pass": ms,
+                          "member_px_per_s": N * W * H / (ms * 1e-3), "gbs": gbs, "link_peak_gbs": peak,
+                          "link_frac": gbs / peak, "exact_sampled_rows": exact}), flush=True)
+
+
 def sweep_serving(args, torch, binding, device, stream):
     """The interactive server: a resident ensemble in HBM plus overflow members
     in pinned host memory, sessions toggling member subsets on a Poisson
@@ -1005,6 +1044,8 @@ def run_sweep(args):
         sweep_compressed(args, torch, binding, device, stream)
     elif args.sweep == "serving":
         sweep_serving(args, torch, binding, device, stream)
+    elif args.sweep == "ingest":
+        sweep_ingest(args, torch, binding, device, stream)
     elif args.sweep == "batched":
         sweep_batched(args, torch, binding, device, stream)
     elif args.sweep == "tiny":

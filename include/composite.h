@@ -116,12 +116,18 @@ typedef struct composite_config {
                                    no staging); 0 = upload through the staging buffers
                                    (the paper's pipeline); default 0                      */
     int32_t tma_box_bytes;      /* CPT_READ_TMA box width in bytes: 64, 128 or 256 (a box is
-                                   2 KiB per member: width x 2048/width rows, x 8 members);
+                                   2 KiB per member: width x 2048/width rows, x 16 members);
                                    0 = 256                                                */
     int32_t mask_format;        /* CPT_MASK_*; CPT_MASK_BITS needs CPT_MODE_COUNT and
                                    CPT_READ_LINEAR; default CPT_MASK_BYTES                */
     int32_t layout_converter;   /* CPT_READ_TEXTURE: how rasters reach the cudaArray;
                                    default CPT_CONVERT_KERNEL                             */
+    int32_t ingest_threads;     /* host threads, the calling thread included, that copy
+                                   pageable rasters into the pinned ring (step a2), each
+                                   chunk cut into pieces copied at once; 1 = the calling
+                                   thread alone; 0 = min(16, the host's hardware threads);
+                                   at most 64.  The threads start at the first pageable
+                                   add and end with the context.                          */
 } composite_config;
 
 /* Fills *cfg with the defaults listed above.  CPT_EINVAL if cfg is NULL. */

@@ -57,6 +57,7 @@ class Config(ctypes.Structure):
         ("tma_box_bytes", ctypes.c_int32),
         ("mask_format", ctypes.c_int32),
         ("layout_converter", ctypes.c_int32),
+        ("ingest_threads", ctypes.c_int32),
     ]
 
 
@@ -311,7 +312,7 @@ def caller_stream():
 def make_config(read_path="linear", staging_buffers=2, chunk_members=16, count_bits=16,
                 mode="count", trace=False, pinned_ring_bytes=0, stream=None,
                 wait_timeout_ms=0, host_read=False, tma_box_bytes=0, mask_format="bytes",
-                layout_converter="kernel") -> Config:
+                layout_converter="kernel", ingest_threads=0) -> Config:
     cfg = composite_default_config()
     cfg.read_path = READ_PATHS[read_path] if isinstance(read_path, str) else int(read_path)
     cfg.staging_buffers = staging_buffers
@@ -328,6 +329,7 @@ def make_config(read_path="linear", staging_buffers=2, chunk_members=16, count_b
         if isinstance(mask_format, str) else int(mask_format)
     cfg.layout_converter = {"copy": CPT_CONVERT_COPY, "kernel": CPT_CONVERT_KERNEL}[layout_converter] \
         if isinstance(layout_converter, str) else int(layout_converter)
+    cfg.ingest_threads = ingest_threads
     return cfg
 
 

@@ -9,15 +9,18 @@
 // kernel and records `consumed`.  No host synchronisation sits between
 // chunks: the ordering is all CUDA events, the remedy the paper gives for
 // synchronisation stalls (Section 7.1).
+#include <algorithm>
 #include <chrono>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <string>
 #include <thread>
 #include <vector>
 
 #include "composite.h"
+#include "copy_pool.cuh"
 #include "internal.cuh"
 
 using cpt::DeviceCaps;
@@ -73,6 +76,7 @@ struct composite_ctx {
     std::vector<Slot> slots;
     uint64_t next_slot = 0;
     int64_t ring_chunk = 0;
+    std::unique_ptr<cpt::CopyPool> ingest;   // step a2 copy threads (pageable inputs)
     uint8_t *out_scratch = nullptr;
     size_t out_scratch_bytes = 0;
     cudaEvent_t done_compute = nullptr, done_copy = nullptr;
@@ -203,6 +207,8 @@ int check_config(const composite_config &c) {
         return fail(nullptr, CPT_EINVAL, "bit-packed masks need CPT_MODE_COUNT and CPT_READ_LINEAR");
     if (c.tma_box_bytes != 0 && !cpt::tma_box_supported(c.tma_box_bytes))
         return fail(nullptr, CPT_EINVAL, "tma_box_bytes %d is not 0, 64, 128 or 256", c.tma_box_bytes);
+    if (c.ingest_threads < 0 || c.ingest_threads > 64)
+        return fail(nullptr, CPT_EINVAL, "ingest_threads %d not in 0..64", c.ingest_threads);
     return CPT_OK;
 }
 
@@ -442,6 +448,8 @@ int run_texture_from_device(composite_ctx *ctx, const uint8_t *src, int n, int64
 }
 
 // Pageable host rasters: host copy into the pinned ring, then as run_staged.
+constexpr int64_t kIngestPiece = 4 << 20;   // bytes per ring-copy piece
+
 int run_ring(composite_ctx *ctx, const uint8_t *src, int n, int64_t stride, int64_t pitch, int sign) {
     const int k = (int)ctx->slots.size();
     if (ctx->ring_chunk == 0) {
@@ -456,6 +464,9 @@ int run_ring(composite_ctx *ctx, const uint8_t *src, int n, int64_t stride, int6
         for (Slot &s : ctx->slots)
             CK(ctx, cudaHostAlloc(&s.ring, (size_t)chunk * ctx->member_bytes, cudaHostAllocDefault));
         ctx->ring_chunk = chunk;
+        int threads = ctx->cfg.ingest_threads;
+        if (threads == 0) threads = std::max(1, std::min(16, (int)std::thread::hardware_concurrency()));
+        if (threads > 1) ctx->ingest.reset(new cpt::CopyPool(threads - 1));
     }
     const int C = (int)ctx->ring_chunk;
     const int64_t row = ctx->row_bytes;
@@ -467,14 +478,30 @@ int run_ring(composite_ctx *ctx, const uint8_t *src, int n, int64_t stride, int6
             int rc = wait_event(ctx, s.ring_free);
             if (rc) return rc;
         }
-        for (int i = 0; i < c; ++i) {
-            const uint8_t *from = src + (int64_t)(m0 + i) * stride;
-            uint8_t *to = s.ring + (int64_t)i * ctx->member_bytes;
+        // the chunk's rasters into the ring slot: pieces of about kIngestPiece
+        // bytes (whole rows), copied by the ingest threads at once
+        const int64_t rows_per_piece = std::max<int64_t>(1, kIngestPiece / std::max<int64_t>(1, row));
+        const int64_t pieces_per_member = (ctx->height + rows_per_piece - 1) / rows_per_piece;
+        const uint8_t *base = src + (int64_t)m0 * stride;
+        uint8_t *ring = s.ring;
+        const int64_t member_bytes = ctx->member_bytes, height = ctx->height;
+        auto piece = [&](int p) {
+            const int64_t i = p / pieces_per_member;
+            const int64_t y0 = (p - i * pieces_per_member) * rows_per_piece;
+            const int64_t y1 = std::min(height, y0 + rows_per_piece);
+            const uint8_t *from = base + i * stride;
+            uint8_t *to = ring + i * member_bytes;
             if (pitch == dpitch && row == dpitch) {
-                memcpy(to, from, (size_t)ctx->member_bytes);
+                memcpy(to + y0 * dpitch, from + y0 * pitch, (size_t)((y1 - y0) * row));
             } else {
-                for (int64_t y = 0; y < ctx->height; ++y) memcpy(to + y * dpitch, from + y * pitch, (size_t)row);
+                for (int64_t y = y0; y < y1; ++y) memcpy(to + y * dpitch, from + y * pitch, (size_t)row);
             }
+        };
+        const int n_pieces = (int)(c * pieces_per_member);
+        if (ctx->ingest) {
+            ctx->ingest->run(n_pieces, piece);
+        } else {
+            for (int p = 0; p < n_pieces; ++p) piece(p);
         }
         CK(ctx, cudaStreamWaitEvent(ctx->copy, s.consumed, 0));
         int rc = trace_open(ctx, kTraceUpload, ctx->copy);
@@ -592,6 +619,7 @@ int composite_default_config(composite_config *cfg) {
     cfg->tma_box_bytes = 0;
     cfg->mask_format = CPT_MASK_BYTES;
     cfg->layout_converter = CPT_CONVERT_KERNEL;
+    cfg->ingest_threads = 0;
     return CPT_OK;
 }
 

@@ -31,7 +31,8 @@ def test_default_config(lib):
     cfg = binding.composite_default_config()
     assert (cfg.read_path, cfg.staging_buffers, cfg.chunk_members, cfg.count_bits, cfg.mode) == (0, 2, 16, 16, 0)
     assert cfg.layout_converter == binding.CPT_CONVERT_KERNEL
-    assert ctypes.sizeof(binding.Config) == 64
+    assert cfg.ingest_threads == 0
+    assert ctypes.sizeof(binding.Config) == 72
 
 
 @pytest.mark.parametrize("w,h", [(0, 5), (5, 0), (-1, 3)])
@@ -46,7 +47,8 @@ def test_begin_rejects_empty_raster(lib, w, h):
                                          ("mode", 2), ("trace", 2), ("wait_timeout_ms", -1),
                                          ("host_read", 2), ("tma_box_bytes", 32),
                                          ("tma_box_bytes", 512), ("mask_format", 2),
-                                         ("layout_converter", 2)])
+                                         ("layout_converter", 2), ("ingest_threads", -1),
+                                         ("ingest_threads", 65)])
 def test_begin_rejects_bad_config(lib, field, value):
     cfg = binding.composite_default_config()
     setattr(cfg, field, value)

@@ -451,3 +451,18 @@ def test_overlap_class_past_two_to_the_24_members():
     c = targets[None, :]
     np.testing.assert_array_equal(got["counts"].astype(np.int64), c)
     np.testing.assert_array_equal(got["bucket"], oracle.bucket(c, n))
+
+
+@pytest.mark.parametrize("threads", [1, 3, 0])
+@pytest.mark.parametrize("w,h,n", [(1024, 1024, 40), (100, 37, 300), (13, 7, 5)])
+def test_pageable_ingest_threads(threads, w, h, n):
+    # pageable rasters through the pinned ring, copied by 1, 3 or the default
+    # number of host threads; a strided view forces row-by-row pieces
+    m = synth.scramble_nonzero(synth.random_masks(160 + w + threads, n, h, w), 160)
+    big = np.zeros((n, h, w + 9), np.uint8)
+    big[:, :, :w] = m
+    with binding.Composite(w, h, ingest_threads=threads, chunk_members=16) as comp:
+        comp.add(m)
+        comp.remove(big[: n // 3, :, :w])
+        comp.add(big[: n // 3, :, :w])
+        check_counts(comp, m)

@@ -466,7 +466,15 @@ int run_ring(composite_ctx *ctx, const uint8_t *src, int n, int64_t stride, int6
         ctx->ring_chunk = chunk;
         int threads = ctx->cfg.ingest_threads;
         if (threads == 0) threads = std::max(1, std::min(16, (int)std::thread::hardware_concurrency()));
-        if (threads > 1) ctx->ingest.reset(new cpt::CopyPool(threads - 1));
+        if (threads > 1) {
+            // no exception may cross the C ABI: a host that refuses the threads
+            // gets the copy on the calling thread
+            try {
+                ctx->ingest.reset(new cpt::CopyPool(threads - 1));
+            } catch (...) {
+                ctx->ingest.reset();
+            }
+        }
     }
     const int C = (int)ctx->ring_chunk;
     const int64_t row = ctx->row_bytes;

@@ -19,18 +19,18 @@ namespace cpt {
 // thread at a time (a context is used from one thread).
 class CopyPool {
 public:
+    // Throws std::system_error when a thread cannot be started (the threads
+    // already started are stopped and joined first).
     explicit CopyPool(int workers) {
-        for (int i = 0; i < workers; ++i) threads_.emplace_back([this] { loop(); });
+        try {
+            for (int i = 0; i < workers; ++i) threads_.emplace_back([this] { loop(); });
+        } catch (...) {
+            stop_all();
+            throw;
+        }
     }
 
-    ~CopyPool() {
-        {
-            std::lock_guard<std::mutex> lock(mu_);
-            stop_ = true;
-        }
-        wake_.notify_all();
-        for (std::thread &t : threads_) t.join();
-    }
+    ~CopyPool() { stop_all(); }
 
     CopyPool(const CopyPool &) = delete;
     CopyPool &operator=(const CopyPool &) = delete;
@@ -57,6 +57,17 @@ public:
     }
 
 private:
+    void stop_all() {
+        {
+            std::lock_guard<std::mutex> lock(mu_);
+            stop_ = true;
+        }
+        wake_.notify_all();
+        for (std::thread &t : threads_)
+            if (t.joinable()) t.join();
+        threads_.clear();
+    }
+
     // Takes pieces of the current job until none is left.
     void work() {
         for (;;) {

@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <new>
 #include <string>
 #include <thread>
 #include <vector>
@@ -609,9 +610,26 @@ int wait_all(composite_ctx *ctx) {
 
 void cpt::set_thread_error(const char *message) { g_begin_error = message; }
 
+int cpt::abi_exception_status() noexcept {
+    int rc = CPT_EINVAL;
+    const char *what = "internal error (exception)";
+    try {
+        throw;
+    } catch (const std::bad_alloc &) {
+        rc = CPT_ENOMEM;
+        what = "out of host memory";
+    } catch (...) {
+    }
+    try {
+        cpt::set_thread_error(what);
+    } catch (...) {
+    }
+    return rc;
+}
+
 extern "C" {
 
-int composite_default_config(composite_config *cfg) {
+int composite_default_config(composite_config *cfg) try {
     if (!cfg) return CPT_EINVAL;
     memset(cfg, 0, sizeof *cfg);
     cfg->read_path = CPT_READ_LINEAR;
@@ -629,9 +647,11 @@ int composite_default_config(composite_config *cfg) {
     cfg->layout_converter = CPT_CONVERT_KERNEL;
     cfg->ingest_threads = 0;
     return CPT_OK;
+} catch (...) {
+    return cpt::abi_exception_status();
 }
 
-int composite_begin(composite_ctx **out, int32_t width, int32_t height, const composite_config *cfg) {
+int composite_begin(composite_ctx **out, int32_t width, int32_t height, const composite_config *cfg) try {
     g_begin_error.clear();
     if (!out) return fail(nullptr, CPT_EINVAL, "out is NULL");
     *out = nullptr;
@@ -663,9 +683,11 @@ int composite_begin(composite_ctx **out, int32_t width, int32_t height, const co
     }
     *out = ctx;
     return CPT_OK;
+} catch (...) {
+    return cpt::abi_exception_status();
 }
 
-int composite_clear(composite_ctx *ctx) {
+int composite_clear(composite_ctx *ctx) try {
     if (!ctx) return CPT_EINVAL;
     ctx->err.clear();
     const size_t bytes = (size_t)ctx->pitch_px * ctx->height *
@@ -678,16 +700,22 @@ int composite_clear(composite_ctx *ctx) {
     ctx->poisoned = false;
     memset(ctx->h_flags, 0, cpt::kFlagCount * sizeof(int));
     return CPT_OK;
+} catch (...) {
+    return cpt::abi_exception_status();
 }
 
 int composite_add_members(composite_ctx *ctx, const void *members, int32_t n_members,
-                          int64_t member_stride_bytes, int32_t row_pitch_bytes) {
+                          int64_t member_stride_bytes, int32_t row_pitch_bytes) try {
     return apply(ctx, members, n_members, member_stride_bytes, row_pitch_bytes, +1);
+} catch (...) {
+    return cpt::abi_exception_status();
 }
 
 int composite_remove_members(composite_ctx *ctx, const void *members, int32_t n_members,
-                             int64_t member_stride_bytes, int32_t row_pitch_bytes) {
+                             int64_t member_stride_bytes, int32_t row_pitch_bytes) try {
     return apply(ctx, members, n_members, member_stride_bytes, row_pitch_bytes, -1);
+} catch (...) {
+    return cpt::abi_exception_status();
 }
 
 }  // extern "C"
@@ -768,31 +796,39 @@ int render(composite_ctx *ctx, void *counts_out, uint8_t *bucket_out, uint8_t *r
 extern "C" {
 
 int composite_render(composite_ctx *ctx, void *counts_out, uint8_t *bucket_out, uint8_t *rgba_out,
-                     float *mean_out, int32_t out_on_device, const uint8_t *lut_rgba) {
+                     float *mean_out, int32_t out_on_device, const uint8_t *lut_rgba) try {
     return render(ctx, counts_out, bucket_out, rgba_out, mean_out, nullptr, out_on_device, lut_rgba);
+} catch (...) {
+    return cpt::abi_exception_status();
 }
 
 int composite_render_histogram(composite_ctx *ctx, void *counts_out, uint8_t *bucket_out, uint8_t *rgba_out,
-                               uint64_t *histogram_out, int32_t out_on_device, const uint8_t *lut_rgba) {
+                               uint64_t *histogram_out, int32_t out_on_device, const uint8_t *lut_rgba) try {
     if (ctx && !histogram_out) return fail(ctx, CPT_EINVAL, "histogram_out is NULL");
     return render(ctx, counts_out, bucket_out, rgba_out, nullptr, histogram_out, out_on_device, lut_rgba);
+} catch (...) {
+    return cpt::abi_exception_status();
 }
 
-int composite_sync(composite_ctx *ctx) {
+int composite_sync(composite_ctx *ctx) try {
     if (!ctx) return CPT_EINVAL;
     ctx->err.clear();
     int rc = wait_all(ctx);
     if (rc) return rc;
     return check_flags(ctx);
+} catch (...) {
+    return cpt::abi_exception_status();
 }
 
-int composite_member_count(const composite_ctx *ctx, int64_t *n_out) {
+int composite_member_count(const composite_ctx *ctx, int64_t *n_out) try {
     if (!ctx || !n_out) return CPT_EINVAL;
     *n_out = ctx->n_members;
     return CPT_OK;
+} catch (...) {
+    return cpt::abi_exception_status();
 }
 
-int composite_trace_read(composite_ctx *ctx, float *records, int32_t capacity, int32_t *n_out) {
+int composite_trace_read(composite_ctx *ctx, float *records, int32_t capacity, int32_t *n_out) try {
     if (!ctx || !n_out || capacity < 0 || (capacity > 0 && !records)) return CPT_EINVAL;
     ctx->err.clear();
     int rc = wait_all(ctx);
@@ -816,16 +852,20 @@ int composite_trace_read(composite_ctx *ctx, float *records, int32_t capacity, i
         records[3 * i + 2] = b;
     }
     return CPT_OK;
+} catch (...) {
+    return cpt::abi_exception_status();
 }
 
-int composite_end(composite_ctx *ctx) {
+int composite_end(composite_ctx *ctx) try {
     if (!ctx) return CPT_OK;
     int rc = wait_all(ctx);
     destroy(ctx);
     return rc == CPT_EUNDERFLOW ? CPT_OK : rc;
+} catch (...) {
+    return cpt::abi_exception_status();
 }
 
-int composite_selftest_bounded_wait(int64_t timeout_us, int32_t *gave_up_out, int64_t *waited_us_out) {
+int composite_selftest_bounded_wait(int64_t timeout_us, int32_t *gave_up_out, int64_t *waited_us_out) try {
     g_begin_error.clear();
     if (timeout_us <= 0 || timeout_us > 10000000 || !gave_up_out)
         return fail(nullptr, CPT_EINVAL, "timeout_us must be in 1..1e7 and gave_up_out not NULL");
@@ -838,10 +878,14 @@ int composite_selftest_bounded_wait(int64_t timeout_us, int32_t *gave_up_out, in
     *gave_up_out = (int32_t)h[0];
     if (waited_us_out) *waited_us_out = (int64_t)(h[1] / 1000ull);
     return CPT_OK;
+} catch (...) {
+    return cpt::abi_exception_status();
 }
 
-const char *composite_last_error(const composite_ctx *ctx) {
+const char *composite_last_error(const composite_ctx *ctx) try {
     return ctx ? ctx->err.c_str() : g_begin_error.c_str();
+} catch (...) {
+    return "internal error (exception)";
 }
 
 }  // extern "C"

@@ -761,16 +761,18 @@ void destroy_engine(composite_engine *e) {
 
 extern "C" {
 
-int composite_engine_default_config(composite_engine_config *cfg) {
+int composite_engine_default_config(composite_engine_config *cfg) try {
     if (!cfg) return CPT_EINVAL;
     memset(cfg, 0, sizeof *cfg);
     cfg->slab_members = 128;
     cfg->ctas_per_sm = 5;
     cfg->schedule = CPT_SCHEDULE_PERSISTENT;
     return CPT_OK;
+} catch (...) {
+    return cpt::abi_exception_status();
 }
 
-int composite_engine_begin(composite_engine **out, const composite_engine_config *cfg) {
+int composite_engine_begin(composite_engine **out, const composite_engine_config *cfg) try {
     g_engine_error.clear();
     if (!out) return efail(nullptr, CPT_EINVAL, "out is NULL");
     *out = nullptr;
@@ -816,14 +818,18 @@ int composite_engine_begin(composite_engine **out, const composite_engine_config
     }
     *out = e;
     return CPT_OK;
+} catch (...) {
+    return cpt::abi_exception_status();
 }
 
-int composite_engine_add_plane(composite_engine *e, int32_t width, int32_t height, int32_t *plane_out) {
+int composite_engine_add_plane(composite_engine *e, int32_t width, int32_t height, int32_t *plane_out) try {
     return composite_engine_add_plane_bits(e, width, height, 32, plane_out);
+} catch (...) {
+    return cpt::abi_exception_status();
 }
 
 int composite_engine_add_plane_bits(composite_engine *e, int32_t width, int32_t height, int32_t count_bits,
-                                    int32_t *plane_out) {
+                                    int32_t *plane_out) try {
     if (!e || !plane_out) return CPT_EINVAL;
     e->err.clear();
     if (width <= 0 || height <= 0) return efail(e, CPT_EINVAL, "plane %d x %d is empty", width, height);
@@ -842,9 +848,11 @@ int composite_engine_add_plane_bits(composite_engine *e, int32_t width, int32_t 
     if (rc) return rc;
     *plane_out = id;
     return CPT_OK;
+} catch (...) {
+    return cpt::abi_exception_status();
 }
 
-int composite_engine_free_plane(composite_engine *e, int32_t plane) {
+int composite_engine_free_plane(composite_engine *e, int32_t plane) try {
     if (!e) return CPT_EINVAL;
     e->err.clear();
     if (!plane_ok(e, plane)) return efail(e, CPT_EINVAL, "no plane %d", plane);
@@ -853,23 +861,29 @@ int composite_engine_free_plane(composite_engine *e, int32_t plane) {
     cudaFree(e->planes[plane].data);
     e->planes[plane] = PlaneRec();
     return CPT_OK;
+} catch (...) {
+    return cpt::abi_exception_status();
 }
 
-int composite_engine_clear(composite_engine *e, int32_t plane) {
+int composite_engine_clear(composite_engine *e, int32_t plane) try {
     if (!e) return CPT_EINVAL;
     e->err.clear();
     if (!plane_ok(e, plane)) return efail(e, CPT_EINVAL, "no plane %d", plane);
     return clear_plane(e, plane);
+} catch (...) {
+    return cpt::abi_exception_status();
 }
 
-int composite_engine_submit(composite_engine *e, const composite_op *ops, int32_t n_ops) {
+int composite_engine_submit(composite_engine *e, const composite_op *ops, int32_t n_ops) try {
     if (!e) return CPT_EINVAL;
     e->err.clear();
     return submit_internal(e, ops, n_ops);
+} catch (...) {
+    return cpt::abi_exception_status();
 }
 
 int composite_engine_render(composite_engine *e, const composite_render_op *ops, int32_t n_ops,
-                            const uint8_t *lut_rgba) {
+                            const uint8_t *lut_rgba) try {
     if (!e) return CPT_EINVAL;
     e->err.clear();
     std::vector<RenderDesc> descs;
@@ -883,15 +897,19 @@ int composite_engine_render(composite_engine *e, const composite_render_op *ops,
     if (rc) return rc;
     ECK(e, cudaEventRecord(u->consumed, e->stream));
     return CPT_OK;
+} catch (...) {
+    return cpt::abi_exception_status();
 }
 
-int composite_engine_member_count(const composite_engine *e, int32_t plane, int64_t *n_out) {
+int composite_engine_member_count(const composite_engine *e, int32_t plane, int64_t *n_out) try {
     if (!e || !n_out || !plane_ok(e, plane)) return CPT_EINVAL;
     *n_out = e->planes[plane].n;
     return CPT_OK;
+} catch (...) {
+    return cpt::abi_exception_status();
 }
 
-int composite_engine_sync(composite_engine *e, int32_t *bad_plane_out) {
+int composite_engine_sync(composite_engine *e, int32_t *bad_plane_out) try {
     if (!e) return CPT_EINVAL;
     e->err.clear();
     if (bad_plane_out) *bad_plane_out = -1;
@@ -905,10 +923,12 @@ int composite_engine_sync(composite_engine *e, int32_t *bad_plane_out) {
             return efail(e, CPT_EUNDERFLOW, "plane %zu: a remove took away a member that was never added", p);
         }
     return CPT_OK;
+} catch (...) {
+    return cpt::abi_exception_status();
 }
 
 int composite_engine_capture(composite_engine *e, const composite_op *ops, int32_t n_ops,
-                             const composite_render_op *rops, int32_t n_rops, const uint8_t *lut_rgba) {
+                             const composite_render_op *rops, int32_t n_rops, const uint8_t *lut_rgba) try {
     if (!e) return CPT_EINVAL;
     e->err.clear();
     std::vector<OpDesc> descs;
@@ -973,9 +993,11 @@ int composite_engine_capture(composite_engine *e, const composite_op *ops, int32
     for (const auto &pn : n_after) e->graph_planes.push_back(pn.first);
     for (int32_t i = 0; i < n_rops; ++i) e->graph_planes.push_back(rops[i].plane);
     return CPT_OK;
+} catch (...) {
+    return cpt::abi_exception_status();
 }
 
-int composite_engine_replay(composite_engine *e) {
+int composite_engine_replay(composite_engine *e) try {
     if (!e) return CPT_EINVAL;
     e->err.clear();
     if (!e->graph_exec) return efail(e, CPT_ESTATE, "nothing captured");
@@ -984,10 +1006,12 @@ int composite_engine_replay(composite_engine *e) {
     ECK(e, cudaGraphLaunch(e->graph_exec, e->stream));
     for (const auto &pn : e->graph_n) e->planes[pn.first].n = pn.second;
     return CPT_OK;
+} catch (...) {
+    return cpt::abi_exception_status();
 }
 
 int composite_engine_tune(composite_engine *e, const composite_op *ops, int32_t n_ops, int32_t repeats,
-                          int32_t *slab_out, int32_t *ctas_out) {
+                          int32_t *slab_out, int32_t *ctas_out) try {
     if (!e) return CPT_EINVAL;
     e->err.clear();
     if (repeats < 1) return efail(e, CPT_EINVAL, "repeats < 1");
@@ -1046,24 +1070,32 @@ int composite_engine_tune(composite_engine *e, const composite_op *ops, int32_t 
     if (slab_out) *slab_out = best_slab;
     if (ctas_out) *ctas_out = best_sched == CPT_SCHEDULE_GRID ? 0 : best_ctas;
     return CPT_OK;
+} catch (...) {
+    return cpt::abi_exception_status();
 }
 
-int composite_engine_get_tuning(const composite_engine *e, int32_t *slab_out, int32_t *ctas_out) {
+int composite_engine_get_tuning(const composite_engine *e, int32_t *slab_out, int32_t *ctas_out) try {
     if (!e) return CPT_EINVAL;
     if (slab_out) *slab_out = e->cfg.slab_members;
     if (ctas_out) *ctas_out = e->cfg.schedule == CPT_SCHEDULE_GRID ? 0 : e->cfg.ctas_per_sm;
     return CPT_OK;
+} catch (...) {
+    return cpt::abi_exception_status();
 }
 
-int composite_engine_end(composite_engine *e) {
+int composite_engine_end(composite_engine *e) try {
     if (!e) return CPT_OK;
     const int rc = drain(e);
     destroy_engine(e);
     return rc;
+} catch (...) {
+    return cpt::abi_exception_status();
 }
 
-const char *composite_engine_last_error(const composite_engine *e) {
+const char *composite_engine_last_error(const composite_engine *e) try {
     return e ? e->err.c_str() : g_engine_error.c_str();
+} catch (...) {
+    return "internal error (exception)";
 }
 
 }  // extern "C"

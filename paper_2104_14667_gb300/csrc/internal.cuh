@@ -104,4 +104,10 @@ cudaError_t launch_render_mean(const Plane &p, uint64_t n_members, float *mean_o
 // composite_last_error(NULL) returns).
 void set_thread_error(const char *message);
 
+// Status for a C++ exception caught at an entry point of the C ABI (none may
+// cross it), called from the catch handler: CPT_ENOMEM for a failed host
+// allocation, CPT_EINVAL for anything else; the message goes to
+// set_thread_error.
+int abi_exception_status() noexcept;
+
 }  // namespace cpt

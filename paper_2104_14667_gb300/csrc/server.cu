@@ -433,7 +433,7 @@ void destroy_server(composite_server *s) {
 
 extern "C" {
 
-int composite_server_default_config(composite_server_config *cfg) {
+int composite_server_default_config(composite_server_config *cfg) try {
     if (!cfg) return CPT_EINVAL;
     memset(cfg, 0, sizeof *cfg);
     cfg->max_sessions = 64;
@@ -441,9 +441,11 @@ int composite_server_default_config(composite_server_config *cfg) {
     cfg->staging_members = 64;
     cfg->max_cycles_in_flight = 4;
     return CPT_OK;
+} catch (...) {
+    return cpt::abi_exception_status();
 }
 
-int composite_server_begin(composite_server **out, const composite_server_config *cfg) {
+int composite_server_begin(composite_server **out, const composite_server_config *cfg) try {
     g_server_error.clear();
     if (!out || !cfg) return sfail(nullptr, CPT_EINVAL, "out and cfg must not be NULL");
     *out = nullptr;
@@ -540,9 +542,11 @@ int composite_server_begin(composite_server **out, const composite_server_config
     }
     *out = s;
     return CPT_OK;
+} catch (...) {
+    return cpt::abi_exception_status();
 }
 
-int composite_server_open_session(composite_server *s, int32_t *session_out) {
+int composite_server_open_session(composite_server *s, int32_t *session_out) try {
     if (!s || !session_out) return CPT_EINVAL;
     s->err.clear();
     int32_t id = -1;
@@ -571,9 +575,11 @@ int composite_server_open_session(composite_server *s, int32_t *session_out) {
     s->used_bytes += s->plane_bytes;
     *session_out = id;
     return CPT_OK;
+} catch (...) {
+    return cpt::abi_exception_status();
 }
 
-int composite_server_close_session(composite_server *s, int32_t session) {
+int composite_server_close_session(composite_server *s, int32_t session) try {
     if (!s) return CPT_EINVAL;
     s->err.clear();
     if (session < 0 || session >= (int32_t)s->sessions.size() || !s->sessions[session].open)
@@ -585,10 +591,12 @@ int composite_server_close_session(composite_server *s, int32_t session) {
     s->used_bytes -= s->plane_bytes;
     ss = Session();
     return CPT_OK;
+} catch (...) {
+    return cpt::abi_exception_status();
 }
 
 int composite_server_request(composite_server *s, int32_t session, const int32_t *toggle, int32_t n,
-                             uint32_t *counts_out, uint8_t *bucket_out, uint8_t *rgba_out, int64_t *request_id_out) {
+                             uint32_t *counts_out, uint8_t *bucket_out, uint8_t *rgba_out, int64_t *request_id_out) try {
     if (!s) return CPT_EINVAL;
     s->err.clear();
     if (session < 0 || session >= (int32_t)s->sessions.size() || !s->sessions[session].open)
@@ -614,9 +622,11 @@ int composite_server_request(composite_server *s, int32_t session, const int32_t
     ++s->stats.queued;
     if (request_id_out) *request_id_out = s->next_id - 1;
     return CPT_OK;
+} catch (...) {
+    return cpt::abi_exception_status();
 }
 
-int composite_server_pump(composite_server *s, int64_t *completed, int32_t capacity, int32_t *n_completed) {
+int composite_server_pump(composite_server *s, int64_t *completed, int32_t capacity, int32_t *n_completed) try {
     if (!s || capacity < 0 || (capacity > 0 && !completed)) return CPT_EINVAL;
     s->err.clear();
     int32_t dummy = 0;
@@ -633,9 +643,11 @@ int composite_server_pump(composite_server *s, int64_t *completed, int32_t capac
                 std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - t0).count();
         if (rc || !launched) return rc;
     }
+} catch (...) {
+    return cpt::abi_exception_status();
 }
 
-int composite_server_drain(composite_server *s) {
+int composite_server_drain(composite_server *s) try {
     if (!s) return CPT_EINVAL;
     s->err.clear();
     auto deadline = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms(s));
@@ -652,30 +664,40 @@ int composite_server_drain(composite_server *s) {
         if (spin > 200) std::this_thread::sleep_for(std::chrono::microseconds(50));
     }
     return CPT_OK;
+} catch (...) {
+    return cpt::abi_exception_status();
 }
 
-int composite_server_session_members(const composite_server *s, int32_t session, int64_t *n_out) {
+int composite_server_session_members(const composite_server *s, int32_t session, int64_t *n_out) try {
     if (!s || !n_out || session < 0 || session >= (int32_t)s->sessions.size() || !s->sessions[session].open)
         return CPT_EINVAL;
     *n_out = s->sessions[session].n_view;
     return CPT_OK;
+} catch (...) {
+    return cpt::abi_exception_status();
 }
 
-int composite_server_get_stats(const composite_server *s, composite_server_stats *out) {
+int composite_server_get_stats(const composite_server *s, composite_server_stats *out) try {
     if (!s || !out) return CPT_EINVAL;
     *out = s->stats;
     return CPT_OK;
+} catch (...) {
+    return cpt::abi_exception_status();
 }
 
-int composite_server_end(composite_server *s) {
+int composite_server_end(composite_server *s) try {
     if (!s) return CPT_OK;
     const int rc = composite_server_drain(s);
     destroy_server(s);
     return rc;
+} catch (...) {
+    return cpt::abi_exception_status();
 }
 
-const char *composite_server_last_error(const composite_server *s) {
+const char *composite_server_last_error(const composite_server *s) try {
     return s ? s->err.c_str() : g_server_error.c_str();
+} catch (...) {
+    return "internal error (exception)";
 }
 
 }  // extern "C"

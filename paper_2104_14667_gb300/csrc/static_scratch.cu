@@ -72,7 +72,7 @@ extern "C" int composite_oneshot_static(const void *members, int32_t n_members,
                                         int64_t member_stride_bytes, int32_t row_pitch_bytes,
                                         int32_t width, int32_t height, uint32_t *counts_out,
                                         uint8_t *bucket_out, uint8_t *rgba_out,
-                                        const uint8_t *lut_rgba, void *cuda_stream) {
+                                        const uint8_t *lut_rgba, void *cuda_stream) try {
     if (width <= 0 || height <= 0) return reject(CPT_EINVAL, "raster is empty");
     if (n_members < 0) return reject(CPT_EINVAL, "n_members < 0");
     const int64_t pitch_px = ((int64_t)width + 15) / 16 * 16;
@@ -119,4 +119,6 @@ extern "C" int composite_oneshot_static(const void *members, int32_t n_members,
                                       reinterpret_cast<uint32_t *>(rgba_out), lut, caps, stream);
     if (e != cudaSuccess) return reject(CPT_ECUDA, cudaGetErrorString(e));
     return CPT_OK;
+} catch (...) {
+    return cpt::abi_exception_status();
 }

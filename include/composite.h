@@ -40,6 +40,9 @@
  *   - One context per host thread; contexts are independent.
  *   - The library never falls back to a CPU implementation: without a usable
  *     CUDA device every compute call returns CPT_ECUDA.
+ *   - No C++ exception crosses this interface (nor those of composite_engine.h
+ *     and composite_server.h): a failed host allocation inside a call returns
+ *     CPT_ENOMEM, with its message in composite_last_error(NULL).
  */
 #ifndef COMPOSITE_H
 #define COMPOSITE_H
@@ -55,7 +58,7 @@ typedef struct composite_ctx composite_ctx;   /* opaque, owned by the library */
 typedef enum composite_status {
     CPT_OK = 0,
     CPT_EINVAL = -1,      /* bad argument; the context is unchanged            */
-    CPT_ENOMEM = -2,      /* device or pinned allocation failed                */
+    CPT_ENOMEM = -2,      /* device, pinned or host allocation failed          */
     CPT_ECUDA = -3,       /* CUDA runtime/driver error (message in last_error) */
     CPT_ESTATE = -4,      /* context poisoned by an earlier underflow          */
     CPT_EUNDERFLOW = -5,  /* a remove took away a member that was never added  */

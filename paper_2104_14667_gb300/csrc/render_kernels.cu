@@ -118,6 +118,9 @@ render_counts_vec_kernel(Plane p, ClassDivisor div, CountT *counts_out, uint8_t 
                 d[q] = make_uint4(table[b[4 * q]], table[b[4 * q + 1]], table[b[4 * q + 2]], table[b[4 * q + 3]]);
         }
         if (kHist) {
+            // one shared-memory atomic per run of equal classes (aggregating
+            // the runs across the warp first, by cooperative-groups labeled
+            // partitions at every pixel, took 8192^2 from 146 to 439 us)
             uint32_t run = 1;
 #pragma unroll
             for (int j = 1; j < 16; ++j) {

@@ -8,9 +8,10 @@
 // ops' first items.  Each lane folds its groups of one slab's members into
 // packed byte counters (member i of the op read at base + idx(i) * stride,
 // the slab's indices staged in the warp's shared memory) and adds the counts
-// into the op's uint32 plane: with L2 atomics, or with a plain read-modify-
-// write when the op is alone on its plane and has a single slab.  The render
-// launch works the same way over (plane, tile) items, per CTA.  Consecutive
+// into the op's plane (uint32, or uint16 for a 16-bit plane): with L2
+// atomics, or with a plain read-modify-write when the op is alone on its
+// plane and has a single slab.  The render launch deals warp-level (plane,
+// chunk) items round robin to its warps.  Consecutive
 // items are neighbouring chunks of the same slab, so concurrently running
 // warps read neighbouring bytes of the same members.
 #include <algorithm>

@@ -64,7 +64,7 @@ cudaError_t launch_convert_to_array(const void *src, int64_t pitch, int64_t memb
 // TMA read path: tensor map over the batch, tiles staged in shared memory.
 // The tensor map must come from encode_tma_map for the same batch.
 // box_bytes: the x extent of a box in bytes (64, 128 or 256); a box is always
-// 2 KiB per member (box_bytes x 2048/box_bytes rows) x 8 members.
+// 2 KiB per member (box_bytes x 2048/box_bytes rows) x 16 members.
 cudaError_t launch_count_tma(const CUtensorMap &map, const RasterBatch &b, const Plane &p, int sign,
                              int *flags, uint64_t timeout_ns, int box_bytes, const DeviceCaps &caps,
                              cudaStream_t s);

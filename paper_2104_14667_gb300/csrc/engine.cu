@@ -276,7 +276,12 @@ __device__ __forceinline__ void run_item(const OpDesc &op, uint32_t item, int la
 // Persistent schedule: warps claim items from the counter one ahead (lane 0
 // asks for the next while the warp works on the current one), so warps
 // never wait for one another and uneven items balance across the GPU.
-__global__ void __launch_bounds__(kThreads, 5)
+// Two register budgets: launched with four or five CTAs per SM, 48 registers
+// (a few spill; four such CTAs still leave a quarter of the register file to
+// a kernel on another stream); with three or fewer, 64 and no spills (three
+// such CTAs leave the same quarter).
+template <int kCtasPerSm>
+__global__ void __launch_bounds__(kThreads, kCtasPerSm)
 engine_accumulate_kernel(const OpDesc *ops, int n_ops, uint32_t n_items, uint32_t *counter, int *flags) {
     __shared__ int32_t s_index[kThreads / 32][kMaxSlab + 1];
     __shared__ uint32_t s_starts[kSmemStarts];
@@ -681,9 +686,14 @@ int launch_accumulate(composite_engine *e, const void *d_ops, int n_ops, int64_t
     } else {
         ECK(e, cudaMemsetAsync(counter, 0, sizeof(uint32_t), e->stream));
         const int64_t warps_needed = (n_items + kThreads / 32 - 1) / (kThreads / 32);
-        engine_accumulate_kernel<<<(unsigned)std::min<int64_t>(persistent_grid(e, n_items), warps_needed),
-                                   kThreads, 0, e->stream>>>(static_cast<const OpDesc *>(d_ops), n_ops,
-                                                             (uint32_t)n_items, counter, e->d_flags);
+        const unsigned grid = (unsigned)std::min<int64_t>(persistent_grid(e, n_items), warps_needed);
+        const OpDesc *ops = static_cast<const OpDesc *>(d_ops);
+        if (e->cfg.ctas_per_sm >= 4)
+            engine_accumulate_kernel<5><<<grid, kThreads, 0, e->stream>>>(ops, n_ops, (uint32_t)n_items, counter,
+                                                                          e->d_flags);
+        else
+            engine_accumulate_kernel<4><<<grid, kThreads, 0, e->stream>>>(ops, n_ops, (uint32_t)n_items, counter,
+                                                                          e->d_flags);
     }
     ECK(e, cudaGetLastError());
     return CPT_OK;

@@ -389,7 +389,7 @@ class Composite:
         return composite_trace_read(self.ctx)
 
     def close(self):
-        if self.ctx is not None:
+        if getattr(self, "ctx", None) is not None:
             ctx, self.ctx = self.ctx, None
             composite_end(ctx)
             self._borrowed.clear()

@@ -11,14 +11,18 @@
 // synchronisation stalls (Section 7.1).
 #include <algorithm>
 #include <chrono>
+#include <cstdlib>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <memory>
 #include <new>
+#include <stdexcept>
 #include <string>
 #include <thread>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "composite.h"
 #include "copy_pool.cuh"
@@ -272,6 +276,7 @@ int setup(composite_ctx *ctx) {
 
     ctx->slots.resize(c.staging_buffers);
     for (Slot &s : ctx->slots) {
+        if (cpt::fault_injected("staging_alloc")) return fail(ctx, CPT_ENOMEM, "staging buffer allocation refused (injected)");
         CK(ctx, cudaMalloc(&s.stage, (size_t)c.chunk_members * ctx->member_bytes));
         CK(ctx, cudaEventCreateWithFlags(&s.ready, cudaEventDisableTiming));
         CK(ctx, cudaEventCreateWithFlags(&s.consumed, cudaEventDisableTiming));
@@ -411,6 +416,7 @@ Slot &next_slot(composite_ctx *ctx) {
 int run_staged(composite_ctx *ctx, const uint8_t *src, int n, int64_t stride, int64_t pitch, int sign) {
     const int C = ctx->cfg.chunk_members;
     for (int m0 = 0; m0 < n; m0 += C) {
+        const cpt::TraceRange chunk_range("composite chunk");
         const int c = n - m0 < C ? n - m0 : C;
         Slot &s = next_slot(ctx);
         CK(ctx, cudaStreamWaitEvent(ctx->copy, s.consumed, 0));
@@ -434,6 +440,7 @@ int run_staged(composite_ctx *ctx, const uint8_t *src, int n, int64_t stride, in
 int run_texture_from_device(composite_ctx *ctx, const uint8_t *src, int n, int64_t stride, int64_t pitch, int sign) {
     const int C = ctx->cfg.chunk_members;
     for (int m0 = 0; m0 < n; m0 += C) {
+        const cpt::TraceRange chunk_range("composite chunk");
         const int c = n - m0 < C ? n - m0 : C;
         Slot &s = next_slot(ctx);
         CK(ctx, cudaStreamWaitEvent(ctx->copy, s.consumed, 0));
@@ -462,8 +469,21 @@ int run_ring(composite_ctx *ctx, const uint8_t *src, int n, int64_t stride, int6
                             (long long)ctx->cfg.pinned_ring_bytes, k);
             if (fit < chunk) chunk = fit;
         }
-        for (Slot &s : ctx->slots)
-            CK(ctx, cudaHostAlloc(&s.ring, (size_t)chunk * ctx->member_bytes, cudaHostAllocDefault));
+        for (Slot &s : ctx->slots) {
+            const cudaError_t e = cpt::fault_injected("pinned_ring")
+                                      ? cudaErrorMemoryAllocation
+                                      : cudaHostAlloc(&s.ring, (size_t)chunk * ctx->member_bytes, cudaHostAllocDefault);
+            if (e != cudaSuccess) {
+                // all or nothing: a later call starts the ring afresh
+                for (Slot &t : ctx->slots)
+                    if (t.ring) {
+                        cudaFreeHost(t.ring);
+                        t.ring = nullptr;
+                    }
+                cudaGetLastError();
+                return fail(ctx, CPT_ENOMEM, "pinned ring allocation failed: %s", cudaGetErrorString(e));
+            }
+        }
         ctx->ring_chunk = chunk;
         int threads = ctx->cfg.ingest_threads;
         if (threads == 0) threads = std::max(1, std::min(16, (int)std::thread::hardware_concurrency()));
@@ -471,6 +491,7 @@ int run_ring(composite_ctx *ctx, const uint8_t *src, int n, int64_t stride, int6
             // no exception may cross the C ABI: a host that refuses the threads
             // gets the copy on the calling thread
             try {
+                if (cpt::fault_injected("ingest_threads")) throw std::runtime_error("ingest threads refused (injected)");
                 ctx->ingest.reset(new cpt::CopyPool(threads - 1));
             } catch (...) {
                 ctx->ingest.reset();
@@ -481,6 +502,7 @@ int run_ring(composite_ctx *ctx, const uint8_t *src, int n, int64_t stride, int6
     const int64_t row = ctx->row_bytes;
     const int64_t dpitch = ctx->stage_pitch;
     for (int m0 = 0; m0 < n; m0 += C) {
+        const cpt::TraceRange chunk_range("composite chunk");
         const int c = n - m0 < C ? n - m0 : C;
         Slot &s = next_slot(ctx);
         if (s.ring_used) {
@@ -530,6 +552,7 @@ int run_ring(composite_ctx *ctx, const uint8_t *src, int n, int64_t stride, int6
 }
 
 int apply(composite_ctx *ctx, const void *members, int32_t n, int64_t stride, int32_t pitch, int sign) {
+    const cpt::TraceRange range(sign > 0 ? "composite_add_members" : "composite_remove_members");
     if (!ctx) return CPT_EINVAL;
     ctx->err.clear();
     if (ctx->poisoned) return fail(ctx, CPT_ESTATE, "context poisoned by an earlier underflow; clear it");
@@ -609,6 +632,22 @@ int wait_all(composite_ctx *ctx) {
 }  // namespace
 
 void cpt::set_thread_error(const char *message) { g_begin_error = message; }
+
+bool cpt::fault_injected(const char *site) {
+    const char *v = std::getenv("CPT_FAULT_INJECT");
+    if (!v || !*v) return false;
+    const size_t n = strlen(site);
+    for (const char *p = v;;) {
+        const char *q = strchr(p, ',');
+        const size_t len = q ? (size_t)(q - p) : strlen(p);
+        if (len == n && strncmp(p, site, n) == 0) return true;
+        if (!q) return false;
+        p = q + 1;
+    }
+}
+
+cpt::TraceRange::TraceRange(const char *name) { nvtxRangePushA(name); }
+cpt::TraceRange::~TraceRange() { nvtxRangePop(); }
 
 int cpt::abi_exception_status() noexcept {
     int rc = CPT_EINVAL;
@@ -724,6 +763,7 @@ namespace {
 
 int render(composite_ctx *ctx, void *counts_out, uint8_t *bucket_out, uint8_t *rgba_out, float *mean_out,
            uint64_t *hist_out, int32_t out_on_device, const uint8_t *lut_rgba) {
+    const cpt::TraceRange range("composite_render");
     if (!ctx) return CPT_EINVAL;
     ctx->err.clear();
     if (ctx->poisoned) return fail(ctx, CPT_ESTATE, "context poisoned by an earlier underflow; clear it");

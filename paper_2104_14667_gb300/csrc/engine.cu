@@ -25,6 +25,7 @@
 
 #include "composite_engine.h"
 #include "bit_count.cuh"
+#include "internal.cuh"
 #include "overlap_class.cuh"
 
 namespace {
@@ -718,6 +719,7 @@ int clear_plane(composite_engine *e, int32_t p) {
 }
 
 int submit_internal(composite_engine *e, const composite_op *ops, int32_t n_ops) {
+    const cpt::TraceRange range("composite_engine_submit");
     std::vector<OpDesc> descs;
     std::vector<std::pair<int32_t, int64_t>> n_after;
     int64_t items = 0;
@@ -851,6 +853,7 @@ int composite_engine_add_plane_bits(composite_engine *e, int32_t width, int32_t 
     r.height = height;
     r.pitch_px = ((int64_t)width + 15) / 16 * 16;
     r.count_bits = count_bits;
+    if (cpt::fault_injected("engine_plane")) return efail(e, CPT_ENOMEM, "plane allocation refused (injected)");
     ECK(e, cudaMalloc(&r.data, r.bytes()));
     r.alive = true;
     e->planes.push_back(r);

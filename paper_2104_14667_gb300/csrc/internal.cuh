@@ -104,6 +104,22 @@ cudaError_t launch_render_mean(const Plane &p, uint64_t n_members, float *mean_o
 // composite_last_error(NULL) returns).
 void set_thread_error(const char *message);
 
+// Host-side fault injection for tests: the environment variable
+// CPT_FAULT_INJECT holds a comma-separated list of sites -- staging_alloc,
+// pinned_ring, ingest_threads, engine_plane, server_stage -- and a listed site
+// behaves as if its host-side request (a device or pinned allocation, the
+// ingest threads) had been refused.  Nothing on the device is affected.
+bool fault_injected(const char *site);
+
+// NVTX range around a host-side phase (a call, a pipeline chunk), for
+// timeline profilers; a no-op call when no profiler is attached.
+struct TraceRange {
+    explicit TraceRange(const char *name);
+    ~TraceRange();
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
+
 // Status for a C++ exception caught at an entry point of the C ABI (none may
 // cross it), called from the catch handler: CPT_ENOMEM for a failed host
 // allocation, CPT_EINVAL for anything else; the message goes to

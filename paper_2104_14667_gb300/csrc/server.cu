@@ -178,6 +178,7 @@ int reap(composite_server *s, int64_t *completed, int32_t capacity, int32_t *n_c
 
 // Builds and queues one cycle from the admissible queued requests.
 int launch_cycle(composite_server *s, bool *launched) {
+    const cpt::TraceRange range("composite_server cycle");
     *launched = false;
     Cycle *cyc = nullptr;
     for (Cycle &c : s->cycles)
@@ -519,6 +520,8 @@ int composite_server_begin(composite_server **out, const composite_server_config
         if (rc) return sfail(s, rc, "engine: %s", composite_engine_last_error(nullptr));
         const int64_t stage = c.n_overflow > 0 ? 2ll * c.staging_members * c.member_stride_bytes : 0;
         if (!budget_allows(s, stage)) return sfail(s, CPT_ENOMEM, "staging halves exceed the device-memory budget");
+        if (stage && cpt::fault_injected("server_stage"))
+            return sfail(s, CPT_ENOMEM, "staging allocation refused (injected)");
         if (stage) SCK(s, cudaMalloc(&s->d_stage, (size_t)stage));
         s->used_bytes += stage;
         for (int h = 0; h < 2; ++h) {

@@ -39,3 +39,60 @@ def test_host_wait_times_out_and_context_recovers():
         comp.sync()
         got = comp.render_host()
     np.testing.assert_array_equal(got["counts"].astype(np.int64), oracle.count(small) * 32 * 64)
+
+
+# Host-side fault injection (CPT_FAULT_INJECT): a listed site behaves as if
+# its allocation, or its threads, had been refused; nothing on the device.
+
+def test_injected_pinned_ring_refusal_then_recovery(monkeypatch):
+    w, h, n = 96, 40, 50
+    m = synth.scramble_nonzero(synth.random_masks(170, n, h, w), 170)
+    with binding.Composite(w, h, chunk_members=8) as comp:
+        monkeypatch.setenv("CPT_FAULT_INJECT", "pinned_ring")
+        with pytest.raises(binding.CompositeError) as e:
+            comp.add(m)                      # pageable: needs the pinned ring
+        assert e.value.code == binding.CPT_ENOMEM
+        assert comp.n == 0
+        monkeypatch.delenv("CPT_FAULT_INJECT")
+        comp.add(m)
+        got = comp.render_host()
+    np.testing.assert_array_equal(got["counts"].astype(np.int64), oracle.count(m))
+
+
+def test_injected_staging_refusal_at_begin(monkeypatch):
+    monkeypatch.setenv("CPT_FAULT_INJECT", "staging_alloc")
+    with pytest.raises(binding.CompositeError) as e:
+        binding.Composite(64, 8)
+    assert e.value.code == binding.CPT_ENOMEM
+    monkeypatch.delenv("CPT_FAULT_INJECT")
+    with binding.Composite(64, 8) as comp:
+        comp.add(np.ones((3, 8, 64), np.uint8))
+        assert (comp.render_host()["counts"] == 3).all()
+
+
+def test_injected_thread_refusal_copies_on_the_calling_thread(monkeypatch):
+    w, h, n = 300, 200, 40
+    m = synth.random_masks(171, n, h, w)
+    monkeypatch.setenv("CPT_FAULT_INJECT", "ingest_threads,engine_plane_unused")
+    with binding.Composite(w, h, ingest_threads=8, chunk_members=16) as comp:
+        comp.add(m)
+        got = comp.render_host()
+    np.testing.assert_array_equal(got["counts"].astype(np.int64), oracle.count(m))
+
+
+def test_injected_engine_and_server_refusals(monkeypatch):
+    monkeypatch.setenv("CPT_FAULT_INJECT", "engine_plane,server_stage")
+    with binding.Engine() as eng:
+        with pytest.raises(binding.CompositeError) as e:
+            eng.add_plane(32, 8)
+        assert e.value.code == binding.CPT_ENOMEM
+        res = torch.zeros((4, 8, 32), dtype=torch.uint8, device="cuda")
+        ovf = torch.zeros((4, 8, 32), dtype=torch.uint8).pin_memory()
+        with pytest.raises(binding.CompositeError) as e:
+            binding.Server(res, ovf)
+        assert e.value.code == binding.CPT_ENOMEM
+        monkeypatch.delenv("CPT_FAULT_INJECT")
+        p = eng.add_plane(32, 8)
+        eng.submit([eng.op(p, res)])
+        eng.sync()
+        assert eng.member_count(p) == 4

@@ -206,6 +206,24 @@ int composite_sync(composite_ctx *ctx);
 /* *n_out = N, the number of members in the multiset. */
 int composite_member_count(const composite_ctx *ctx, int64_t *n_out);
 
+/* Resume from a checkpoint: replaces the composite by the given per-pixel
+ * counts and member count N, as if the members behind them had been added to
+ * an empty composite.  The other half of the checkpoint is composite_render
+ * with counts_out plus composite_member_count (a composite is fully described
+ * by its counts and N; Section 2's interactive list may then go on adding and
+ * removing).  CPT_MODE_COUNT only (a mean-depth composite renders means, not
+ * its sums).
+ *   counts: width x height dense rows of the context's count type (uint16 or
+ *           uint32), host (pageable or pinned) or device memory, aligned to
+ *           its element; copied, not borrowed, stream-ordered after earlier
+ *           work.
+ *   n_members: 0 <= N <= the count type's limit.  Every count must be <= N;
+ *           host counts are checked (CPT_EINVAL, nothing changed), device
+ *           counts are the caller's responsibility (a count above N renders
+ *           as class 255).
+ * Clears the underflow state like composite_clear. */
+int composite_load_counts(composite_ctx *ctx, const void *counts, int64_t n_members);
+
 /* With config.trace = 1: copies up to `capacity` records of 3 floats
  * {kind, start_ms, end_ms} into `records` (host memory), kind 0 = upload,
  * 1 = layout conversion, 2 = accumulation kernel, times relative to the

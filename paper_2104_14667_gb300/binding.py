@@ -91,6 +91,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
             "composite_render_histogram": (ctypes.c_int, [vp, vp, vp, vp, vp, i32, vp]),
             "composite_sync": (ctypes.c_int, [vp]),
             "composite_member_count": (ctypes.c_int, [vp, ctypes.POINTER(i64)]),
+            "composite_load_counts": (ctypes.c_int, [vp, vp, i64]),
             "composite_trace_read": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_float), i32,
                                                     ctypes.POINTER(i32)]),
             "composite_end": (ctypes.c_int, [vp]),
@@ -380,6 +381,22 @@ class Composite:
         rgba = np.empty((h, w, 4), np.uint8)
         self.render(counts, bucket, rgba, lut=lut)
         return {"counts": counts, "bucket": bucket, "rgba": rgba}
+
+    def load_counts(self, counts, n_members: int):
+        """Resumes from a checkpoint: the composite becomes `counts` (a dense
+        [H, W] array of the count type, host or device) with N members."""
+        lib = load()
+        item = self.config.count_bits // 8
+        if hasattr(counts, "data_ptr"):
+            if not counts.is_contiguous() or counts.element_size() != item or tuple(counts.shape) != (self.height, self.width):
+                raise ValueError(f"counts must be a contiguous [{self.height}, {self.width}] tensor of {8 * item}-bit counts")
+            ptr = counts.data_ptr()
+        else:
+            counts = np.ascontiguousarray(counts)
+            if counts.itemsize != item or counts.shape != (self.height, self.width):
+                raise ValueError(f"counts must be [{self.height}, {self.width}] of {8 * item}-bit counts")
+            ptr = counts.ctypes.data
+        _check(lib, self.ctx, lib.composite_load_counts(self.ctx, ctypes.c_void_p(ptr), int(n_members)))
 
     def sync(self):
         composite_sync(self.ctx)

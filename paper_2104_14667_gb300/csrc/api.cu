@@ -726,6 +726,47 @@ int composite_begin(composite_ctx **out, int32_t width, int32_t height, const co
     return cpt::abi_exception_status();
 }
 
+int composite_load_counts(composite_ctx *ctx, const void *counts, int64_t n_members) try {
+    if (!ctx) return CPT_EINVAL;
+    ctx->err.clear();
+    if (ctx->cfg.mode != CPT_MODE_COUNT) return fail(ctx, CPT_EINVAL, "counts can be loaded only in CPT_MODE_COUNT");
+    if (!counts) return fail(ctx, CPT_EINVAL, "counts is NULL");
+    const int64_t limit = ctx->cfg.count_bits == 16 ? 0xFFFFll : 0xFFFFFFFFll;
+    if (n_members < 0 || n_members > limit)
+        return fail(ctx, CPT_EINVAL, "n_members %lld outside 0..%lld", (long long)n_members, (long long)limit);
+    const size_t elem = (size_t)ctx->cfg.count_bits / 8;
+    if (reinterpret_cast<uintptr_t>(counts) % elem) return fail(ctx, CPT_EINVAL, "counts not aligned to its element");
+    const MemKind kind = memory_kind(counts);
+    const int64_t px = (int64_t)ctx->width * ctx->height;
+    if (kind != kDevice) {
+        // host counts are checked against N before anything changes
+        for (int64_t i = 0; i < px; ++i) {
+            const uint64_t c = elem == 2 ? static_cast<const uint16_t *>(counts)[i] : static_cast<const uint32_t *>(counts)[i];
+            if (c > (uint64_t)n_members)
+                return fail(ctx, CPT_EINVAL, "count %llu at pixel %lld exceeds N = %lld", (unsigned long long)c,
+                            (long long)i, (long long)n_members);
+        }
+    }
+    CK(ctx, cudaMemcpy2DAsync(ctx->plane.data, (size_t)ctx->pitch_px * elem, counts, (size_t)ctx->width * elem,
+                              (size_t)ctx->width * elem, (size_t)ctx->height, cudaMemcpyDefault, ctx->compute));
+    CK(ctx, cudaMemsetAsync(ctx->flags, 0, cpt::kFlagCount * sizeof(int), ctx->compute));
+    if (kind != kDevice) {
+        // host counts: the caller may reuse them as soon as the call returns
+        cudaEvent_t copied = nullptr;
+        CK(ctx, cudaEventCreateWithFlags(&copied, cudaEventDisableTiming));
+        cudaError_t e = cudaEventRecord(copied, ctx->compute);
+        const int rc = e == cudaSuccess ? wait_event(ctx, copied) : cuda_fail(ctx, e, "cudaEventRecord");
+        cudaEventDestroy(copied);
+        if (rc) return rc;
+    }
+    ctx->n_members = n_members;
+    ctx->poisoned = false;
+    memset(ctx->h_flags, 0, cpt::kFlagCount * sizeof(int));
+    return CPT_OK;
+} catch (...) {
+    return cpt::abi_exception_status();
+}
+
 int composite_clear(composite_ctx *ctx) try {
     if (!ctx) return CPT_EINVAL;
     ctx->err.clear();

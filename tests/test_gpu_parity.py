@@ -466,3 +466,44 @@ def test_pageable_ingest_threads(threads, w, h, n):
         comp.remove(big[: n // 3, :, :w])
         comp.add(big[: n // 3, :, :w])
         check_counts(comp, m)
+
+
+@pytest.mark.parametrize("count_bits", [16, 32])
+@pytest.mark.parametrize("source", ["pageable", "pinned", "device"])
+def test_checkpoint_and_resume(count_bits, source):
+    # save: the rendered counts and N; resume: load them into a fresh context,
+    # then keep adding and removing -- the same as one context all along
+    w, h = 100, 37
+    a = synth.scramble_nonzero(synth.random_masks(180, 60, h, w), 180)
+    b = synth.random_masks(181, 25, h, w)
+    dtype = np.uint16 if count_bits == 16 else np.uint32
+    with binding.Composite(w, h, count_bits=count_bits) as first:
+        first.add(a)
+        saved = first.render_host()["counts"].astype(dtype)
+        n = first.n
+    if source == "pageable":
+        counts = saved
+    else:
+        t = torch.from_numpy(saved.view(np.int16 if count_bits == 16 else np.int32))
+        counts = t.pin_memory() if source == "pinned" else t.cuda()
+    with binding.Composite(w, h, count_bits=count_bits) as resumed:
+        resumed.load_counts(counts, n)
+        assert resumed.n == n
+        check_counts(resumed, a)
+        resumed.add(b)
+        resumed.remove(a[:20])
+        check_counts(resumed, np.concatenate([a[20:], b]))
+
+
+def test_resume_rejects_counts_above_n():
+    w, h = 16, 4
+    bad = np.full((h, w), 3, np.uint16)
+    with binding.Composite(w, h) as comp:
+        with pytest.raises(binding.CompositeError) as e:
+            comp.load_counts(bad, 2)
+        assert e.value.code == binding.CPT_EINVAL
+        with pytest.raises(binding.CompositeError) as e:
+            comp.load_counts(bad, 70000)
+        assert e.value.code == binding.CPT_EINVAL
+        comp.load_counts(bad, 3)
+        assert (comp.render_host()["bucket"] == 255).all()

@@ -20,11 +20,17 @@
  *     that is cheaper, a clear and a re-add of the new member set;
  *   - resident members of every admitted request: one engine submit (a
  *     single persistent launch, members gathered by index lists);
- *   - overflow members: uploaded from pinned host memory into two device
- *     staging halves on a copy stream, alternating, each half followed by one
- *     engine submit for all requests' members in it (the paper's dual-buffer
- *     upload, Section 4, shared by the requests of the cycle);
+ *   - overflow members: each distinct one uploaded once per cycle from pinned
+ *     host memory into one of two device staging halves, alternating, by one
+ *     gather kernel per half on a copy stream (it reads the pinned rasters
+ *     through their device mapping), members ordered by the set of requests
+ *     that toggle them so that each request's members lie in few runs; each
+ *     half is followed by one engine submit for all requests' members in it
+ *     (the paper's dual-buffer upload, Section 4, shared by the requests of
+ *     the cycle);
  *   - one render launch for all admitted sessions.
+ * The overflow part must be pinned host memory (or device memory) whose
+ * device address is 16-byte aligned.
  * A request completes when its cycle's event has completed; pump reports
  * completed request ids.  Requests that arrive while cycles run are admitted
  * into the next cycle; cycles run back to back on the device, the copy stream

@@ -53,15 +53,6 @@ __device__ __forceinline__ void bitcount_add16(BitCounter &s, const uint32_t (&w
     }
 }
 
-// Count of pixel i (0..31).
-__device__ __forceinline__ uint32_t bitcount_get(const BitCounter &s, int i) {
-    uint32_t v = ((s.ones >> i) & 1u) | (((s.twos >> i) & 1u) << 1) | (((s.fours >> i) & 1u) << 2) |
-                 (((s.eights >> i) & 1u) << 3);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) v += ((s.hi[j] >> i) & 1u) << (4 + j);
-    return v;
-}
-
 // The 32 counts of a BitCounter as 16 words of two 16-bit counts (pixel 2i in
 // the low half of pairs[i], pixel 2i+1 in the high half).  Eight pixels at a
 // time, byte b of each of the eight bit-slices becomes row j of an 8 x 8 bit

@@ -85,8 +85,6 @@ cudaError_t launch_bounded_wait_selftest(uint64_t timeout_ns, unsigned long long
 // Returns 0 on success; a CUresult otherwise.  elem_bytes 1 (masks) or 4.
 int encode_tma_map(CUtensorMap *map, const RasterBatch &b, int width, int height, int elem_bytes,
                    int box_bytes);
-// Requirements of the TMA path for a batch (alignment of base and strides).
-bool tma_compatible(const RasterBatch &b);
 
 // Render: counts -> dense counts / bucket / rgba, or sums -> mean.
 struct Lut {

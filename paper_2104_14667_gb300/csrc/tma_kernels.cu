@@ -538,12 +538,6 @@ cudaError_t launch_bounded_wait_selftest(uint64_t timeout_ns, unsigned long long
     return cudaGetLastError();
 }
 
-bool tma_compatible(const RasterBatch &b) {
-    return (reinterpret_cast<uintptr_t>(b.base) % 16 == 0) && (b.row_pitch % 16 == 0) &&
-           (b.member_stride % 16 == 0) && b.row_pitch < (int64_t(1) << 40) &&
-           b.member_stride < (int64_t(1) << 40);
-}
-
 bool tma_box_supported(int box_bytes) {
     return box_bytes == 64 || box_bytes == 128 || box_bytes == 256;
 }

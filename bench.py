@@ -488,7 +488,7 @@ def run_ours(args):
     clocks = sampler.stop() if sampler else None
 
     cpu = cpu_all = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:   # the oracle baseline: rank 0 at N = 1 only
         rate, done, spent = cpu_oracle_rate(ens, N, args.cpu_seconds)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{done} of {N} members of the {W}x{H} workload ({spent:.1f} s, one thread)"}

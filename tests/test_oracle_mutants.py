@@ -56,6 +56,7 @@ PINS = [
     pins.test_mean_depth_add_then_remove,
     pins.test_histogram_counts_every_pixel_once,
     pins.test_histogram_closed_forms,
+    pins.test_brute_force_on_random_8x8_inputs,
 ]
 
 

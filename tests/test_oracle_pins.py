@@ -222,3 +222,27 @@ def test_histogram_closed_forms():
     half.add(np.concatenate([m, np.ones((1, h, w), np.uint8)]))     # counts 1 or 2 of N = 2
     hist = half.render()["histogram"]
     assert hist[255] == int(m.sum()) and hist[127] == h * w - int(m.sum())
+
+
+def test_brute_force_on_random_8x8_inputs():
+    # 10^4 random 8x8 ensembles of 1..12 members with arbitrary byte values
+    # (about half of them zero): counts by walking every member and pixel,
+    # classes by Python integers
+    rng = np.random.default_rng(12)
+    for case in range(10_000):
+        n = int(rng.integers(1, 13))
+        m = (rng.integers(0, 256, (n, 8, 8)) * rng.integers(0, 2, (n, 8, 8))).astype(np.uint8)
+        got = oracle.count(m)
+        if case < 300:
+            want = np.zeros((8, 8), np.int64)
+            for k in range(n):
+                for y in range(8):
+                    for x in range(8):
+                        want[y, x] += 1 if m[k, y, x] else 0
+            b = oracle.bucket(got, n)
+            for y in range(8):
+                for x in range(8):
+                    assert b[y, x] == (255 * int(want[y, x])) // n
+        else:
+            want = np.count_nonzero(m, axis=0)
+        np.testing.assert_array_equal(got, want)

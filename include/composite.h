@@ -60,7 +60,8 @@ typedef enum composite_status {
     CPT_EINVAL = -1,      /* bad argument; the context is unchanged            */
     CPT_ENOMEM = -2,      /* device, pinned or host allocation failed          */
     CPT_ECUDA = -3,       /* CUDA runtime/driver error (message in last_error) */
-    CPT_ESTATE = -4,      /* context poisoned by an earlier underflow          */
+    CPT_ESTATE = -4,      /* context poisoned by an earlier underflow or by an
+                             add/remove that failed part-way                   */
     CPT_EUNDERFLOW = -5,  /* a remove took away a member that was never added  */
     CPT_ETIMEOUT = -6     /* a bounded wait (host or device) ran out           */
 } composite_status;
@@ -155,9 +156,16 @@ int composite_clear(composite_ctx *ctx);
  * buffer slot i mod k, accumulate, advance).
  * member_stride_bytes >= row_pitch_bytes * height; row_pitch_bytes >= the
  * row's bytes (width x element size, or ceil(width / 8) for bit-packed
- * masks); float32 rasters need 4-byte aligned pointer, pitch and stride.  n_members == 0 is a no-op.  Errors: CPT_EINVAL (NULL members
- * with n > 0, bad strides, N would exceed 65535 with count_bits 16),
- * CPT_ESTATE, CPT_ECUDA, CPT_ETIMEOUT. */
+ * masks); float32 rasters need 4-byte aligned pointer, pitch and stride.
+ * n_members == 0 is a no-op.  Errors: CPT_EINVAL (NULL members with n > 0,
+ * bad strides, N would exceed 65535 with count_bits 16; nothing changed),
+ * CPT_ESTATE, CPT_ECUDA, CPT_ENOMEM, CPT_ETIMEOUT.
+ * A call that fails after the work of its first chunk was queued (a CUDA
+ * error, a ring wait that ran out) leaves the composite holding an unknown
+ * part of its rasters while N stays that of the call before: the context is
+ * then poisoned -- add, remove and render return CPT_ESTATE -- until
+ * composite_clear or composite_load_counts.  A failure before any chunk
+ * leaves the context unchanged. */
 int composite_add_members(composite_ctx *ctx, const void *members, int32_t n_members,
                           int64_t member_stride_bytes, int32_t row_pitch_bytes);
 

@@ -101,7 +101,8 @@ int composite_engine_add_plane_bits(composite_engine *eng, int32_t width, int32_
 /* Frees a plane after the engine's queued work; its id is not reused. */
 int composite_engine_free_plane(composite_engine *eng, int32_t plane);
 
-/* Queues a clear of the plane (counts 0, N = 0, underflow state cleared). */
+/* Queues a clear of the plane (counts 0, N = 0, underflow state and a
+ * failed submit's mark cleared). */
 int composite_engine_clear(composite_engine *eng, int32_t plane);
 
 /* Queues every op in one persistent accumulate launch.  Validates all ops on
@@ -109,7 +110,12 @@ int composite_engine_clear(composite_engine *eng, int32_t plane);
  * sign not +-1, N of a plane would go negative or above its count type's
  * maximum (2^32-1, or 65535 for a 16-bit plane), bad strides).
  * A pixel count that would go below zero raises the plane's underflow state
- * (reported by composite_engine_sync). */
+ * (reported by composite_engine_sync).
+ * A failure before the launch (descriptor upload) leaves every plane and N
+ * as they were.  A failure of the launch itself (CPT_ECUDA) marks every plane
+ * of the submit as failed: they may hold part of the ops, so submits and
+ * renders naming them return CPT_ESTATE until composite_engine_clear (or a
+ * captured graph that refolds them). */
 int composite_engine_submit(composite_engine *eng, const composite_op *ops, int32_t n_ops);
 
 /* Queues the render of every listed plane in one persistent launch.

@@ -115,7 +115,12 @@ int composite_server_request(composite_server *srv, int32_t session, const int32
 
 /* Makes progress without blocking: collects completed cycles (their request
  * ids go to `completed`, up to `capacity`; *n_completed = how many were
- * written) and queues new cycles for admissible requests. */
+ * written) and queues new cycles for admissible requests.
+ * If a cycle fails after admission (an engine error, a refused upload), its
+ * sessions may hold part of its work: every request of those sessions in the
+ * cycle or still queued is dropped (it never completes), the error names the
+ * sessions, and further requests on them return CPT_ESTATE until they are
+ * closed.  Other sessions are unaffected. */
 int composite_server_pump(composite_server *srv, int64_t *completed, int32_t capacity, int32_t *n_completed);
 
 /* Pumps until nothing is queued or in flight (bounded by wait_timeout_ms per

@@ -75,6 +75,8 @@ struct composite_ctx {
     int *h_flags = nullptr;    // pinned copy of the flags
     int64_t n_members = 0;
     bool poisoned = false;
+    std::string poison_reason;   // why the context refuses work until a clear
+    int64_t call_chunks = 0;     // chunks of the current add/remove queued so far
     int device = 0;
     DeviceCaps caps{};
     cudaStream_t compute = nullptr, copy = nullptr;
@@ -167,6 +169,27 @@ int trace_open(composite_ctx *ctx, int kind, cudaStream_t s) {
 int trace_close(composite_ctx *ctx, cudaStream_t s) {
     if (!ctx->cfg.trace) return CPT_OK;
     CK(ctx, cudaEventRecord(ctx->trace.back().b, s));
+    return CPT_OK;
+}
+
+// Poisons the context: every call but clear, load_counts, sync, trace_read
+// and end returns CPT_ESTATE until composite_clear or composite_load_counts.
+void poison(composite_ctx *ctx, const char *reason) {
+    ctx->poisoned = true;
+    ctx->poison_reason = reason;
+}
+
+int refuse_poisoned(composite_ctx *ctx) {
+    return fail(ctx, CPT_ESTATE, "context poisoned: %s; clear it", ctx->poison_reason.c_str());
+}
+
+// Called before the work of each chunk of an add or remove is queued.  From
+// then on a failure leaves part of the call's rasters folded in, which
+// apply() turns into a poisoned context.
+int begin_chunk(composite_ctx *ctx) {
+    if (cpt::fault_injected_value("chunk_fail") == ctx->call_chunks)
+        return fail(ctx, CPT_ECUDA, "upload of chunk %lld refused (injected)", (long long)ctx->call_chunks);
+    ++ctx->call_chunks;
     return CPT_OK;
 }
 
@@ -418,9 +441,11 @@ int run_staged(composite_ctx *ctx, const uint8_t *src, int n, int64_t stride, in
     for (int m0 = 0; m0 < n; m0 += C) {
         const cpt::TraceRange chunk_range("composite chunk");
         const int c = n - m0 < C ? n - m0 : C;
+        int rc = begin_chunk(ctx);
+        if (rc) return rc;
         Slot &s = next_slot(ctx);
         CK(ctx, cudaStreamWaitEvent(ctx->copy, s.consumed, 0));
-        int rc = trace_open(ctx, kTraceUpload, ctx->copy);
+        rc = trace_open(ctx, kTraceUpload, ctx->copy);
         if (rc) return rc;
         rc = upload(ctx, s.stage, src + (int64_t)m0 * stride, c, stride, pitch);
         if (rc) return rc;
@@ -442,9 +467,11 @@ int run_texture_from_device(composite_ctx *ctx, const uint8_t *src, int n, int64
     for (int m0 = 0; m0 < n; m0 += C) {
         const cpt::TraceRange chunk_range("composite chunk");
         const int c = n - m0 < C ? n - m0 : C;
+        int rc = begin_chunk(ctx);
+        if (rc) return rc;
         Slot &s = next_slot(ctx);
         CK(ctx, cudaStreamWaitEvent(ctx->copy, s.consumed, 0));
-        int rc = convert_to_array(ctx, s, src + (int64_t)m0 * stride, pitch, c, ctx->copy);
+        rc = convert_to_array(ctx, s, src + (int64_t)m0 * stride, pitch, c, ctx->copy);
         if (rc) return rc;
         CK(ctx, cudaEventRecord(s.ready, ctx->copy));
         CK(ctx, cudaStreamWaitEvent(ctx->compute, s.ready, 0));
@@ -504,9 +531,11 @@ int run_ring(composite_ctx *ctx, const uint8_t *src, int n, int64_t stride, int6
     for (int m0 = 0; m0 < n; m0 += C) {
         const cpt::TraceRange chunk_range("composite chunk");
         const int c = n - m0 < C ? n - m0 : C;
+        int rc = begin_chunk(ctx);
+        if (rc) return rc;
         Slot &s = next_slot(ctx);
         if (s.ring_used) {
-            int rc = wait_event(ctx, s.ring_free);
+            rc = wait_event(ctx, s.ring_free);
             if (rc) return rc;
         }
         // the chunk's rasters into the ring slot: pieces of about kIngestPiece
@@ -535,7 +564,7 @@ int run_ring(composite_ctx *ctx, const uint8_t *src, int n, int64_t stride, int6
             for (int p = 0; p < n_pieces; ++p) piece(p);
         }
         CK(ctx, cudaStreamWaitEvent(ctx->copy, s.consumed, 0));
-        int rc = trace_open(ctx, kTraceUpload, ctx->copy);
+        rc = trace_open(ctx, kTraceUpload, ctx->copy);
         if (rc) return rc;
         CK(ctx, cudaMemcpyAsync(s.stage, s.ring, (size_t)c * ctx->member_bytes, cudaMemcpyHostToDevice, ctx->copy));
         rc = trace_close(ctx, ctx->copy);
@@ -555,7 +584,7 @@ int apply(composite_ctx *ctx, const void *members, int32_t n, int64_t stride, in
     const cpt::TraceRange range(sign > 0 ? "composite_add_members" : "composite_remove_members");
     if (!ctx) return CPT_EINVAL;
     ctx->err.clear();
-    if (ctx->poisoned) return fail(ctx, CPT_ESTATE, "context poisoned by an earlier underflow; clear it");
+    if (ctx->poisoned) return refuse_poisoned(ctx);
     if (n < 0) return fail(ctx, CPT_EINVAL, "n_members %d < 0", n);
     if (n == 0) return CPT_OK;
     if (!members) return fail(ctx, CPT_EINVAL, "members is NULL");
@@ -574,6 +603,7 @@ int apply(composite_ctx *ctx, const void *members, int32_t n, int64_t stride, in
 
     const uint8_t *src = static_cast<const uint8_t *>(members);
     const MemKind kind = memory_kind(members);
+    ctx->call_chunks = 0;
     // uploads on the copy stream start after the caller's earlier work on the
     // compute stream (which may have produced the rasters)
     CK(ctx, cudaEventRecord(ctx->caller_ready, ctx->compute));
@@ -587,7 +617,8 @@ int apply(composite_ctx *ctx, const void *members, int32_t n, int64_t stride, in
                         : run_staged(ctx, src, n, stride, pitch, sign);
         } else if (aligned) {
             RasterBatch b{members, stride, pitch, n};
-            rc = accumulate(ctx, b, sign);
+            rc = begin_chunk(ctx);
+            if (!rc) rc = accumulate(ctx, b, sign);
         } else {
             rc = run_staged(ctx, src, n, stride, pitch, sign);
         }
@@ -598,14 +629,21 @@ int apply(composite_ctx *ctx, const void *members, int32_t n, int64_t stride, in
             void *dptr = nullptr;
             CK(ctx, cudaHostGetDevicePointer(&dptr, const_cast<void *>(members), 0));
             RasterBatch b{dptr, stride, pitch, n};
-            rc = accumulate(ctx, b, sign, true);
+            rc = begin_chunk(ctx);
+            if (!rc) rc = accumulate(ctx, b, sign, true);
         } else {
             rc = run_staged(ctx, src, n, stride, pitch, sign);
         }
     } else {
         rc = run_ring(ctx, src, n, stride, pitch, sign);
     }
-    if (rc) return rc;
+    if (rc) {
+        // Chunks queued before the failure still fold into the composite, so
+        // it holds an unknown part of this call's rasters while N is that of
+        // the call before: refuse further work until a clear.
+        if (ctx->call_chunks > 0) poison(ctx, "an add or remove failed part-way; the composite holds part of its rasters");
+        return rc;
+    }
     ctx->n_members = after;
     return CPT_OK;
 }
@@ -614,7 +652,7 @@ int apply(composite_ctx *ctx, const void *members, int32_t n, int64_t stride, in
 int check_flags(composite_ctx *ctx) {
     if (ctx->h_flags[cpt::kFlagTimeout]) return fail(ctx, CPT_ETIMEOUT, "a device-side wait ran out");
     if (ctx->h_flags[cpt::kFlagUnderflow]) {
-        ctx->poisoned = true;
+        poison(ctx, "a remove took away a member that was never added");
         return fail(ctx, CPT_EUNDERFLOW, "a remove took away a member that was never added");
     }
     return CPT_OK;
@@ -632,6 +670,26 @@ int wait_all(composite_ctx *ctx) {
 }  // namespace
 
 void cpt::set_thread_error(const char *message) { g_begin_error = message; }
+
+int64_t cpt::fault_injected_value(const char *site) {
+    const char *v = std::getenv("CPT_FAULT_INJECT");
+    if (!v || !*v) return -1;
+    const size_t n = strlen(site);
+    for (const char *p = v;;) {
+        const char *q = strchr(p, ',');
+        const size_t len = q ? (size_t)(q - p) : strlen(p);
+        if (len > n + 1 && strncmp(p, site, n) == 0 && p[n] == '=') {
+            int64_t k = 0;
+            for (size_t i = n + 1; i < len; ++i) {
+                if (p[i] < '0' || p[i] > '9') return -1;
+                k = k * 10 + (p[i] - '0');
+            }
+            return k;
+        }
+        if (!q) return -1;
+        p = q + 1;
+    }
+}
 
 bool cpt::fault_injected(const char *site) {
     const char *v = std::getenv("CPT_FAULT_INJECT");
@@ -807,7 +865,7 @@ int render(composite_ctx *ctx, void *counts_out, uint8_t *bucket_out, uint8_t *r
     const cpt::TraceRange range("composite_render");
     if (!ctx) return CPT_EINVAL;
     ctx->err.clear();
-    if (ctx->poisoned) return fail(ctx, CPT_ESTATE, "context poisoned by an earlier underflow; clear it");
+    if (ctx->poisoned) return refuse_poisoned(ctx);
     const bool count = ctx->cfg.mode == CPT_MODE_COUNT;
     if (count && mean_out) return fail(ctx, CPT_EINVAL, "mean_out needs CPT_MODE_MEAN_DEPTH");
     if (!count && (counts_out || bucket_out || rgba_out || hist_out))

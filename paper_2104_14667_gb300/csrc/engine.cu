@@ -420,6 +420,7 @@ struct PlaneRec {
     int32_t count_bits = 32;
     int64_t n = 0;
     bool alive = false;
+    bool poisoned = false;       // a submit failed after its launch may have begun
 
     size_t bytes() const { return (size_t)pitch_px * height * (count_bits / 8); }
     int64_t max_members() const { return count_bits == 16 ? 0xFFFFll : 0xFFFFFFFFll; }
@@ -645,9 +646,15 @@ int plan_render(composite_engine *e, const composite_render_op *ops, int32_t n_o
         if ((reinterpret_cast<uintptr_t>(o.counts_out) % (p.count_bits / 8)) || (reinterpret_cast<uintptr_t>(o.rgba_out) % 4))
             return efail(e, CPT_EINVAL, "render %d: counts_out must be aligned to its count type, rgba_out to 4 bytes", i);
         int64_t n = p.n;
+        bool refolded = false;   // a captured graph clears and refolds the plane first
         if (n_override)
             for (const auto &pn : *n_override)
-                if (pn.first == o.plane) n = pn.second;
+                if (pn.first == o.plane) {
+                    n = pn.second;
+                    refolded = true;
+                }
+        if (p.poisoned && !refolded)
+            return efail(e, CPT_ESTATE, "render %d: plane %d: an earlier submit failed part-way; clear it", i, o.plane);
         RenderDesc d{};
         d.plane = p.data;
         d.counts_out = o.counts_out;
@@ -715,6 +722,7 @@ int clear_plane(composite_engine *e, int32_t p) {
     ECK(e, cudaMemsetAsync(r.data, 0, r.bytes(), e->stream));
     ECK(e, cudaMemsetAsync(e->d_flags + p, 0, sizeof(int), e->stream));
     r.n = 0;
+    r.poisoned = false;
     return CPT_OK;
 }
 
@@ -725,13 +733,24 @@ int submit_internal(composite_engine *e, const composite_op *ops, int32_t n_ops)
     int64_t items = 0;
     int rc = plan_ops(e, ops, n_ops, &descs, &items, &n_after, false);
     if (rc) return rc;
+    for (const auto &pn : n_after)
+        if (e->planes[pn.first].poisoned)
+            return efail(e, CPT_ESTATE, "plane %d: an earlier submit failed part-way; clear it", pn.first);
     if (items > 0) {
         Upload *u = nullptr;
         rc = upload(e, e->up_ops, &e->up_i, descs.data(), descs.size() * sizeof(OpDesc), &u);
-        if (rc) return rc;
+        if (rc) return rc;   // nothing launched: every plane is as before
+        if (cpt::fault_injected("engine_submit")) return efail(e, CPT_ECUDA, "submit refused before its launch (injected)");
         rc = launch_accumulate(e, u->d, (int)descs.size(), items, e->d_counter);
-        if (rc) return rc;
+        if (rc) {
+            // the launch may have begun: the planes it touches hold an unknown
+            // part of the ops until they are cleared
+            for (const auto &pn : n_after) e->planes[pn.first].poisoned = true;
+            return rc;
+        }
+        for (const auto &pn : n_after) e->planes[pn.first].n = pn.second;
         ECK(e, cudaEventRecord(u->consumed, e->stream));
+        return CPT_OK;
     }
     for (const auto &pn : n_after) e->planes[pn.first].n = pn.second;
     return CPT_OK;
@@ -1018,7 +1037,11 @@ int composite_engine_replay(composite_engine *e) try {
     for (const int32_t p : e->graph_planes)
         if (!plane_ok(e, p)) return efail(e, CPT_ESTATE, "a captured plane was freed");
     ECK(e, cudaGraphLaunch(e->graph_exec, e->stream));
-    for (const auto &pn : e->graph_n) e->planes[pn.first].n = pn.second;
+    // the graph clears every plane it folds into before folding
+    for (const auto &pn : e->graph_n) {
+        e->planes[pn.first].n = pn.second;
+        e->planes[pn.first].poisoned = false;
+    }
     return CPT_OK;
 } catch (...) {
     return cpt::abi_exception_status();

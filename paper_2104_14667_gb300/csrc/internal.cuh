@@ -106,8 +106,16 @@ void set_thread_error(const char *message);
 // CPT_FAULT_INJECT holds a comma-separated list of sites -- staging_alloc,
 // pinned_ring, ingest_threads, engine_plane, server_stage -- and a listed site
 // behaves as if its host-side request (a device or pinned allocation, the
-// ingest threads) had been refused.  Nothing on the device is affected.
+// ingest threads) had been refused; engine_submit makes every engine submit
+// fail after its descriptors are uploaded and before its launch.  Nothing on
+// the device is affected.
 bool fault_injected(const char *site);
+// Indexed sites in the same list, written "site=K": returns K when the site
+// is listed, -1 otherwise.  chunk_fail=K makes chunk K (from 0) of every add
+// or remove fail as if its upload had been refused, after chunks 0..K-1 were
+// queued; server_chunk_fail=K does the same to overflow chunk K of every
+// server cycle.  Each fails on the host, before that chunk's work is queued.
+int64_t fault_injected_value(const char *site);
 
 // NVTX range around a host-side phase (a call, a pipeline chunk), for
 // timeline profilers; a no-op call when no profiler is attached.

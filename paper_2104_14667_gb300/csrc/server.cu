@@ -28,6 +28,7 @@ struct Session {
     int64_t n_view = 0;
     int pending = 0;               // queued + in flight
     bool busy = false;             // a request in flight
+    bool failed = false;           // a cycle failed part-way over this session's plane
 };
 
 struct Request {
@@ -176,6 +177,32 @@ int reap(composite_server *s, int64_t *completed, int32_t capacity, int32_t *n_c
     return CPT_OK;
 }
 
+int build_cycle(composite_server *s, Cycle *cyc, std::vector<Request> &batch);
+
+// A cycle that failed after admission: its sessions' planes hold an unknown
+// part of its work, so the sessions are marked failed (further requests get
+// CPT_ESTATE until they are closed), and their requests -- the admitted ones
+// and any queued behind them -- are dropped: they never complete.
+void abandon_cycle(composite_server *s, const std::vector<Request> &batch) {
+    for (const Request &q : batch) {
+        Session &ss = s->sessions[q.session];
+        ss.failed = true;
+        ss.busy = false;
+        --ss.pending;
+        --s->stats.queued;
+    }
+    for (auto it = s->queue.begin(); it != s->queue.end();) {
+        Session &ss = s->sessions[it->session];
+        if (!ss.failed) {
+            ++it;
+            continue;
+        }
+        --ss.pending;
+        --s->stats.queued;
+        it = s->queue.erase(it);
+    }
+}
+
 // Builds and queues one cycle from the admissible queued requests.
 int launch_cycle(composite_server *s, bool *launched) {
     const cpt::TraceRange range("composite_server cycle");
@@ -202,7 +229,23 @@ int launch_cycle(composite_server *s, bool *launched) {
         it = s->queue.erase(it);
     }
     if (batch.empty()) return CPT_OK;
+    const int rc = build_cycle(s, cyc, batch);
+    if (rc) {
+        std::string sessions;
+        for (const Request &q : batch) sessions += (sessions.empty() ? "" : ", ") + std::to_string(q.session);
+        const std::string why = s->err;
+        abandon_cycle(s, batch);
+        return sfail(s, rc, "%s; the requests of sessions %s were dropped and the sessions must be closed",
+                     why.c_str(), sessions.c_str());
+    }
+    *launched = true;
+    return CPT_OK;
+}
 
+// The body of a cycle: session updates, index lists, the engine submits for
+// resident and overflow members, the render.  On error the caller abandons
+// the cycle.
+int build_cycle(composite_server *s, Cycle *cyc, std::vector<Request> &batch) {
     const int32_t R = s->cfg.n_resident;
     const int words = (s->n_total + 63) / 64;
     std::vector<std::vector<int32_t>> res_add(batch.size()), res_rem(batch.size());
@@ -341,7 +384,10 @@ int launch_cycle(composite_server *s, bool *launched) {
     cursor = group_start;
     group_start.push_back(ovf.size());
     const int half = s->cfg.staging_members;
+    const int64_t inject_at = cpt::fault_injected_value("server_chunk_fail");
     for (size_t c0 = 0; c0 < distinct.size(); c0 += half) {
+        if (inject_at >= 0 && (int64_t)(c0 / half) == inject_at)
+            return sfail(s, CPT_ECUDA, "upload of overflow chunk %lld refused (injected)", (long long)inject_at);
         const size_t c1 = std::min(distinct.size(), c0 + (size_t)half);
         const int h = s->stage_half;
         s->stage_half ^= 1;
@@ -407,7 +453,6 @@ int launch_cycle(composite_server *s, bool *launched) {
     s->stats.queued -= (int64_t)batch.size();
     ++s->stats.cycles;
     cyc->in_flight = true;
-    *launched = true;
     return CPT_OK;
 }
 
@@ -604,6 +649,8 @@ int composite_server_request(composite_server *s, int32_t session, const int32_t
     s->err.clear();
     if (session < 0 || session >= (int32_t)s->sessions.size() || !s->sessions[session].open)
         return sfail(s, CPT_EINVAL, "no session %d", session);
+    if (s->sessions[session].failed)
+        return sfail(s, CPT_ESTATE, "session %d lost a cycle to an error; close it and open a new one", session);
     if (n < 0 || (n > 0 && !toggle)) return sfail(s, CPT_EINVAL, "bad toggle list");
     for (int32_t i = 0; i < n; ++i)
         if (toggle[i] < 0 || toggle[i] >= s->n_total)

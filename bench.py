@@ -567,6 +567,21 @@ def identity_rows_exact(comp, terrain, levels, rows=(0, 1, -2, -1)) -> bool:
     return bool(np.array_equal(got[rows], ident))
 
 
+def depth_identity_max_error(comp, terrain, levels, rows=(0, 1, -2, -1)) -> float:
+    """Renders the mean depth and returns the largest deviation of sampled rows
+    from its closed form: every depth is max(w_m - terrain(p), 0), so the sum
+    over the members is the sum of the levels above terrain(p) minus their
+    number times terrain(p) (FP64, levels sorted once)."""
+    got = comp.render_host()["mean"].astype(np.float64)
+    lv = np.sort(np.asarray(levels, np.float32)).astype(np.float64)
+    suffix = np.append(np.cumsum(lv[::-1])[::-1], 0.0)
+    rows = sorted({r % terrain.shape[0] for r in rows})
+    t = terrain[rows].astype(np.float64)
+    i = np.searchsorted(lv, t.ravel(), side="right").reshape(t.shape)
+    ident = (suffix[i] - (len(lv) - i) * t) / len(lv)
+    return float(np.abs(got[rows] - ident).max())
+
+
 def _timed(torch, stream, fn, steps: int, warmup: int) -> float:
     """Average ms of fn() over `steps` runs (CUDA events on `stream`)."""
     for _ in range(warmup):
@@ -618,7 +633,11 @@ def sweep_readpath(args, torch, binding, device, stream):
             with binding.Composite(W, H, trace=True, **cfg) as comp:
                 comp.add(data)
                 rec = comp.trace()
-                exact = identity_rows_exact(comp, ens.terrain, ens.levels) if mode == "count" else None
+                if mode == "count":
+                    exact, depth_err = identity_rows_exact(comp, ens.terrain, ens.levels), None
+                else:
+                    depth_err = depth_identity_max_error(comp, ens.terrain, ens.levels)
+                    exact = depth_err <= 1e-5 * N
             launches = int(sum(1 for k, _, _ in rec if int(k) == 2))
             kernel_ms = _busy(rec, (2,))
             convert_ms = _busy(rec, (1,))
@@ -633,7 +652,8 @@ def sweep_readpath(args, torch, binding, device, stream):
                     "kernel_alg_gbs": kernel_bytes / (kernel_ms * 1e-3) / 1e9,
                     "kernel_frac_of_hbm": kernel_bytes / (kernel_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
                     "conversion_gbs": (N * P * elem / (convert_ms * 1e-3) / 1e9) if convert_ms else None,
-                    "exact_sampled_rows": exact}
+                    "exact_sampled_rows": exact, "depth_max_abs_error_sampled_rows": depth_err,
+                    "depth_tolerance": 1e-5 * N if mode != "count" else None}
             print(json.dumps(line), flush=True)
         del data
         torch.cuda.empty_cache()

@@ -44,10 +44,11 @@ def check(got, ident, sample):
     np.testing.assert_array_equal(got["bucket"], oracle.bucket(ident, N))
 
 
-@pytest.mark.parametrize("path", ["linear", "tma"])
+@pytest.mark.parametrize("path", ["linear", "tma", "texture"])
 def test_device_resident_one_launch(ensemble, path):
     # the bench's device-resident pass: clear, one accumulate over all 1024
-    # members read in place, render
+    # members read in place, render (the texture path converts chunks of 16
+    # members into its layered arrays first)
     _, dev, ident, sample = ensemble
     with binding.Composite(W, H, read_path=path) as comp:
         comp.add(dev)

@@ -16,7 +16,8 @@ mathematics of the problem:
   by the inequality that defines a floor, b*N <= 255c < (b+1)*N;
 * the colour map at its ends (white, saturated blue) and its monotone
   saturation;
-* the mean depth against exact rational arithmetic.
+* the mean depth against exact rational arithmetic, and against its closed
+  form over one ensemble (a sum of the highest water levels minus k * t).
 """
 import itertools
 from fractions import Fraction
@@ -26,6 +27,7 @@ import pytest
 
 import oracle
 import synth
+from tests.identities import depth_rounding_bound, mean_depth_identity
 
 
 def nested_threshold_counts(ens: synth.Ensemble) -> np.ndarray:
@@ -177,6 +179,17 @@ def test_mean_depth_against_exact_rationals():
         for x in range(6):
             exact = sum(Fraction(float(v)) for v in d[:, y, x]) / 9
             assert abs(Fraction(got[y, x]) - exact) <= Fraction(1, 2 ** 50) * (1 + abs(exact))
+
+
+@pytest.mark.parametrize("seed,w,h,n", [(6, 64, 48, 9), (12, 131, 77, 40)])
+def test_mean_depth_matches_threshold_closed_form(seed, w, h, n):
+    # an independent algorithm: the depths of one ensemble are w_m - t where
+    # positive, so their sum is a sum of the highest levels minus k * t
+    ens = synth.ensemble(seed, w, h, n)
+    got = oracle.mean_depth(synth.depths(ens))
+    ref = mean_depth_identity(ens.terrain, ens.levels)
+    assert np.abs(got - ref).max() <= depth_rounding_bound(ens.terrain, ens.levels)
+    assert np.abs(ref).max() > 0.01
 
 
 def test_mean_depth_special_cases():

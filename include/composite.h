@@ -268,10 +268,15 @@ int composite_selftest_bounded_wait(int64_t timeout_us, int32_t *gave_up_out, in
  * through its own pool and forbids libraries from allocating.
  * Computes, over the n_members device-resident uint8 masks, uint32 counts,
  * overlap classes and colours exactly as composite_begin + add_members +
- * render would (same kernels), writing every non-NULL output (dense
- * row-major, device memory, counts_out and rgba_out 4-byte aligned).
- * members, row_pitch_bytes and member_stride_bytes must be 16-byte aligned
- * and in device memory; lut_rgba is a host table or NULL for the default.
+ * render would (same kernels), writing every non-NULL output: dense
+ * row-major width x height, counts_out uint32 and rgba_out 4 x uint8 per
+ * pixel (both 4-byte aligned), bucket_out uint8 per pixel, each in device
+ * memory of the current device and large enough (the library cannot check
+ * sizes).  members, row_pitch_bytes and member_stride_bytes must be 16-byte
+ * aligned and members in device memory of the current device (or managed
+ * memory); host memory or another GPU's memory is rejected with CPT_EINVAL
+ * before anything is queued.  lut_rgba is a host table or NULL for the
+ * default.
  * The work is queued on cuda_stream (a cudaStream_t, NULL = legacy default
  * stream) and the call returns without waiting.
  * Scratch: a file-scope __device__ array of CPT_ONESHOT_MAX_PIXELS uint32
@@ -282,8 +287,9 @@ int composite_selftest_bounded_wait(int64_t timeout_us, int32_t *gave_up_out, in
  * calls whose work overlaps on the GPU (different streams, or host threads)
  * race and must be serialised by the caller.
  * Errors: CPT_EINVAL (empty raster, raster larger than the scratch,
- * unaligned or non-device members, bad strides), CPT_ECUDA; the message is
- * in composite_last_error(NULL). */
+ * unaligned members or outputs, members or outputs not in the current
+ * device's memory, bad strides), CPT_ECUDA; the message is in
+ * composite_last_error(NULL). */
 int composite_oneshot_static(const void *members, int32_t n_members, int64_t member_stride_bytes,
                              int32_t row_pitch_bytes, int32_t width, int32_t height,
                              uint32_t *counts_out, uint8_t *bucket_out, uint8_t *rgba_out,

@@ -274,12 +274,37 @@ def composite_last_error(ctx=None) -> str:
     return msg.decode() if msg else ""
 
 
+def _check_static_outputs(members, h, w, counts_out, bucket_out, rgba_out):
+    """The allocation-free entry point writes its outputs straight from the
+    GPU: they must be CUDA tensors of exactly the raster's shape and type, on
+    the members' device (the C side checks memory kinds, not sizes)."""
+    import torch
+    want = {"counts_out": (counts_out, (h, w), (torch.int32,)),
+            "bucket_out": (bucket_out, (h, w), (torch.uint8,)),
+            "rgba_out": (rgba_out, (h, w, 4), (torch.uint8,))}
+    if hasattr(torch, "uint32"):
+        want["counts_out"] = (counts_out, (h, w), (torch.int32, torch.uint32))
+    dev = members.device if isinstance(members, torch.Tensor) else None
+    for name, (t, shape, dtypes) in want.items():
+        if t is None:
+            continue
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if tuple(t.shape) != shape or t.dtype not in dtypes or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous {shape} tensor of {dtypes[0]}")
+        if dev is not None and t.device != dev:
+            raise ValueError(f"{name} must be on the members' device {dev}")
+
+
 def composite_oneshot_static(members, counts_out=None, bucket_out=None, rgba_out=None, lut=None,
                              stream=None) -> None:
     """One-shot composite of device-resident masks with no allocation in the
     library (scratch in a fixed device array); queued on ``stream``."""
     lib = load()
-    ptr, n, h, w, stride, pitch, _, _ = _raster_view(members)
+    ptr, n, h, w, stride, pitch, dtype, _ = _raster_view(members)
+    if dtype is not np.uint8:
+        raise ValueError("composite_oneshot_static takes uint8 masks")
+    _check_static_outputs(members, h, w, counts_out, bucket_out, rgba_out)
     lut_arr = None
     if lut is not None:
         lut_arr = np.ascontiguousarray(np.asarray(lut, dtype=np.uint8).reshape(256, 4))

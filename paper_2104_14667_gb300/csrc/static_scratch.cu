@@ -32,6 +32,7 @@ struct DeviceScratch {
     uint32_t *plane = nullptr;
     int *flags = nullptr;
     int num_sms = 0;
+    int device = 0;
 };
 
 std::mutex g_mutex;
@@ -40,6 +41,19 @@ DeviceScratch g_scratch[kMaxDevices];
 int reject(int code, const char *message) {
     cpt::set_thread_error(message);
     return code;
+}
+
+// True when p is device (or managed) memory the current device can address
+// as its own: kernels here read and write these pointers directly, so host
+// memory or another GPU's memory must be turned away before any launch.
+bool on_current_device(const void *p, int dev) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 // Device addresses of the static scratch on the current device.
@@ -60,6 +74,7 @@ int resolve(DeviceScratch *out) {
         if (e != cudaSuccess) return reject(CPT_ECUDA, cudaGetErrorString(e));
         s.plane = static_cast<uint32_t *>(plane);
         s.flags = static_cast<int *>(flags);
+        s.device = dev;
         s.ready = true;
     }
     *out = s;
@@ -85,12 +100,6 @@ extern "C" int composite_oneshot_static(const void *members, int32_t n_members,
             return reject(CPT_EINVAL, "row pitch or member stride too small");
         if ((reinterpret_cast<uintptr_t>(members) % 16) || (row_pitch_bytes % 16) || (member_stride_bytes % 16))
             return reject(CPT_EINVAL, "members, row pitch and member stride must be 16-byte aligned");
-        cudaPointerAttributes a;
-        if (cudaPointerGetAttributes(&a, members) != cudaSuccess ||
-            (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)) {
-            cudaGetLastError();
-            return reject(CPT_EINVAL, "members must be device memory");
-        }
     }
     if ((reinterpret_cast<uintptr_t>(counts_out) % 4) || (reinterpret_cast<uintptr_t>(rgba_out) % 4))
         return reject(CPT_EINVAL, "counts_out and rgba_out must be 4-byte aligned");
@@ -98,6 +107,12 @@ extern "C" int composite_oneshot_static(const void *members, int32_t n_members,
     DeviceScratch s;
     int rc = resolve(&s);
     if (rc) return rc;
+    if (n_members > 0 && !on_current_device(members, s.device))
+        return reject(CPT_EINVAL, "members must be device memory of the current device");
+    const void *outs[3] = {counts_out, bucket_out, rgba_out};
+    for (const void *o : outs)
+        if (o && !on_current_device(o, s.device))
+            return reject(CPT_EINVAL, "outputs must be device memory of the current device");
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
     cpt::Lut lut;
     for (int b = 0; b < 256; ++b) {

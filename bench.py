@@ -23,7 +23,6 @@ step a bounded sample of members) and prints its own line.
 from __future__ import annotations
 
 import argparse
-import hashlib
 import json
 import os
 import statistics
@@ -71,6 +70,8 @@ def parse_args():
     p.add_argument("--requests", type=int, default=200, help="serving: requests per offered rate")
     p.add_argument("--max-batch", type=int, default=64, help="serving: requests per cycle")
     p.add_argument("--poll-us", type=float, default=100.0, help="serving: host back-off between idle polls")
+    p.add_argument("--plain-arm", type=int, default=1,
+                   help="serving: 1 = also time the plain per-request pipeline (recompute with the plain calls)")
     p.add_argument("--engine-count-bits", type=int, choices=[16, 32], default=16,
                    help="batched: count width of the engine's planes")
     p.add_argument("--paths", nargs="+", choices=["linear", "texture", "tma"], default=["linear", "texture", "tma"],
@@ -180,31 +181,20 @@ def measured_peaks():
         return {"hbm_gbs": HBM_FALLBACK_GBS}, "fallback"
 
 
-def kernel_source_hash() -> str:
-    h = hashlib.sha256()
-    for name in ("count_kernels.cu", "device_common.cuh"):
-        with open(os.path.join(ROOT, "paper_2104_14667_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
-    return h.hexdigest()[:16]
-
-
 def profiled_traffic(workload_key: str):
-    """DRAM bytes per launch of the accumulation kernel from the committed ncu
-    summary, if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "count_linear_4096x4096x1024.md")
+    """DRAM bytes per launch of the accumulation kernel, from the JSON record
+    that paper_2104_14667_gb300.ncu_traffic wrote from an ncu capture; None
+    unless it was taken on the current kernel source and this workload."""
+    from paper_2104_14667_gb300 import ncu_traffic
+    path = os.path.join(ROOT, "profiles", f"dram_traffic_count_linear_{workload_key}.json")
     try:
-        text = open(path).read()
-    except OSError:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
         return None
-    src = cnt = None
-    for line in text.splitlines():
-        if line.startswith("kernel_source_sha256_16:"):
-            src = line.split(":", 1)[1].strip()
-        if line.startswith(f"dram_bytes_per_launch[{workload_key}]:"):
-            cnt = float(line.split(":", 1)[1].split()[0])
-    if src != kernel_source_hash() or cnt is None:
+    if rec.get("kernel_source_sha256_16") != ncu_traffic.kernel_source_hash() or rec.get("workload") != workload_key:
         return None
-    return cnt
+    return float(rec["dram_bytes_per_launch"])
 
 
 def make_ensemble(args, torch, device):
@@ -217,61 +207,86 @@ def make_ensemble(args, torch, device):
     return ens, dev
 
 
-def cpu_oracle_rate(ens, members: int, target_s: float, batch: int = 4):
-    """The oracle (plain C, one thread) over batches of members of the same
-    workload until about target_s seconds of CPU work; member-px/s."""
-    import oracle
+def _oracle_fill(ens, buf, ids, mode):
     import synth
+    if mode == "count":
+        synth.fill_masks(ens, buf, ids)
+    else:
+        buf[:] = synth.depths(ens, members=ids)
+
+
+def _oracle_apply(acc, buf, mode):
+    import oracle
+    if mode == "count":
+        oracle.count_apply(acc, buf, 1)
+    else:
+        oracle.depth_apply(acc, buf, 1)
+
+
+def _oracle_buffers(n, h, w, mode):
+    if mode == "count":
+        return np.empty((n, h, w), dtype=np.uint8), np.zeros((h, w), dtype=np.int64)
+    return np.empty((n, h, w), dtype=np.float32), np.zeros((h, w), dtype=np.float64)
+
+
+def cpu_oracle_rate(ens, members: int, target_s: float, batch: int = 4, mode: str = "count"):
+    """The oracle (plain C, one thread) over batches of members of the same
+    workload until about target_s seconds of CPU work; member-px/s.  mode
+    "count" folds uint8 masks into int64 counts, "mean_depth" float32 depths
+    into FP64 sums."""
     h, w = ens.height, ens.width
-    buf = np.empty((batch, h, w), dtype=np.uint8)
-    counts = np.zeros((h, w), dtype=np.int64)
+    buf, acc = _oracle_buffers(batch, h, w, mode)
     done, spent = 0, 0.0
-    while done == 0 or (spent < target_s and done < members):
-        b = min(batch, members - done)
-        synth.fill_masks(ens, buf[:b], range(done, done + b))
+    cycle = target_s > 0 and members < 64     # a small workload is passed over again until target_s
+    while done == 0 or (spent < target_s and (cycle or done < members)):
+        b = batch if cycle else min(batch, members - done)
+        _oracle_fill(ens, buf[:b], [(done + j) % members for j in range(b)], mode)
         t0 = time.perf_counter()
-        oracle.count_apply(counts, buf[:b], 1)
+        _oracle_apply(acc, buf[:b], mode)
         spent += time.perf_counter() - t0
         done += b
     return done * w * h / spent, done, spent
 
 
-def _oracle_worker(seed, width, height, members, first, target_s, barrier, out):
+def _oracle_worker(seed, width, height, members, first, target_s, barrier, out, mode="count"):
     # one process of the all-cores CPU baseline: members first, first + P, ...
-    import oracle
     import synth
     ens = synth.ensemble(seed, width, height, members)
     stride = out["procs"]
-    buf = np.empty((1, height, width), dtype=np.uint8)
-    counts = np.zeros((height, width), dtype=np.int64)
+    buf, acc = _oracle_buffers(1, height, width, mode)
     ids = list(range(first, members, stride)) or [first % members]
-    synth.fill_masks(ens, buf, ids[:1])
-    oracle.count_apply(counts, buf, 1)          # warm: library load, page faults
+    _oracle_fill(ens, buf, ids[:1], mode)
+    _oracle_apply(acc, buf, mode)               # warm: library load, page faults
     barrier.wait()
     done, spent, i = 0, 0.0, 0
     t_start = time.perf_counter()
     while time.perf_counter() - t_start < target_s:
-        synth.fill_masks(ens, buf, [ids[i % len(ids)]])
+        _oracle_fill(ens, buf, [ids[i % len(ids)]], mode)
         t0 = time.perf_counter()
-        oracle.count_apply(counts, buf, 1)
+        _oracle_apply(acc, buf, mode)
         spent += time.perf_counter() - t0
         done += 1
         i += 1
     out[first] = (done, spent, time.perf_counter() - t_start)
 
 
-def cpu_oracle_rate_all_cores(args, target_s: float):
+def cpu_oracle_rate_all_cores(args, target_s: float, seed=None, width=None, height=None, members=None,
+                              mode: str = "count"):
     """The oracle, unchanged, in one spawned process per host core, each on
     its own members of the workload, all starting at one barrier; member-px/s
     = all processes' member-pixels / the longest process's oracle time."""
     import multiprocessing as mp
+    seed = args.seed if seed is None else seed
+    width = args.width if width is None else width
+    height = args.height if height is None else height
+    members = args.members if members is None else members
     procs = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
     ctx = mp.get_context("spawn")
     with ctx.Manager() as mgr:
         out = mgr.dict(procs=procs)
         barrier = mgr.Barrier(procs)
-        ps = [ctx.Process(target=_oracle_worker, args=(args.seed, args.width, args.height, args.members, i,
-                                                       target_s, barrier, out)) for i in range(procs)]
+        ps = [ctx.Process(target=_oracle_worker, args=(seed, width, height, members, i,
+                                                       target_s, barrier, out, mode)) for i in range(procs)]
         for p in ps:
             p.start()
         for p in ps:
@@ -281,9 +296,24 @@ def cpu_oracle_rate_all_cores(args, target_s: float):
         return None
     done = sum(r[0] for r in res)
     spent = max(r[1] for r in res)
-    return {"value": done * args.width * args.height / spent, "unit": UNIT, "cores": procs, "kind": "oracle",
+    return {"value": done * width * height / spent, "unit": UNIT, "cores": procs, "kind": "oracle",
             "sample": f"{done} member passes over {procs} processes, one member at a time "
                       f"({spent:.1f} s of oracle time in the longest process)"}
+
+
+def cpu_baseline_line(args, sweep: str, seed: int, width: int, height: int, members: int, mode: str):
+    """One JSON line: the oracle timed on a bounded sample of a sweep's
+    workload, one thread and one process per host core (spawned after the GPU
+    work, so no process is forked from a CUDA context)."""
+    import synth
+    ens = synth.ensemble(seed, width, height, members)
+    rate, done, spent = cpu_oracle_rate(ens, members, args.cpu_seconds, batch=1, mode=mode)
+    one = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{done} member passes over the {members} members of the {width}x{height} workload "
+                     f"({spent:.1f} s, one thread)"}
+    allc = cpu_oracle_rate_all_cores(args, args.cpu_seconds, seed, width, height, members, mode)
+    print(json.dumps({"sweep": sweep, "cpu_baseline": True, "mode": mode, "width": width, "height": height,
+                      "members": members, "seed": seed, "one_thread": one, "all_cores": allc}), flush=True)
 
 
 def run_reference(args):
@@ -315,8 +345,11 @@ def run_reference(args):
 
 
 def workload_config(args):
-    return {"workload": f"streaming sweep point: {args.members} flood masks of {args.width}x{args.height} "
-                        f"uint8, uint16 counts, bucket + RGBA render",
+    return {"workload": f"{args.members} flood masks of {args.width}x{args.height} uint8 (a streaming-sweep "
+                        f"point), uint16 counts, bucket + RGBA render",
+            "value_regime": "device resident: the masks already in HBM, one pass = clear + accumulate + render",
+            "e2e_regime": "streamed: the masks in pinned host memory, uploaded through the staging buffers "
+                          "(or read in place with --e2e-mode host_read), outputs read back to the host",
             "width": args.width, "height": args.height, "members": args.members,
             "read_path": args.read_path, "chunk_members": args.chunk, "staging_buffers": args.staging,
             "seed": args.seed, "l2": "inputs larger than L2 (no flush needed)"}
@@ -687,34 +720,46 @@ def sweep_layout(args, torch, binding, device, stream):
 def sweep_streaming(args, torch, binding, device, stream, sides=None, counts=None, chunks=None,
                     stagings=None, pool_bytes=16 << 30, plan=None):
     """Members streamed from pinned host memory: member-px/s, H2D GB/s against
-    the measured pinned copy rate, copy/compute overlap, MB per 100 ms."""
+    the measured pinned copy rate, copy/compute overlap, MB per 100 ms.  A plan
+    entry is (side, members, chunk depth (0 = automatic), staging buffers[,
+    read path]); the texture path's conversion runs between each upload and
+    its kernel, so its busy time is reported beside the kernel's."""
     import synth
     from paper_2104_14667_gb300 import metrics
     peak = link_peak_gbs(torch, device)
     sides = sides or [512, 1024, 2048, 4096, 8192]
     counts = counts or [16, 64, 256, 1024, 4096]
     if plan is None:
-        plan = [(s, n, args.chunk, args.staging) for s in sides for n in counts]
+        plan = [(s, n, c, args.staging) for c in sorted({args.chunk, 0}, reverse=True) for s in sides for n in counts]
         for c in (chunks or []):
             plan.append((4096, 1024, c, args.staging))
         for k in (stagings or []):
             plan.append((4096, 1024, args.chunk, k))
-    counts = sorted({n for _, n, _, _ in plan})
+        for path in ("texture", "tma"):
+            for c in sorted({args.chunk, 0}, reverse=True):
+                for k in (2, 3):
+                    plan.append((4096, 1024, c, k, path))
+    plan = [tuple(e) + ("linear",) * (5 - len(e)) for e in plan]
+    counts = sorted({e[1] for e in plan})
     pools = {}
-    for side, n, chunk, k in plan:
+    for side, n, chunk, k, path in plan:
         P = side * side
         if side not in pools:
+            for old_host, _, old_handle in pools.values():
+                release_host_buffer(torch, old_host, old_handle)
             pools.clear()
             torch.cuda.empty_cache()
             pool_n = max(1, min(max(counts), pool_bytes // P))
             ens = synth.ensemble(2, side, side, pool_n)
             dev = torch.empty((pool_n, side, side), dtype=torch.uint8, device=device)
             synth.fill_masks_torch(ens, dev)
-            host = torch.empty((pool_n, side, side), dtype=torch.uint8, pin_memory=True)
+            # huge-page advised and registered, like the e2e leg's buffer:
+            # repeated 16 GB cudaHostAlloc pools slowed the copy engines
+            host, handle = pinned_host_buffer(torch, (pool_n, side, side))
             host.copy_(dev)
             del dev
-            pools[side] = (host, ens)
-        host, ens = pools[side]
+            pools[side] = (host, ens, handle)
+        host, ens, _ = pools[side]
         pool_n = host.shape[0]
 
         def add_all(comp):
@@ -724,7 +769,7 @@ def sweep_streaming(args, torch, binding, device, stream, sides=None, counts=Non
                 comp.add(host[:take])
                 done += take
 
-        cfg = dict(chunk_members=chunk, staging_buffers=k, stream=stream.cuda_stream)
+        cfg = dict(chunk_members=chunk, staging_buffers=k, stream=stream.cuda_stream, read_path=path)
         with binding.Composite(side, side, **cfg) as comp:
             for _ in range(args.warmup):
                 comp.clear()
@@ -743,23 +788,30 @@ def sweep_streaming(args, torch, binding, device, stream, sides=None, counts=Non
         copies = [(float(a), float(b)) for kk, a, b in rec if int(kk) == 0]
         kernels = [(float(a), float(b)) for kk, a, b in rec if int(kk) != 0]
         gbs = n * P / (ms * 1e-3) / 1e9
-        # Section 7.1's model over the traced chunks: copy c_i, no layout
-        # transform on the linear path, processing p_i; beside the traced wall
+        # Section 7.1's model over the traced chunks: copy c_i, layout
+        # transform m_i (texture path; none on the others), processing p_i;
+        # beside the traced wall
         model = {}
         ups = sorted(copies)
         ks = sorted((float(a), float(b)) for kk, a, b in rec if int(kk) == 2)
-        if ups and len(ups) == len(ks):
+        ms_conv = sorted((float(a), float(b)) for kk, a, b in rec if int(kk) == 1)
+        if ups and len(ups) == len(ks) and len(ms_conv) in (0, len(ks)):
             c = [b - a for a, b in ups]
             pk = [b - a for a, b in ks]
-            model = {"model_wall_ms": metrics.pipeline_wall(c, [0.0] * len(c), pk),
+            mk = [b - a for a, b in ms_conv] or [0.0] * len(c)
+            model = {"model_wall_ms": metrics.pipeline_wall(c, mk, pk),
                      "traced_wall_ms": max(b for _, b in ks) - min(a for a, _ in ups),
-                     "paper_e": metrics.pipeline_ratio(c, [0.0] * len(c), pk), "traced_chunks": len(c)}
+                     "paper_e": metrics.pipeline_ratio(c, mk, pk), "traced_chunks": len(c)}
+        busy = {"upload_busy_ms": _busy(rec, (0,)), "conversion_busy_ms": _busy(rec, (1,)),
+                "kernel_busy_ms": _busy(rec, (2,))}
         print(json.dumps({"sweep": "streaming", "side": side, "members": n, "chunk_members": chunk,
-                          "staging_buffers": k, "pool_members": pool_n, "ms_per_pass": ms,
+                          "read_path": path, "staging_buffers": k, "pool_members": pool_n, "ms_per_pass": ms,
                           "member_px_per_s": n * P / (ms * 1e-3), "h2d_gbs": gbs,
                           "link_peak_gbs": peak, "link_frac": gbs / peak,
                           "overlap_fraction": metrics.overlap_fraction(copies, kernels),
-                          "mb_per_100ms": gbs * 100.0, **model, "exact_sampled_rows": exact}), flush=True)
+                          "mb_per_100ms": gbs * 100.0, **model, **busy, "exact_sampled_rows": exact}), flush=True)
+    for old_host, _, old_handle in pools.values():
+        release_host_buffer(torch, old_host, old_handle)
     pools.clear()
 
 
@@ -969,18 +1021,85 @@ def sweep_serving(args, torch, binding, device, stream):
                 "recomputes": stats["recomputes"], "checked": len(checks), "exact": exact,
                 "cycle_device_s": stats["cycle_device_us"] * 1e-6, "enqueue_host_s": stats["enqueue_host_us"] * 1e-6}
 
+    def runs_of(ids):
+        """Maximal runs of consecutive ids as (first, length)."""
+        out = []
+        for i in ids:
+            if out and out[-1][0] + out[-1][1] == i:
+                out[-1][1] += 1
+            else:
+                out.append([int(i), 1])
+        return out
+
+    def run_plain(trace):
+        """The plain per-request pipeline: no server, one composite context
+        per session (32-bit counts), and every request recomputed from its
+        session's member set with the plain calls -- clear, one add per run of
+        consecutive member ids (resident runs read in place, overflow runs
+        streamed through the staging buffers), render -- one request at a time
+        in arrival order."""
+        ctxs = [binding.Composite(W, H, count_bits=32, stream=stream.cuda_stream, mask_format=args.mask_format)
+                for _ in range(n_sessions)]
+        sets = [np.zeros(R + O, bool) for _ in range(n_sessions)]
+        lat, checks = [], []
+        t0 = time.perf_counter()
+        try:
+            for i, (t_arr, s, ids) in enumerate(trace):
+                now = time.perf_counter() - t0
+                if t_arr > now:
+                    time.sleep(t_arr - now)
+                for t in ids:
+                    sets[s][t] ^= True
+                members = np.flatnonzero(sets[s])
+                comp = ctxs[s]
+                comp.clear()
+                for first, length in runs_of(members):
+                    if first < R:
+                        take = min(length, R - first)
+                        comp.add(resident[first:first + take])
+                        first, length = first + take, length - take
+                    if length:
+                        comp.add(overflow[first - R:first - R + length])
+                if i % 25 == 0:
+                    c = torch.empty((H, W), dtype=torch.int32, device=device)
+                    comp.render(counts_out=c)
+                    checks.append((c, members))
+                else:
+                    comp.render(bucket_out=outs[s][0], rgba_out=outs[s][1])
+                comp.sync()
+                lat.append(1e3 * (time.perf_counter() - t0 - t_arr))
+                if time.perf_counter() - t0 > 300:
+                    raise RuntimeError("plain serving run exceeded 300 s")
+            wall = time.perf_counter() - t0 - trace[0][0]
+        finally:
+            for comp in ctxs:
+                comp.close()
+        exact = True
+        for c, members in checks:
+            lv = np.sort(sorted_levels[members])
+            ident = len(members) - np.searchsorted(lv, ens.terrain.ravel(), side="right").reshape(H, W)
+            exact &= bool(np.array_equal(c.cpu().numpy().astype(np.int64), ident))
+        return {"composites_per_s": len(trace) / wall, "p50_ms": metrics.percentile(lat, 50),
+                "p99_ms": metrics.percentile(lat, 99), "mean_ms": float(np.mean(lat)), "wall_s": wall,
+                "checked": len(checks), "exact": exact}
+
     for rate in args.rates:
         trace = synth.serving_trace(5, args.requests, rate, n_sessions, R + O)
         batched = run(trace, args.max_batch, 4)
         single = run(trace, 1, 1)      # the queue alone: one request on the device at a time
+        plain = run_plain(trace) if args.plain_arm else None
         print(json.dumps({"sweep": "serving", "mask_format": args.mask_format, "rate_per_s": rate,
                           "requests": len(trace), "resident": R,
                           "overflow": O, "side": W, "sessions": n_sessions, "staging_members": staging,
                           "setup_s": setup_s,
                           "toggle_members_mean": float(np.mean([len(t[2]) for t in trace])),
-                          "batched": batched, "one_at_a_time": single,
+                          "batched": batched, "one_at_a_time": single, "plain_per_request": plain,
                           "throughput_gain": batched["composites_per_s"] / single["composites_per_s"],
-                          "p99_gain": single["p99_ms"] / batched["p99_ms"]}), flush=True)
+                          "p99_gain": single["p99_ms"] / batched["p99_ms"],
+                          "throughput_gain_vs_plain": (batched["composites_per_s"] / plain["composites_per_s"]
+                                                       if plain else None),
+                          "p99_gain_vs_plain": plain["p99_ms"] / batched["p99_ms"] if plain else None}),
+              flush=True)
 
 
 def sweep_compressed(args, torch, binding, device, stream):
@@ -1094,6 +1213,9 @@ def run_sweep(args):
     binding.load()
     if args.sweep == "readpath":
         sweep_readpath(args, torch, binding, device, stream)
+        if not args.no_cpu_baseline:
+            for mode in ("count", "mean_depth"):
+                cpu_baseline_line(args, "readpath", 3, 4096, 4096, 256, mode)
     elif args.sweep == "layout":
         sweep_layout(args, torch, binding, device, stream)
     elif args.sweep == "streaming":
@@ -1112,6 +1234,8 @@ def run_sweep(args):
     elif args.sweep == "tiny":
         sweep_streaming(args, torch, binding, device, stream,
                         plan=[(1024, 16, c, k) for c in (16, 1, 2, 4, 8) for k in (2, 1)])
+        if not args.no_cpu_baseline:
+            cpu_baseline_line(args, "tiny", 1, 1024, 1024, 16, "count")
 
 
 def main():

@@ -102,8 +102,14 @@ typedef struct composite_config {
     int32_t staging_buffers;    /* k device receiving buffers, 1..8; 1 is the paper's
                                    single-buffer control ("1b"), 2 its dual buffer ("2b");
                                    default 2                                              */
-    int32_t chunk_members;      /* C members per upload and per kernel launch, 1..255;
-                                   default 16                                             */
+    int32_t chunk_members;      /* C members per upload and per kernel launch, 1..255, or
+                                   0 = automatic (the default): a staging buffer holds up
+                                   to 256 MiB of rasters (at most 255), and each add or
+                                   remove of n rasters is cut into chunks of
+                                   max(16 MiB of rasters, min(that cap, ceil(n / 32)))
+                                   members, so that a call has about 32 chunks: the
+                                   kernel of a call's last chunk has no upload left to
+                                   hide under                                             */
     int32_t count_bits;         /* 16 (N <= 65535) or 32; default 16                      */
     int32_t mode;               /* CPT_MODE_*; default CPT_MODE_COUNT                     */
     int32_t trace;              /* 1 = time every copy and kernel with CUDA events

@@ -335,7 +335,7 @@ def caller_stream():
     return None
 
 
-def make_config(read_path="linear", staging_buffers=2, chunk_members=16, count_bits=16,
+def make_config(read_path="linear", staging_buffers=2, chunk_members=0, count_bits=16,
                 mode="count", trace=False, pinned_ring_bytes=0, stream=None,
                 wait_timeout_ms=0, host_read=False, tma_box_bytes=0, mask_format="bytes",
                 layout_converter="kernel", ingest_threads=0) -> Config:
@@ -459,6 +459,9 @@ class EngineConfig(ctypes.Structure):
         ("wait_timeout_ms", ctypes.c_int64),
         ("schedule", ctypes.c_int32),
         ("upload_stream", ctypes.c_void_p),
+        ("item_member_groups", ctypes.c_int32),
+        ("staging_buffers", ctypes.c_int32),
+        ("staging_bytes", ctypes.c_int64),
     ]
 
 
@@ -512,6 +515,7 @@ def _engine_lib():
             "composite_engine_replay": (ctypes.c_int, [vp]),
             "composite_engine_tune": (ctypes.c_int, [vp, ctypes.POINTER(Op), i32, i32, p32, p32]),
             "composite_engine_get_tuning": (ctypes.c_int, [vp, p32, p32]),
+            "composite_engine_get_config": (ctypes.c_int, [vp, ctypes.POINTER(EngineConfig)]),
             "composite_engine_end": (ctypes.c_int, [vp]),
             "composite_engine_last_error": (ctypes.c_char_p, [vp]),
         }
@@ -540,7 +544,8 @@ class Engine:
     """Many composite planes on one GPU; ops on all of them run in one
     persistent launch (include/composite_engine.h)."""
 
-    def __init__(self, stream=None, slab_members=0, ctas_per_sm=0, wait_timeout_ms=0, schedule="persistent"):
+    def __init__(self, stream=None, slab_members=0, ctas_per_sm=0, wait_timeout_ms=0, schedule="persistent",
+                 item_member_groups=0, staging_buffers=0, staging_bytes=0):
         self.lib = _engine_lib()
         cfg = EngineConfig()
         self.lib.composite_engine_default_config(ctypes.byref(cfg))
@@ -549,6 +554,9 @@ class Engine:
         cfg.ctas_per_sm = ctas_per_sm
         cfg.wait_timeout_ms = wait_timeout_ms
         cfg.schedule = {"persistent": CPT_SCHEDULE_PERSISTENT, "grid": CPT_SCHEDULE_GRID}[schedule]
+        cfg.item_member_groups = item_member_groups
+        cfg.staging_buffers = staging_buffers
+        cfg.staging_bytes = staging_bytes
         h = ctypes.c_void_p()
         _echeck(self.lib, None, self.lib.composite_engine_begin(ctypes.byref(h), ctypes.byref(cfg)))
         self.h = h
@@ -570,9 +578,10 @@ class Engine:
         _echeck(self.lib, self.h, self.lib.composite_engine_clear(self.h, plane))
 
     def op(self, plane: int, members, sign: int = 1, index=None, mask_format: str = "bytes") -> Op:
-        """An op from a device tensor of masks [n, H, W] (bit-packed: [n, H,
-        ceil(W/8)]), or the whole ensemble when an int32 device index tensor
-        selects members.  The engine keeps the tensors alive until sync."""
+        """An op from a tensor of masks [n, H, W] (bit-packed: [n, H,
+        ceil(W/8)]) in device or pinned host memory, or the whole ensemble
+        when an int32 device index tensor selects members (device members
+        only).  The engine keeps the tensors alive until sync."""
         ptr, n, _, _, stride, pitch, _, _ = _raster_view(members)
         self._keep.extend([members, index])
         o = Op()
@@ -641,6 +650,14 @@ class Engine:
         s, c = ctypes.c_int32(), ctypes.c_int32()
         _echeck(self.lib, self.h, self.lib.composite_engine_get_tuning(self.h, ctypes.byref(s), ctypes.byref(c)))
         return s.value, c.value
+
+    def config(self) -> dict:
+        """Every field of the engine's current configuration (after tuning:
+        the tuned values)."""
+        cfg = EngineConfig()
+        _echeck(self.lib, self.h, self.lib.composite_engine_get_config(self.h, ctypes.byref(cfg)))
+        return {name: getattr(cfg, name) for name, _ in EngineConfig._fields_
+                if name not in ("cuda_stream", "upload_stream")}
 
     def close(self):
         if getattr(self, "h", None) is not None:

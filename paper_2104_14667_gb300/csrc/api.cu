@@ -69,6 +69,8 @@ struct composite_ctx {
     int64_t row_bytes = 0;     // bytes of one raster row as the caller lays it out (unpadded)
     int64_t stage_pitch = 0;   // staging row pitch, bytes (a multiple of 16)
     int64_t member_bytes = 0;  // staging raster stride, bytes
+    int slot_members = 0;      // rasters a staging slot holds: chunk_members, or the automatic depth's cap
+    int call_chunk = 0;        // C of the current add/remove
     bool bits = false;         // masks are bit-packed
     Plane plane{};
     int *flags = nullptr;      // device flags
@@ -183,6 +185,28 @@ int refuse_poisoned(composite_ctx *ctx) {
     return fail(ctx, CPT_ESTATE, "context poisoned: %s; clear it", ctx->poison_reason.c_str());
 }
 
+// Automatic chunk depth (chunk_members = 0).  A staging slot holds up to
+// kAutoSlotBytes of rasters.  Each call is cut into about kAutoChunksPerCall
+// chunks, no smaller than kAutoMinChunkBytes: the kernel of a call's last
+// chunk has no later upload to hide under, so the share of kernel time left
+// exposed is about one chunk in the number of chunks, while chunks too small
+// pay a fixed cost per copy and launch.
+constexpr int64_t kAutoSlotBytes = 256ll << 20;
+constexpr int64_t kAutoMinChunkBytes = 16ll << 20;
+constexpr int kAutoChunksPerCall = 32;
+
+int auto_slot_members(int64_t member_bytes) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>(255, kAutoSlotBytes / member_bytes));
+}
+
+int chunk_for_call(const composite_ctx *ctx, int n) {
+    if (ctx->cfg.chunk_members > 0) return ctx->cfg.chunk_members;
+    const int cap = ctx->slot_members;
+    const int floor_c = (int)std::min<int64_t>(cap, std::max<int64_t>(1, (kAutoMinChunkBytes + ctx->member_bytes - 1) / ctx->member_bytes));
+    const int want = (n + kAutoChunksPerCall - 1) / kAutoChunksPerCall;
+    return std::max(floor_c, std::min(cap, want));
+}
+
 // Called before the work of each chunk of an add or remove is queued.  From
 // then on a failure leaves part of the call's rasters folded in, which
 // apply() turns into a poisoned context.
@@ -221,7 +245,7 @@ Lut pack_lut(const uint8_t *rgba) {
 int check_config(const composite_config &c) {
     if (c.read_path < CPT_READ_LINEAR || c.read_path > CPT_READ_TMA) return fail(nullptr, CPT_EINVAL, "read_path %d out of range", c.read_path);
     if (c.staging_buffers < 1 || c.staging_buffers > 8) return fail(nullptr, CPT_EINVAL, "staging_buffers %d not in 1..8", c.staging_buffers);
-    if (c.chunk_members < 1 || c.chunk_members > 255) return fail(nullptr, CPT_EINVAL, "chunk_members %d not in 1..255", c.chunk_members);
+    if (c.chunk_members < 0 || c.chunk_members > 255) return fail(nullptr, CPT_EINVAL, "chunk_members %d not in 0..255", c.chunk_members);
     if (c.count_bits != 16 && c.count_bits != 32) return fail(nullptr, CPT_EINVAL, "count_bits %d is not 16 or 32", c.count_bits);
     if (c.mode != CPT_MODE_COUNT && c.mode != CPT_MODE_MEAN_DEPTH) return fail(nullptr, CPT_EINVAL, "mode %d out of range", c.mode);
     if (c.trace != 0 && c.trace != 1) return fail(nullptr, CPT_EINVAL, "trace must be 0 or 1");
@@ -281,9 +305,9 @@ int setup(composite_ctx *ctx) {
         CK(ctx, cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxTexture2DLayeredWidth, ctx->device));
         CK(ctx, cudaDeviceGetAttribute(&maxh, cudaDevAttrMaxTexture2DLayeredHeight, ctx->device));
         CK(ctx, cudaDeviceGetAttribute(&maxl, cudaDevAttrMaxTexture2DLayeredLayers, ctx->device));
-        if (groups > maxw || ctx->height > maxh || c.chunk_members > maxl)
+        if (groups > maxw || ctx->height > maxh || ctx->slot_members > maxl)
             return fail(ctx, CPT_EINVAL, "raster %dx%d with %d layers exceeds the layered texture limits (%d texels, %d rows, %d layers)",
-                        ctx->width, ctx->height, c.chunk_members, maxw, maxh, maxl);
+                        ctx->width, ctx->height, ctx->slot_members, maxw, maxh, maxl);
     }
 
     const int count_bytes = c.mode == CPT_MODE_COUNT ? c.count_bits / 8 : 4;
@@ -300,7 +324,7 @@ int setup(composite_ctx *ctx) {
     ctx->slots.resize(c.staging_buffers);
     for (Slot &s : ctx->slots) {
         if (cpt::fault_injected("staging_alloc")) return fail(ctx, CPT_ENOMEM, "staging buffer allocation refused (injected)");
-        CK(ctx, cudaMalloc(&s.stage, (size_t)c.chunk_members * ctx->member_bytes));
+        CK(ctx, cudaMalloc(&s.stage, (size_t)ctx->slot_members * ctx->member_bytes));
         CK(ctx, cudaEventCreateWithFlags(&s.ready, cudaEventDisableTiming));
         CK(ctx, cudaEventCreateWithFlags(&s.consumed, cudaEventDisableTiming));
         CK(ctx, cudaEventCreateWithFlags(&s.ring_free, cudaEventDisableTiming));
@@ -310,7 +334,7 @@ int setup(composite_ctx *ctx) {
                     ? cudaCreateChannelDesc(32, 32, 32, 32, cudaChannelFormatKindUnsigned)
                     : cudaCreateChannelDesc(32, 32, 32, 32, cudaChannelFormatKindFloat);
             CK(ctx, cudaMalloc3DArray(&s.array, &desc,
-                                      make_cudaExtent((size_t)groups, ctx->height, c.chunk_members),
+                                      make_cudaExtent((size_t)groups, ctx->height, ctx->slot_members),
                                       cudaArrayLayered | cudaArraySurfaceLoadStore));
             cudaResourceDesc rd{};
             rd.resType = cudaResourceTypeArray;
@@ -437,7 +461,7 @@ Slot &next_slot(composite_ctx *ctx) {
 
 // Pinned-host or device rasters: upload chunk by chunk through the slots.
 int run_staged(composite_ctx *ctx, const uint8_t *src, int n, int64_t stride, int64_t pitch, int sign) {
-    const int C = ctx->cfg.chunk_members;
+    const int C = ctx->call_chunk;
     for (int m0 = 0; m0 < n; m0 += C) {
         const cpt::TraceRange chunk_range("composite chunk");
         const int c = n - m0 < C ? n - m0 : C;
@@ -463,7 +487,7 @@ int run_staged(composite_ctx *ctx, const uint8_t *src, int n, int64_t stride, in
 // Device rasters on the texture path, converted straight from the caller's
 // memory into the slot arrays on the copy stream.
 int run_texture_from_device(composite_ctx *ctx, const uint8_t *src, int n, int64_t stride, int64_t pitch, int sign) {
-    const int C = ctx->cfg.chunk_members;
+    const int C = ctx->call_chunk;
     for (int m0 = 0; m0 < n; m0 += C) {
         const cpt::TraceRange chunk_range("composite chunk");
         const int c = n - m0 < C ? n - m0 : C;
@@ -488,7 +512,7 @@ constexpr int64_t kIngestPiece = 4 << 20;   // bytes per ring-copy piece
 int run_ring(composite_ctx *ctx, const uint8_t *src, int n, int64_t stride, int64_t pitch, int sign) {
     const int k = (int)ctx->slots.size();
     if (ctx->ring_chunk == 0) {
-        int64_t chunk = ctx->cfg.chunk_members;
+        int64_t chunk = ctx->slot_members;
         if (ctx->cfg.pinned_ring_bytes > 0) {
             const int64_t fit = ctx->cfg.pinned_ring_bytes / ((int64_t)k * ctx->member_bytes);
             if (fit < 1)
@@ -525,7 +549,7 @@ int run_ring(composite_ctx *ctx, const uint8_t *src, int n, int64_t stride, int6
             }
         }
     }
-    const int C = (int)ctx->ring_chunk;
+    const int C = (int)std::min<int64_t>(ctx->ring_chunk, ctx->call_chunk);
     const int64_t row = ctx->row_bytes;
     const int64_t dpitch = ctx->stage_pitch;
     for (int m0 = 0; m0 < n; m0 += C) {
@@ -604,6 +628,7 @@ int apply(composite_ctx *ctx, const void *members, int32_t n, int64_t stride, in
     const uint8_t *src = static_cast<const uint8_t *>(members);
     const MemKind kind = memory_kind(members);
     ctx->call_chunks = 0;
+    ctx->call_chunk = chunk_for_call(ctx, n);
     // uploads on the copy stream start after the caller's earlier work on the
     // compute stream (which may have produced the rasters)
     CK(ctx, cudaEventRecord(ctx->caller_ready, ctx->compute));
@@ -731,7 +756,7 @@ int composite_default_config(composite_config *cfg) try {
     memset(cfg, 0, sizeof *cfg);
     cfg->read_path = CPT_READ_LINEAR;
     cfg->staging_buffers = 2;
-    cfg->chunk_members = 16;
+    cfg->chunk_members = 0;
     cfg->count_bits = 16;
     cfg->mode = CPT_MODE_COUNT;
     cfg->trace = 0;
@@ -772,6 +797,7 @@ int composite_begin(composite_ctx **out, int32_t width, int32_t height, const co
     ctx->row_bytes = ctx->bits ? ((int64_t)width + 7) / 8 : (int64_t)width * ctx->elem;
     ctx->stage_pitch = (ctx->row_bytes + 15) / 16 * 16;
     ctx->member_bytes = ctx->stage_pitch * height;
+    ctx->slot_members = c.chunk_members > 0 ? c.chunk_members : auto_slot_members(ctx->member_bytes);
     rc = setup(ctx);
     if (rc) {
         g_begin_error = ctx->err;

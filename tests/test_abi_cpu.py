@@ -29,7 +29,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_default_config(lib):
     cfg = binding.composite_default_config()
-    assert (cfg.read_path, cfg.staging_buffers, cfg.chunk_members, cfg.count_bits, cfg.mode) == (0, 2, 16, 16, 0)
+    assert (cfg.read_path, cfg.staging_buffers, cfg.chunk_members, cfg.count_bits, cfg.mode) == (0, 2, 0, 16, 0)   # chunk_members 0 = automatic
     assert cfg.layout_converter == binding.CPT_CONVERT_KERNEL
     assert cfg.ingest_threads == 0
     assert ctypes.sizeof(binding.Config) == 72
@@ -43,7 +43,7 @@ def test_begin_rejects_empty_raster(lib, w, h):
 
 
 @pytest.mark.parametrize("field,value", [("read_path", 3), ("staging_buffers", 0), ("staging_buffers", 9),
-                                         ("chunk_members", 0), ("chunk_members", 256), ("count_bits", 8),
+                                         ("chunk_members", -1), ("chunk_members", 256), ("count_bits", 8),
                                          ("mode", 2), ("trace", 2), ("wait_timeout_ms", -1),
                                          ("host_read", 2), ("tma_box_bytes", 32),
                                          ("tma_box_bytes", 512), ("mask_format", 2),
@@ -81,12 +81,15 @@ def test_engine_defaults_and_no_gpu(lib):
     assert eng_lib.composite_engine_default_config(ctypes.byref(cfg)) == binding.CPT_OK
     assert (cfg.slab_members, cfg.ctas_per_sm) == (128, 5)
     assert ctypes.sizeof(binding.Op) == 48 and ctypes.sizeof(binding.RenderOp) == 32
-    assert ctypes.sizeof(binding.EngineConfig) == 40 and cfg.schedule == binding.CPT_SCHEDULE_PERSISTENT
+    assert ctypes.sizeof(binding.EngineConfig) == 56 and cfg.schedule == binding.CPT_SCHEDULE_PERSISTENT
+    assert (cfg.item_member_groups, cfg.staging_buffers, cfg.staging_bytes) == (512, 2, 256 << 20)
     assert eng_lib.composite_engine_end(None) == binding.CPT_OK
-    bad = binding.EngineConfig()
-    bad.slab_members = 256
     h = ctypes.c_void_p()
-    assert eng_lib.composite_engine_begin(ctypes.byref(h), ctypes.byref(bad)) == binding.CPT_EINVAL
+    for field, value in (("slab_members", 256), ("item_member_groups", 8), ("item_member_groups", 8193),
+                         ("staging_buffers", 1), ("staging_buffers", 9), ("staging_bytes", 1 << 19)):
+        bad = binding.EngineConfig()
+        setattr(bad, field, value)
+        assert eng_lib.composite_engine_begin(ctypes.byref(h), ctypes.byref(bad)) == binding.CPT_EINVAL, field
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         with pytest.raises(binding.CompositeError):

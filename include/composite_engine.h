@@ -19,11 +19,16 @@
  *   bucket(p) = N_P == 0 ? 0 : floor(255 count(p) / N_P); rgba(p) = lut[bucket(p)]
  *
  * Conventions: every call returns CPT_OK (0) or a negative composite_status
- * (composite.h); the message is in composite_engine_last_error.  Device
- * pointers only (members, index lists, outputs); rasters need 16-byte
- * aligned base, row pitch and member stride.  Work is queued on the engine's
- * stream; host waits are bounded by wait_timeout_ms.  Members and index
- * lists are borrowed until the next composite_engine_sync returns.
+ * (composite.h); the message is in composite_engine_last_error.  Members are
+ * device memory or pinned host memory; index lists and outputs are device
+ * memory; rasters need 16-byte aligned base, row pitch and member stride.
+ * Ops on pinned host members stream through the engine's own staging
+ * buffers (the dual-buffer pipeline of Section 4, Figs. 3-4): rasters of
+ * consecutive host ops are packed into a buffer of staging_bytes, uploaded on
+ * a copy stream while the previous buffer is folded, one accumulate launch
+ * per buffer.  Work is queued on the engine's stream; host waits are bounded
+ * by wait_timeout_ms.  Members and index lists are borrowed until the next
+ * composite_engine_sync returns.
  */
 #ifndef COMPOSITE_ENGINE_H
 #define COMPOSITE_ENGINE_H
@@ -56,16 +61,25 @@ typedef struct composite_engine_config {
                                  that streams its own rasters on a copy stream passes
                                  it here so the small uploads queue behind its uploads
                                  in order instead of competing for a copy engine      */
+    int32_t item_member_groups; /* work item size: a lane folds about this many
+                                 (member, 16-pixel group) pairs per item, so an item
+                                 covers 32 x (item_member_groups / slab) groups of one
+                                 slab; 16..8192, 0 = 512                                */
+    int32_t staging_buffers;  /* staging buffers for host ops, 2..8; 0 = 2           */
+    int64_t staging_bytes;    /* bytes per staging buffer, >= 1 MiB (and >= the largest
+                                 host raster); 0 = 256 MiB.  Allocated at the first
+                                 host op.                                              */
 } composite_engine_config;
 
 /* One add or remove of n_members masks to one plane.  Member i of the op is
  * the raster at members + idx(i) * member_stride_bytes, idx(i) =
  * member_index[i] (a device int32 array) or i when member_index is NULL.
- * The raster's width and height are the plane's. */
+ * The raster's width and height are the plane's.  members is device memory,
+ * or pinned host memory (then member_index must be NULL). */
 typedef struct composite_op {
     int32_t plane;
     int32_t sign;                 /* +1 add, -1 remove */
-    const void *members;          /* device, 16-byte aligned */
+    const void *members;          /* device or pinned host, 16-byte aligned */
     const int32_t *member_index;  /* device, n_members entries, or NULL */
     int32_t n_members;
     int32_t row_pitch_bytes;      /* multiple of 16, >= the row's bytes (width, or
@@ -133,24 +147,33 @@ int composite_engine_sync(composite_engine *eng, int32_t *bad_plane_out);
 
 /* Captures "clear every target plane, submit ops, render rops" as a CUDA
  * graph held by the engine (replacing any earlier one); the ops' member
- * sets, index lists and outputs are fixed by the capture.  Does not run it. */
+ * sets, index lists and outputs are fixed by the capture.  Does not run it.
+ * Device members only (CPT_EINVAL for an op on host memory). */
 int composite_engine_capture(composite_engine *eng, const composite_op *ops, int32_t n_ops,
                              const composite_render_op *rops, int32_t n_rops, const uint8_t *lut_rgba);
 
 /* Launches the captured graph once on the engine's stream. */
 int composite_engine_replay(composite_engine *eng);
 
-/* Autotuner: times "clear the ops' planes + submit ops" for every candidate
- * (slab_members in {32, 64, 128, 255} x schedule {grid, persistent with
- * ctas_per_sm 3, 4, 5}), `repeats` runs each, keeps the fastest as the
- * engine's configuration and reports it (either pointer may be NULL;
- * *ctas_per_sm_out = 0 means the grid schedule won).  The planes end holding
- * the result of the ops applied once to cleared planes. */
+/* Autotuner: times "clear the ops' planes + submit ops", `repeats` runs per
+ * candidate, in three rounds, each keeping the fastest: (1) slab_members in
+ * {32, 64, 128, 255} x schedule {grid, persistent with ctas_per_sm 3, 4, 5};
+ * (2) item_member_groups in {256, 512, 1024, 2048} (the work item's tile of
+ * groups); (3) when some op reads pinned host members, staging_buffers in
+ * {2, 3, 4} x staging_bytes in {64, 128, 256, 512} MiB.  The winner becomes
+ * the engine's configuration (composite_engine_get_config reports every
+ * field); slab and schedule are also reported here (either pointer may be
+ * NULL; *ctas_per_sm_out = 0 means the grid schedule won).  The planes end
+ * holding the result of the ops applied once to cleared planes. */
 int composite_engine_tune(composite_engine *eng, const composite_op *ops, int32_t n_ops, int32_t repeats,
                           int32_t *slab_out, int32_t *ctas_per_sm_out);
 
 /* Current (slab_members, ctas_per_sm); ctas_per_sm 0 = grid schedule. */
 int composite_engine_get_tuning(const composite_engine *eng, int32_t *slab_out, int32_t *ctas_per_sm_out);
+
+/* The engine's whole current configuration (defaults filled in, tuned values
+ * after composite_engine_tune). */
+int composite_engine_get_config(const composite_engine *eng, composite_engine_config *cfg_out);
 
 /* Waits (bounded) and frees everything.  NULL is accepted. */
 int composite_engine_end(composite_engine *eng);

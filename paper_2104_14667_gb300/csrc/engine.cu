@@ -436,6 +436,17 @@ struct Upload {
     bool used = false;
 };
 
+// A staging buffer for ops on pinned host members.
+struct StageSlot {
+    uint8_t *d = nullptr;
+    cudaEvent_t ready = nullptr;     // its upload finished (copy stream)
+    cudaEvent_t consumed = nullptr;  // the launch that read it finished (engine stream)
+    bool used = false;
+};
+
+constexpr int64_t kDefaultStageBytes = 256ll << 20;
+constexpr int kDefaultItemMemberGroups = 512;
+
 thread_local std::string g_engine_error;
 
 }  // namespace
@@ -462,6 +473,12 @@ struct composite_engine {
     std::vector<std::pair<int32_t, int64_t>> graph_n;   // plane -> N after a replay
     std::vector<int32_t> graph_planes;                  // every plane the graph touches
     cudaStream_t capture_stream = nullptr;              // private stream for graph capture
+    // ops on pinned host members
+    std::vector<StageSlot> stage;
+    int64_t stage_bytes = 0;       // bytes per allocated staging buffer
+    uint64_t stage_next = 0;
+    cudaStream_t copy = nullptr;   // their uploads
+    cudaEvent_t caller_ready = nullptr;
     std::string err;
 };
 
@@ -563,7 +580,8 @@ bool plane_ok(const composite_engine *e, int32_t p) {
 // Validates ops and builds their descriptors.  n_after holds, per plane
 // touched, the member count after the ops starting from `start` counts.
 int plan_ops(composite_engine *e, const composite_op *ops, int32_t n_ops, std::vector<OpDesc> *descs,
-             int64_t *n_items, std::vector<std::pair<int32_t, int64_t>> *n_after, bool from_zero) {
+             int64_t *n_items, std::vector<std::pair<int32_t, int64_t>> *n_after, bool from_zero,
+             bool check_n = true) {
     if (n_ops < 0 || (n_ops > 0 && !ops)) return efail(e, CPT_EINVAL, "bad op list");
     descs->clear();
     n_after->clear();
@@ -578,8 +596,9 @@ int plan_ops(composite_engine *e, const composite_op *ops, int32_t n_ops, std::v
         const PlaneRec &p = e->planes[o.plane];
         if (n[o.plane] < 0) n[o.plane] = from_zero ? 0 : p.n;
         n[o.plane] += (int64_t)o.sign * o.n_members;
-        if (n[o.plane] < 0) return efail(e, CPT_EINVAL, "op %d: plane %d would hold fewer than 0 members", i, o.plane);
-        if (n[o.plane] > p.max_members())
+        if (check_n && n[o.plane] < 0)
+            return efail(e, CPT_EINVAL, "op %d: plane %d would hold fewer than 0 members", i, o.plane);
+        if (check_n && n[o.plane] > p.max_members())
             return efail(e, CPT_EINVAL, "op %d: plane %d would exceed %lld members (%d-bit counts)", i, o.plane,
                          (long long)p.max_members(), p.count_bits);
         if (o.n_members == 0) continue;
@@ -609,9 +628,10 @@ int plan_ops(composite_engine *e, const composite_op *ops, int32_t n_ops, std::v
         d.words_per_row = (int32_t)(((int64_t)p.width + 31) / 32);
         const int64_t groups = bits ? (int64_t)d.words_per_row * p.height : (int64_t)d.groups_per_row * p.height;
         // a warp item: 32 lanes x groups_per_thread groups, so that a lane
-        // streams about 512 member-groups per item whatever the slab length
+        // streams about item_member_groups member-groups per item whatever
+        // the slab length
         const int first_slab = std::min(o.n_members, slab);
-        d.groups_per_thread = std::max(1, 512 / first_slab);
+        d.groups_per_thread = std::max(1, e->cfg.item_member_groups / first_slab);
         const int64_t per_item = 32ll * d.groups_per_thread;
         d.tiles = (int32_t)((groups + per_item - 1) / per_item);
         d.slab = slab;
@@ -726,6 +746,144 @@ int clear_plane(composite_engine *e, int32_t p) {
     return CPT_OK;
 }
 
+// Memory kind of an op's members: 1 = pinned host, 0 = device, -1 = neither.
+int member_kind(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return 0;
+    return a.type == cudaMemoryTypeHost ? 1 : -1;
+}
+
+void free_stage(composite_engine *e) {
+    for (StageSlot &s : e->stage) {
+        if (s.d) cudaFree(s.d);
+        if (s.ready) cudaEventDestroy(s.ready);
+        if (s.consumed) cudaEventDestroy(s.consumed);
+    }
+    e->stage.clear();
+    e->stage_bytes = 0;
+    e->stage_next = 0;
+}
+
+// Staging buffers of the configured count and size, allocated at the first
+// host op and again whenever the configuration changed (after the engine's
+// queued work, which may still read the old ones).
+int ensure_stage(composite_engine *e) {
+    const int k = e->cfg.staging_buffers;
+    const int64_t bytes = e->cfg.staging_bytes;
+    if ((int)e->stage.size() == k && e->stage_bytes == bytes) return CPT_OK;
+    int rc = drain(e);
+    if (rc) return rc;
+    free_stage(e);
+    if (!e->copy) ECK(e, cudaStreamCreateWithFlags(&e->copy, cudaStreamNonBlocking));
+    if (!e->caller_ready) ECK(e, cudaEventCreateWithFlags(&e->caller_ready, cudaEventDisableTiming));
+    e->stage.resize(k);
+    for (StageSlot &s : e->stage) {
+        cudaError_t err = cudaMalloc(&s.d, (size_t)bytes);
+        if (err == cudaSuccess) err = cudaEventCreateWithFlags(&s.ready, cudaEventDisableTiming);
+        if (err == cudaSuccess) err = cudaEventCreateWithFlags(&s.consumed, cudaEventDisableTiming);
+        if (err != cudaSuccess) {
+            free_stage(e);
+            return ecuda(e, err, "staging buffer allocation");
+        }
+    }
+    e->stage_bytes = bytes;
+    return CPT_OK;
+}
+
+// Launches the accumulate kernel over ops (already validated as a whole).
+int launch_ops(composite_engine *e, const composite_op *ops, int32_t n_ops, bool *launched) {
+    std::vector<OpDesc> descs;
+    std::vector<std::pair<int32_t, int64_t>> n_after;
+    int64_t items = 0;
+    int rc = plan_ops(e, ops, n_ops, &descs, &items, &n_after, false, false);
+    if (rc || items == 0) return rc;
+    Upload *u = nullptr;
+    rc = upload(e, e->up_ops, &e->up_i, descs.data(), descs.size() * sizeof(OpDesc), &u);
+    if (rc) return rc;
+    if (cpt::fault_injected("engine_submit")) return efail(e, CPT_ECUDA, "submit refused before its launch (injected)");
+    *launched = true;   // from here on the launch may have begun
+    rc = launch_accumulate(e, u->d, (int)descs.size(), items, e->d_counter);
+    if (rc) return rc;
+    ECK(e, cudaEventRecord(u->consumed, e->stream));
+    return CPT_OK;
+}
+
+// Ops on pinned host members: their rasters are packed, op after op, into
+// staging buffers of stage_bytes; a full buffer is uploaded on the copy
+// stream (after the launch that last read it) and folded by one accumulate
+// launch on the engine stream (after the upload), so the upload of one
+// buffer overlaps the fold of the previous one.
+int stream_host_ops(composite_engine *e, const std::vector<composite_op> &hops, bool *launched) {
+    int rc = ensure_stage(e);
+    if (rc) return rc;
+    // uploads start after the caller's earlier work on the engine stream
+    ECK(e, cudaEventRecord(e->caller_ready, e->stream));
+    ECK(e, cudaStreamWaitEvent(e->copy, e->caller_ready, 0));
+    struct Run {
+        size_t op;
+        int32_t m0, cnt;
+        int64_t offset;
+    };
+    std::vector<Run> runs;
+    int64_t used = 0;
+    int64_t chunk = 0;
+    const int64_t inject_at = cpt::fault_injected_value("engine_chunk_fail");
+    auto flush = [&]() -> int {
+        if (runs.empty()) return CPT_OK;
+        if (inject_at == chunk) return efail(e, CPT_ECUDA, "upload of staging chunk %lld refused (injected)", (long long)chunk);
+        ++chunk;
+        StageSlot &slot = e->stage[e->stage_next++ % e->stage.size()];
+        if (slot.used) ECK(e, cudaStreamWaitEvent(e->copy, slot.consumed, 0));
+        std::vector<composite_op> cops;
+        cops.reserve(runs.size());
+        for (const Run &r : runs) {
+            const composite_op &o = hops[r.op];
+            const int64_t rb = (int64_t)o.row_pitch_bytes * e->planes[o.plane].height;
+            const uint8_t *src = static_cast<const uint8_t *>(o.members) + (int64_t)r.m0 * o.member_stride_bytes;
+            if (o.member_stride_bytes == rb)
+                ECK(e, cudaMemcpyAsync(slot.d + r.offset, src, (size_t)(r.cnt * rb), cudaMemcpyHostToDevice, e->copy));
+            else
+                ECK(e, cudaMemcpy2DAsync(slot.d + r.offset, (size_t)rb, src, (size_t)o.member_stride_bytes, (size_t)rb,
+                                         (size_t)r.cnt, cudaMemcpyHostToDevice, e->copy));
+            composite_op c = o;
+            c.members = slot.d + r.offset;
+            c.member_index = nullptr;
+            c.n_members = r.cnt;
+            c.member_stride_bytes = rb;
+            cops.push_back(c);
+        }
+        ECK(e, cudaEventRecord(slot.ready, e->copy));
+        ECK(e, cudaStreamWaitEvent(e->stream, slot.ready, 0));
+        int r = launch_ops(e, cops.data(), (int32_t)cops.size(), launched);
+        if (r) return r;
+        ECK(e, cudaEventRecord(slot.consumed, e->stream));
+        slot.used = true;
+        runs.clear();
+        used = 0;
+        return CPT_OK;
+    };
+    for (size_t i = 0; i < hops.size(); ++i) {
+        const composite_op &o = hops[i];
+        const int64_t rb = (int64_t)o.row_pitch_bytes * e->planes[o.plane].height;
+        for (int32_t m = 0; m < o.n_members;) {
+            const int64_t fit = (e->stage_bytes - used) / rb;
+            if (fit <= 0) {
+                if ((rc = flush())) return rc;
+                continue;
+            }
+            const int32_t take = (int32_t)std::min<int64_t>(fit, o.n_members - m);
+            runs.push_back({i, m, take, used});
+            used += take * rb;
+            m += take;
+        }
+    }
+    return flush();
+}
+
 int submit_internal(composite_engine *e, const composite_op *ops, int32_t n_ops) {
     const cpt::TraceRange range("composite_engine_submit");
     std::vector<OpDesc> descs;
@@ -736,21 +894,48 @@ int submit_internal(composite_engine *e, const composite_op *ops, int32_t n_ops)
     for (const auto &pn : n_after)
         if (e->planes[pn.first].poisoned)
             return efail(e, CPT_ESTATE, "plane %d: an earlier submit failed part-way; clear it", pn.first);
-    if (items > 0) {
-        Upload *u = nullptr;
-        rc = upload(e, e->up_ops, &e->up_i, descs.data(), descs.size() * sizeof(OpDesc), &u);
-        if (rc) return rc;   // nothing launched: every plane is as before
-        if (cpt::fault_injected("engine_submit")) return efail(e, CPT_ECUDA, "submit refused before its launch (injected)");
-        rc = launch_accumulate(e, u->d, (int)descs.size(), items, e->d_counter);
-        if (rc) {
-            // the launch may have begun: the planes it touches hold an unknown
-            // part of the ops until they are cleared
-            for (const auto &pn : n_after) e->planes[pn.first].poisoned = true;
-            return rc;
+    // device ops fold in one launch; ops on pinned host members stream
+    std::vector<composite_op> dev_ops, host_ops;
+    for (int32_t i = 0; i < n_ops; ++i) {
+        const composite_op &o = ops[i];
+        if (o.n_members == 0) continue;
+        const int kind = member_kind(o.members);
+        if (kind < 0) return efail(e, CPT_EINVAL, "op %d: members must be device or pinned host memory", i);
+        if (kind == 0) {
+            dev_ops.push_back(o);
+            continue;
         }
-        for (const auto &pn : n_after) e->planes[pn.first].n = pn.second;
-        ECK(e, cudaEventRecord(u->consumed, e->stream));
-        return CPT_OK;
+        if (o.member_index) return efail(e, CPT_EINVAL, "op %d: an index list needs device members", i);
+        if ((int64_t)o.row_pitch_bytes * e->planes[o.plane].height > e->cfg.staging_bytes)
+            return efail(e, CPT_EINVAL, "op %d: a raster is larger than staging_bytes", i);
+        host_ops.push_back(o);
+    }
+    bool launched = false;
+    if (host_ops.empty()) {
+        if (items > 0) {
+            Upload *u = nullptr;
+            rc = upload(e, e->up_ops, &e->up_i, descs.data(), descs.size() * sizeof(OpDesc), &u);
+            if (rc) return rc;   // nothing launched: every plane is as before
+            if (cpt::fault_injected("engine_submit"))
+                return efail(e, CPT_ECUDA, "submit refused before its launch (injected)");
+            launched = true;
+            rc = launch_accumulate(e, u->d, (int)descs.size(), items, e->d_counter);
+            if (!rc) {
+                for (const auto &pn : n_after) e->planes[pn.first].n = pn.second;
+                ECK(e, cudaEventRecord(u->consumed, e->stream));
+                return CPT_OK;
+            }
+        }
+    } else {
+        rc = launch_ops(e, dev_ops.data(), (int32_t)dev_ops.size(), &launched);
+        if (!rc) rc = stream_host_ops(e, host_ops, &launched);
+    }
+    if (rc) {
+        // a launch may have begun: the planes of the submit hold an unknown
+        // part of the ops until they are cleared
+        if (launched)
+            for (const auto &pn : n_after) e->planes[pn.first].poisoned = true;
+        return rc;
     }
     for (const auto &pn : n_after) e->planes[pn.first].n = pn.second;
     return CPT_OK;
@@ -786,6 +971,9 @@ void destroy_engine(composite_engine *e) {
     if (e->d_counter) cudaFree(e->d_counter);
     if (e->done_ev) cudaEventDestroy(e->done_ev);
     if (e->capture_stream) cudaStreamDestroy(e->capture_stream);
+    free_stage(e);
+    if (e->copy) cudaStreamDestroy(e->copy);
+    if (e->caller_ready) cudaEventDestroy(e->caller_ready);
     delete e;
 }
 
@@ -799,6 +987,9 @@ int composite_engine_default_config(composite_engine_config *cfg) try {
     cfg->slab_members = 128;
     cfg->ctas_per_sm = 5;
     cfg->schedule = CPT_SCHEDULE_PERSISTENT;
+    cfg->item_member_groups = kDefaultItemMemberGroups;
+    cfg->staging_buffers = 2;
+    cfg->staging_bytes = kDefaultStageBytes;
     return CPT_OK;
 } catch (...) {
     return cpt::abi_exception_status();
@@ -817,12 +1008,19 @@ int composite_engine_begin(composite_engine **out, const composite_engine_config
         if (cfg->ctas_per_sm) c.ctas_per_sm = cfg->ctas_per_sm;
         c.schedule = cfg->schedule;
         c.upload_stream = cfg->upload_stream;
+        if (cfg->item_member_groups) c.item_member_groups = cfg->item_member_groups;
+        if (cfg->staging_buffers) c.staging_buffers = cfg->staging_buffers;
+        if (cfg->staging_bytes) c.staging_bytes = cfg->staging_bytes;
     }
     if (c.schedule != CPT_SCHEDULE_PERSISTENT && c.schedule != CPT_SCHEDULE_GRID)
         return efail(nullptr, CPT_EINVAL, "schedule must be CPT_SCHEDULE_PERSISTENT or CPT_SCHEDULE_GRID");
     if (c.slab_members < 1 || c.slab_members > kMaxSlab) return efail(nullptr, CPT_EINVAL, "slab_members not in 1..255");
     if (c.ctas_per_sm < 1 || c.ctas_per_sm > 8) return efail(nullptr, CPT_EINVAL, "ctas_per_sm not in 1..8");
     if (c.wait_timeout_ms < 0) return efail(nullptr, CPT_EINVAL, "negative timeout");
+    if (c.item_member_groups < 16 || c.item_member_groups > 8192)
+        return efail(nullptr, CPT_EINVAL, "item_member_groups not in 16..8192");
+    if (c.staging_buffers < 2 || c.staging_buffers > 8) return efail(nullptr, CPT_EINVAL, "staging_buffers not in 2..8");
+    if (c.staging_bytes < (1ll << 20)) return efail(nullptr, CPT_EINVAL, "staging_bytes below 1 MiB");
     composite_engine *e = new composite_engine();
     e->cfg = c;
     auto setup = [&]() -> int {
@@ -970,6 +1168,9 @@ int composite_engine_capture(composite_engine *e, const composite_op *ops, int32
     int64_t items = 0, ritems = 0;
     int rc = plan_ops(e, ops, n_ops, &descs, &items, &n_after, true);
     if (rc) return rc;
+    for (int32_t i = 0; i < n_ops; ++i)
+        if (ops[i].n_members > 0 && member_kind(ops[i].members) != 0)
+            return efail(e, CPT_EINVAL, "op %d: a captured graph reads device members only", i);
     rc = plan_render(e, rops, n_rops, &rdescs, &ritems, &n_after);
     if (rc) return rc;
     rc = drain(e);
@@ -1057,14 +1258,16 @@ int composite_engine_tune(composite_engine *e, const composite_op *ops, int32_t 
     int64_t items = 0;
     int rc = plan_ops(e, ops, n_ops, &descs, &items, &n_after, true);
     if (rc) return rc;
-    static const int slabs[] = {32, 64, 128, 255};
-    // ctas_per_sm 0 stands for the grid schedule
-    static const int ctas[] = {0, 3, 4, 5};
-    cudaEvent_t a, b;
+    bool any_host = false;
+    for (int32_t i = 0; i < n_ops; ++i)
+        if (ops[i].n_members > 0 && member_kind(ops[i].members) == 1) any_host = true;
+    cudaEvent_t a = nullptr, b = nullptr;
     ECK(e, cudaEventCreate(&a));
-    ECK(e, cudaEventCreate(&b));
-    float best = 1e30f;
-    int best_slab = e->cfg.slab_members, best_ctas = e->cfg.ctas_per_sm, best_sched = e->cfg.schedule;
+    cudaError_t ce = cudaEventCreate(&b);
+    if (ce != cudaSuccess) {
+        cudaEventDestroy(a);
+        return ecuda(e, ce, "cudaEventCreate");
+    }
     auto run = [&]() -> int {
         for (const auto &pn : n_after) {
             int r = clear_plane(e, pn.first);
@@ -1072,40 +1275,78 @@ int composite_engine_tune(composite_engine *e, const composite_op *ops, int32_t 
         }
         return submit_internal(e, ops, n_ops);
     };
-    for (int s : slabs)
-        for (int c : ctas) {
-            e->cfg.slab_members = s;
-            e->cfg.schedule = c ? CPT_SCHEDULE_PERSISTENT : CPT_SCHEDULE_GRID;
-            e->cfg.ctas_per_sm = c ? c : best_ctas;
-            float t_best = 1e30f;
-            for (int r = 0; r < repeats && rc == CPT_OK; ++r) {
-                if ((rc = run())) break;             // warm and measure alike: clear + submit
-                if (cudaEventRecord(a, e->stream) != cudaSuccess) { rc = CPT_ECUDA; break; }
-                if ((rc = run())) break;
-                if (cudaEventRecord(b, e->stream) != cudaSuccess) { rc = CPT_ECUDA; break; }
-                if ((rc = ewait(e, b))) break;
-                float ms = 0;
-                cudaEventElapsedTime(&ms, a, b);
-                t_best = std::min(t_best, ms);
-            }
-            if (rc) break;
-            if (t_best < best) {
-                best = t_best;
-                best_slab = s;
-                best_sched = e->cfg.schedule;
-                if (c) best_ctas = c;
-            }
+    // Best of `repeats` timed runs (each after an untimed one) of the current
+    // configuration, in ms; < 0 on error (rc set).
+    auto time_config = [&]() -> float {
+        float t_best = 1e30f;
+        for (int r = 0; r < repeats; ++r) {
+            if ((rc = run())) return -1.f;             // warm and measure alike: clear + submit
+            if (cudaEventRecord(a, e->stream) != cudaSuccess) { rc = efail(e, CPT_ECUDA, "cudaEventRecord"); return -1.f; }
+            if ((rc = run())) return -1.f;
+            if (cudaEventRecord(b, e->stream) != cudaSuccess) { rc = efail(e, CPT_ECUDA, "cudaEventRecord"); return -1.f; }
+            if ((rc = ewait(e, b))) return -1.f;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, a, b);
+            t_best = std::min(t_best, ms);
         }
+        return t_best;
+    };
+    composite_engine_config best = e->cfg;
+    float best_ms = 1e30f;
+    auto consider = [&]() -> bool {
+        const float ms = time_config();
+        if (ms < 0) return false;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = e->cfg;
+        }
+        return true;
+    };
+    // round 1: slab depth x schedule (ctas_per_sm 0 stands for the grid schedule)
+    static const int slabs[] = {32, 64, 128, 255};
+    static const int ctas[] = {0, 3, 4, 5};
+    const int ctas_before = e->cfg.ctas_per_sm;
+    for (int sl : slabs)
+        for (int c : ctas) {
+            if (rc) break;
+            e->cfg.slab_members = sl;
+            e->cfg.schedule = c ? CPT_SCHEDULE_PERSISTENT : CPT_SCHEDULE_GRID;
+            e->cfg.ctas_per_sm = c ? c : ctas_before;
+            if (!consider()) break;
+        }
+    // round 2: the work item's tile of groups
+    static const int item_groups[] = {256, 512, 1024, 2048};
+    if (!rc) {
+        e->cfg = best;
+        for (int g : item_groups) {
+            e->cfg.item_member_groups = g;
+            if (!consider()) break;
+        }
+    }
+    // round 3: staging buffers for host members
+    static const int stage_counts[] = {2, 3, 4};
+    static const int stage_mib[] = {64, 128, 256, 512};
+    if (!rc && any_host) {
+        int64_t largest = 0;
+        for (int32_t i = 0; i < n_ops; ++i)
+            largest = std::max<int64_t>(largest, (int64_t)ops[i].row_pitch_bytes * e->planes[ops[i].plane].height);
+        e->cfg = best;
+        for (int k : stage_counts)
+            for (int mib : stage_mib) {
+                if (rc || ((int64_t)mib << 20) < largest) continue;
+                e->cfg.staging_buffers = k;
+                e->cfg.staging_bytes = (int64_t)mib << 20;
+                if (!consider()) break;
+            }
+    }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
-    e->cfg.slab_members = best_slab;
-    e->cfg.ctas_per_sm = best_ctas;
-    e->cfg.schedule = best_sched;
+    e->cfg = best;
     if (rc) return rc;
     rc = run();
     if (rc) return rc;
-    if (slab_out) *slab_out = best_slab;
-    if (ctas_out) *ctas_out = best_sched == CPT_SCHEDULE_GRID ? 0 : best_ctas;
+    if (slab_out) *slab_out = best.slab_members;
+    if (ctas_out) *ctas_out = best.schedule == CPT_SCHEDULE_GRID ? 0 : best.ctas_per_sm;
     return CPT_OK;
 } catch (...) {
     return cpt::abi_exception_status();
@@ -1115,6 +1356,14 @@ int composite_engine_get_tuning(const composite_engine *e, int32_t *slab_out, in
     if (!e) return CPT_EINVAL;
     if (slab_out) *slab_out = e->cfg.slab_members;
     if (ctas_out) *ctas_out = e->cfg.schedule == CPT_SCHEDULE_GRID ? 0 : e->cfg.ctas_per_sm;
+    return CPT_OK;
+} catch (...) {
+    return cpt::abi_exception_status();
+}
+
+int composite_engine_get_config(const composite_engine *e, composite_engine_config *cfg_out) try {
+    if (!e || !cfg_out) return CPT_EINVAL;
+    *cfg_out = e->cfg;
     return CPT_OK;
 } catch (...) {
     return cpt::abi_exception_status();

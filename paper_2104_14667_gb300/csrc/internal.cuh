@@ -114,7 +114,8 @@ bool fault_injected(const char *site);
 // is listed, -1 otherwise.  chunk_fail=K makes chunk K (from 0) of every add
 // or remove fail as if its upload had been refused, after chunks 0..K-1 were
 // queued; server_chunk_fail=K does the same to overflow chunk K of every
-// server cycle.  Each fails on the host, before that chunk's work is queued.
+// server cycle, engine_chunk_fail=K to staging chunk K of an engine submit's
+// host ops.  Each fails on the host, before that chunk's work is queued.
 int64_t fault_injected_value(const char *site);
 
 // NVTX range around a host-side phase (a call, a pipeline chunk), for

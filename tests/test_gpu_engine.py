@@ -219,3 +219,109 @@ def test_bit_packed_ops_mixed_with_byte_ops(schedule, count_bits):
         eng.sync()
         for m, p, o in items:
             check(o, m)
+
+
+def pinned_padded(m: np.ndarray, extra_rows: int = 0):
+    """Pinned host copy of uint8[n, H, W], rows padded to 16 bytes and each
+    raster followed by extra_rows rows of nonzero padding (stride > pitch*H)."""
+    n, h, w = m.shape
+    pitch = (w + 15) // 16 * 16
+    buf = torch.full((n, h + extra_rows, pitch), 255, dtype=torch.uint8).pin_memory()
+    buf[:, :h, :w] = torch.from_numpy(m)
+    return buf[:, :h, :w]
+
+
+@pytest.mark.parametrize("count_bits", [32, 16])
+@pytest.mark.parametrize("stage_mib", [1, 256])
+def test_host_ops_stream_through_staging(count_bits, stage_mib):
+    # ops on pinned host members, mixed with device ops in one submit; a 1 MiB
+    # staging buffer cuts the host rasters into many chunks that split ops
+    with binding.Engine(staging_bytes=stage_mib << 20, staging_buffers=3) as eng:
+        ops, rops, outs, kept = [], [], [], []
+        for i, (w, h, n) in enumerate([(1024, 1024, 6), (257, 131, 300), (13, 7, 5), (4096, 3, 9), (100, 37, 40)]):
+            m = synth.scramble_nonzero(synth.random_masks(80 + i, n, h, w, density=0.4), 80 + i)
+            p = eng.add_plane(w, h, count_bits)
+            half = n // 2
+            host = pinned_padded(m[:half], extra_rows=i % 2)
+            dev = padded(m[half:])
+            ops += [eng.op(p, host), eng.op(p, dev)]
+            o = outputs(w, h, count_bits)
+            outs.append(o)
+            rops.append(eng.render_op(p, *o))
+            kept.append((m, host, p))
+        eng.submit(ops)
+        # remove the host half again, then add it back, through the staging
+        eng.submit([eng.op(p, host, sign=-1) for _, host, p in kept])
+        eng.submit([eng.op(p, host) for _, host, p in kept])
+        eng.render(rops)
+        eng.sync()
+        for (m, _, p), o in zip(kept, outs):
+            assert eng.member_count(p) == m.shape[0]
+            check(o, m)
+
+
+def test_host_ops_rejections():
+    with binding.Engine() as eng:
+        p = eng.add_plane(64, 8)
+        host = pinned_padded(synth.random_masks(90, 4, 8, 64))
+        idx = torch.arange(2, dtype=torch.int32, device="cuda")
+        for bad in (eng.op(p, host, index=idx), eng.op(p, synth.random_masks(91, 2, 8, 64))):
+            with pytest.raises(binding.CompositeError) as e:
+                eng.submit([bad])
+            assert e.value.code == binding.CPT_EINVAL
+        assert eng.member_count(p) == 0
+    with binding.Engine(staging_bytes=1 << 20) as eng:
+        p = eng.add_plane(2048, 1024)      # a 2 MiB raster cannot fit a 1 MiB buffer
+        big = pinned_padded(np.ones((1, 1024, 2048), np.uint8))
+        with pytest.raises(binding.CompositeError) as e:
+            eng.submit([eng.op(p, big)])
+        assert e.value.code == binding.CPT_EINVAL and "staging" in str(e.value)
+
+
+def test_tuner_with_host_ops_reports_every_dimension():
+    with binding.Engine() as eng:
+        data, ops = [], []
+        for i, (w, h, n) in enumerate([(512, 512, 64), (256, 1024, 40)]):
+            m = synth.random_masks(95 + i, n, h, w)
+            p = eng.add_plane(w, h)
+            host = pinned_padded(m)
+            data.append((m, p))
+            ops.append(eng.op(p, host))
+        slab, ctas = eng.tune(ops, repeats=1)
+        cfg = eng.config()
+        assert cfg["slab_members"] == slab and cfg["item_member_groups"] in (256, 512, 1024, 2048)
+        assert cfg["staging_buffers"] in (2, 3, 4) and cfg["staging_bytes"] in [m << 20 for m in (64, 128, 256, 512)]
+        outs = [outputs(512, 512), outputs(256, 1024)]
+        eng.render([eng.render_op(p, *o) for (_, p), o in zip(data, outs)])
+        eng.sync()
+        for (m, _), o in zip(data, outs):
+            check(o, m)
+
+
+def test_host_chunk_failure_poisons_the_submit_planes(monkeypatch):
+    with binding.Engine(staging_bytes=1 << 20) as eng:
+        m = synth.random_masks(97, 8, 256, 1024)          # 256 KiB rasters: 4 per chunk
+        p = eng.add_plane(1024, 256)
+        q = eng.add_plane(64, 8)
+        other = synth.random_masks(98, 3, 8, 64)
+        eng.submit([eng.op(q, padded(other))])
+        host = pinned_padded(m)
+        monkeypatch.setenv("CPT_FAULT_INJECT", "engine_chunk_fail=1")
+        with pytest.raises(binding.CompositeError) as e:
+            eng.submit([eng.op(p, host)])
+        assert e.value.code == binding.CPT_ECUDA
+        monkeypatch.delenv("CPT_FAULT_INJECT")
+        assert eng.member_count(p) == 0
+        with pytest.raises(binding.CompositeError) as e:
+            eng.submit([eng.op(p, host)])
+        assert e.value.code == binding.CPT_ESTATE
+        with pytest.raises(binding.CompositeError) as e:
+            eng.render([eng.render_op(p, *outputs(1024, 256))])
+        assert e.value.code == binding.CPT_ESTATE
+        eng.clear(p)
+        eng.submit([eng.op(p, host)])
+        o, oq = outputs(1024, 256), outputs(64, 8)
+        eng.render([eng.render_op(p, *o), eng.render_op(q, *oq)])
+        eng.sync()
+    check(o, m)
+    check(oq, other)

@@ -51,7 +51,7 @@ def parse_args():
     p.add_argument("--width", type=int, default=4096)
     p.add_argument("--height", type=int, default=4096)
     p.add_argument("--members", type=int, default=1024)
-    p.add_argument("--chunk", type=int, default=32)
+    p.add_argument("--chunk", type=int, default=0, help="members per chunk; 0 = the library's automatic depth")
     p.add_argument("--staging", type=int, default=2)
     p.add_argument("--read-path", default="linear", choices=["linear", "texture", "tma"])
     p.add_argument("--seed", type=int, default=2)
@@ -499,6 +499,7 @@ def run_ours(args):
     # ---- e2e: pinned host ensemble through the C ABI -----------------------
     e2e = None
     link = None
+    e2e_launches = 0
     if not args.no_e2e:
         host, host_handle = pinned_host_buffer(torch, (N, H, W))
         host.copy_(dev_masks)
@@ -548,10 +549,14 @@ def run_ours(args):
         kernels = [(float(a), float(b)) for k, a, b in rec if int(k) != 0]
         overlap = metrics.overlap_fraction(copies, kernels)
         copy_busy = sum(b - a for a, b in copies)
+        n_chunks = sum(1 for k, _, _ in rec if int(k) == 2)
+        chunk_used = -(-N // max(1, n_chunks))
+        e2e_launches = 2 if use_direct else n_chunks + 1     # accumulate launches + the render
         e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": N * P,
                "d2h_bytes_per_step": 5 * P, "ms_per_step": e2e_ms / args.steps,
                "mode": "host_read (kernel loads pinned host memory over the link)" if use_direct
-               else f"staged ({args.staging} staging buffers of {args.chunk} members, copy stream + events)"}
+               else f"staged ({args.staging} staging buffers, chunks of {chunk_used} members"
+                    f"{' (automatic depth)' if args.chunk == 0 else ''}, copy stream + events)"}
         link = {"h2d_gbs": h2d_gbs, "link_peak_gbs": peak_link, "link_frac": h2d_gbs / peak_link,
                 "link_peak_how": "best of 5 pinned 1 GiB cudaMemcpyAsync host->device",
                 "staged_h2d_gbs": N * P / (staged_ms * 1e-3 / args.steps) / 1e9,
@@ -573,7 +578,7 @@ def run_ours(args):
 
     if rank == 0:
         launches_per_step = 2
-        launches_e2e = -(-N // args.chunk) + 1
+        launches_e2e = e2e_launches if e2e else 0
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
@@ -657,7 +662,7 @@ def sweep_readpath(args, torch, binding, device, stream):
                                 ("tma", 64, "kernel"), ("tma", 128, "kernel"), ("tma", 256, "kernel")):
             if path not in args.paths:
                 continue
-            cfg = dict(read_path=path, chunk_members=args.chunk, staging_buffers=args.staging,
+            cfg = dict(read_path=path, chunk_members=args.chunk or 32, staging_buffers=args.staging,
                        mode=mode, stream=stream.cuda_stream, tma_box_bytes=box, layout_converter=conv)
             with binding.Composite(W, H, **cfg) as comp:
                 def step():
@@ -681,7 +686,7 @@ def sweep_readpath(args, torch, binding, device, stream):
             line = {"sweep": "readpath", "mode": mode, "read_path": path, "tma_box_bytes": box or None,
                     "layout_converter": conv if path == "texture" else None,
                     "width": W, "height": H,
-                    "members": N, "chunk_members": args.chunk, "ms_per_pass": ms,
+                    "members": N, "chunk_members": args.chunk or 32, "ms_per_pass": ms,
                     "member_px_per_s": N * P / (ms * 1e-3), "kernel_launches": launches,
                     "kernel_busy_ms": kernel_ms, "conversion_busy_ms": convert_ms,
                     "kernel_alg_gbs": kernel_bytes / (kernel_ms * 1e-3) / 1e9,
@@ -732,15 +737,17 @@ def sweep_streaming(args, torch, binding, device, stream, sides=None, counts=Non
     sides = sides or [512, 1024, 2048, 4096, 8192]
     counts = counts or [16, 64, 256, 1024, 4096]
     if plan is None:
-        plan = [(s, n, c, args.staging) for c in sorted({args.chunk, 0}, reverse=True) for s in sides for n in counts]
+        plan = [(s, n, c, args.staging) for c in sorted({args.chunk or 32, 0}, reverse=True) for s in sides for n in counts]
         for c in (chunks or []):
             plan.append((4096, 1024, c, args.staging))
         for k in (stagings or []):
-            plan.append((4096, 1024, args.chunk, k))
+            plan.append((4096, 1024, args.chunk or 32, k))
         for path in ("texture", "tma"):
-            for c in sorted({args.chunk, 0}, reverse=True):
+            for c in sorted({args.chunk or 32, 0}, reverse=True):
                 for k in (2, 3):
                     plan.append((4096, 1024, c, k, path))
+        for side in (1024, 4096):
+            plan.append((side, 1024, 0, 2, "host_read"))
     plan = [tuple(e) + ("linear",) * (5 - len(e)) for e in plan]
     counts = sorted({e[1] for e in plan})
     pools = {}
@@ -771,7 +778,9 @@ def sweep_streaming(args, torch, binding, device, stream, sides=None, counts=Non
                 comp.add(host[:take])
                 done += take
 
-        cfg = dict(chunk_members=chunk, staging_buffers=k, stream=stream.cuda_stream, read_path=path)
+        # "host_read": the linear kernel loads the pinned rasters over the link itself
+        cfg = dict(chunk_members=chunk, staging_buffers=k, stream=stream.cuda_stream,
+                   read_path="linear" if path == "host_read" else path, host_read=path == "host_read")
         with binding.Composite(side, side, **cfg) as comp:
             for _ in range(args.warmup):
                 comp.clear()
@@ -1362,7 +1371,8 @@ def run_sweep(args):
         sweep_batched(args, torch, binding, device, stream)
     elif args.sweep == "tiny":
         sweep_streaming(args, torch, binding, device, stream,
-                        plan=[(1024, 16, c, k) for c in (16, 1, 2, 4, 8) for k in (2, 1)])
+                        plan=[(1024, 16, c, k) for c in (16, 1, 2, 4, 8) for k in (2, 1)] +
+                             [(1024, 16, 0, 2), (1024, 16, 16, 2, "host_read")])
         if not args.no_cpu_baseline:
             cpu_baseline_line(args, "tiny", 1, 1024, 1024, 16, "count")
 

@@ -82,6 +82,19 @@ enum {
                                  unaligned sources fall back to the copy                */
 };
 
+/* How pageable host rasters reach the device (step a2). */
+enum {
+    CPT_INGEST_AUTO = 0,      /* register batches of at least 64 MiB, copy smaller ones
+                                 through the ring                                         */
+    CPT_INGEST_RING = 1,      /* copy into the library's pinned ring on host threads, then
+                                 upload from the ring                                    */
+    CPT_INGEST_REGISTER = 2   /* page-lock the caller's batch in place for the call
+                                 (cudaHostRegister), upload straight from it, wait for the
+                                 uploads and unregister it before returning; a batch the
+                                 driver will not register (already registered, say) goes
+                                 through the ring                                        */
+};
+
 enum {
     CPT_MODE_COUNT = 0,       /* uint8 masks -> per-pixel member counts      */
     CPT_MODE_MEAN_DEPTH = 1   /* float32 depths -> per-pixel mean (float32)   */
@@ -138,6 +151,8 @@ typedef struct composite_config {
                                    thread alone; 0 = min(16, the host's hardware threads);
                                    at most 64.  The threads start at the first pageable
                                    add and end with the context.                          */
+    int32_t pageable_ingest;    /* CPT_INGEST_*; default CPT_INGEST_AUTO.  Either way the
+                                   caller may reuse a pageable batch once the call returns */
 } composite_config;
 
 /* Fills *cfg with the defaults listed above.  CPT_EINVAL if cfg is NULL. */

@@ -58,6 +58,7 @@ class Config(ctypes.Structure):
         ("mask_format", ctypes.c_int32),
         ("layout_converter", ctypes.c_int32),
         ("ingest_threads", ctypes.c_int32),
+        ("pageable_ingest", ctypes.c_int32),
     ]
 
 
@@ -335,10 +336,13 @@ def caller_stream():
     return None
 
 
+PAGEABLE_INGEST = {"auto": 0, "ring": 1, "register": 2}
+
+
 def make_config(read_path="linear", staging_buffers=2, chunk_members=0, count_bits=16,
                 mode="count", trace=False, pinned_ring_bytes=0, stream=None,
                 wait_timeout_ms=0, host_read=False, tma_box_bytes=0, mask_format="bytes",
-                layout_converter="kernel", ingest_threads=0) -> Config:
+                layout_converter="kernel", ingest_threads=0, pageable_ingest="auto") -> Config:
     cfg = composite_default_config()
     cfg.read_path = READ_PATHS[read_path] if isinstance(read_path, str) else int(read_path)
     cfg.staging_buffers = staging_buffers
@@ -356,6 +360,8 @@ def make_config(read_path="linear", staging_buffers=2, chunk_members=0, count_bi
     cfg.layout_converter = {"copy": CPT_CONVERT_COPY, "kernel": CPT_CONVERT_KERNEL}[layout_converter] \
         if isinstance(layout_converter, str) else int(layout_converter)
     cfg.ingest_threads = ingest_threads
+    cfg.pageable_ingest = PAGEABLE_INGEST[pageable_ingest] if isinstance(pageable_ingest, str) \
+        else int(pageable_ingest)
     return cfg
 
 

@@ -104,11 +104,12 @@ void set_thread_error(const char *message);
 
 // Host-side fault injection for tests: the environment variable
 // CPT_FAULT_INJECT holds a comma-separated list of sites -- staging_alloc,
-// pinned_ring, ingest_threads, engine_plane, server_stage -- and a listed site
-// behaves as if its host-side request (a device or pinned allocation, the
-// ingest threads) had been refused; engine_submit makes every engine submit
-// fail after its descriptors are uploaded and before its launch.  Nothing on
-// the device is affected.
+// pinned_ring, ingest_threads, host_register, engine_plane, server_stage --
+// and a listed site behaves as if its host-side request (a device or pinned
+// allocation, the ingest threads, the page-locking of a pageable batch) had
+// been refused; engine_submit makes every engine submit fail after its
+// descriptors are uploaded and before its launch.  Nothing on the device is
+// affected.
 bool fault_injected(const char *site);
 // Indexed sites in the same list, written "site=K": returns K when the site
 // is listed, -1 otherwise.  chunk_fail=K makes chunk K (from 0) of every add

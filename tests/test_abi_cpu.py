@@ -48,7 +48,8 @@ def test_begin_rejects_empty_raster(lib, w, h):
                                          ("host_read", 2), ("tma_box_bytes", 32),
                                          ("tma_box_bytes", 512), ("mask_format", 2),
                                          ("layout_converter", 2), ("ingest_threads", -1),
-                                         ("ingest_threads", 65)])
+                                         ("ingest_threads", 65), ("pageable_ingest", 3),
+                                         ("pageable_ingest", -1)])
 def test_begin_rejects_bad_config(lib, field, value):
     cfg = binding.composite_default_config()
     setattr(cfg, field, value)

@@ -461,10 +461,41 @@ def test_pageable_ingest_threads(threads, w, h, n):
     m = synth.scramble_nonzero(synth.random_masks(160 + w + threads, n, h, w), 160)
     big = np.zeros((n, h, w + 9), np.uint8)
     big[:, :, :w] = m
-    with binding.Composite(w, h, ingest_threads=threads, chunk_members=16) as comp:
+    with binding.Composite(w, h, ingest_threads=threads, chunk_members=16, pageable_ingest="ring") as comp:
         comp.add(m)
         comp.remove(big[: n // 3, :, :w])
         comp.add(big[: n // 3, :, :w])
+        check_counts(comp, m)
+
+
+@pytest.mark.parametrize("mode", ["register", "auto"])
+@pytest.mark.parametrize("path", PATHS)
+def test_pageable_batches_registered_for_the_call(mode, path):
+    # register: every pageable batch is page-locked in place for the call;
+    # auto: batches of 64 MiB and more (here 80 rasters of 1 MiB) are, and
+    # smaller ones take the ring.  The caller may overwrite a batch as soon
+    # as the call returns, so the call must not return before its uploads.
+    w, h, n = 1024, 1024, 80
+    m = synth.scramble_nonzero(synth.random_masks(170, n, h, w, density=0.3), 170)
+    strided = np.zeros((n, h, w + 32), np.uint8)
+    strided[:, :, :w] = m
+    with binding.Composite(w, h, read_path=path, pageable_ingest=mode) as comp:
+        batch = m.copy()
+        comp.add(batch)
+        batch[:] = 0                      # reused right after the call
+        comp.remove(strided[:10, :, :w])  # a strided view, registered or ringed
+        comp.add(m[:10])                  # small: the ring in auto mode
+        check_counts(comp, m)
+
+
+def test_registration_refused_falls_back_to_the_ring(monkeypatch):
+    # host_register: the driver's page-locking refused, as for a batch that
+    # overlaps memory registered elsewhere
+    w, h, n = 512, 256, 20
+    m = synth.random_masks(171, n, h, w)
+    monkeypatch.setenv("CPT_FAULT_INJECT", "host_register")
+    with binding.Composite(w, h, pageable_ingest="register") as comp:
+        comp.add(m)
         check_counts(comp, m)
 
 

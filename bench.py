@@ -917,7 +917,8 @@ def sweep_batched_streamed(args, torch, binding, device, stream, reqs, data, mem
     chunk depth), against one engine submit of 64 host ops streamed through
     the engine's staging buffers, after the tuner picked slab, schedule, item
     size, staging count and buffer size; one render per request / one render
-    launch.  Wall time per pass with CUDA events; outputs compared."""
+    launch.  Passes of the two forms alternate; median pass time with CUDA
+    events; outputs compared."""
     total = sum(int(d.numel()) for d in data)
     flat, handle = pinned_host_buffer(torch, (total,))
     hosts, off = [], 0
@@ -941,10 +942,6 @@ def sweep_batched_streamed(args, torch, binding, device, stream, reqs, data, mem
             ctx.add(src)
             ctx.render(bucket_out=b, rgba_out=c)
 
-    ms_plain = _timed(torch, stream, plain_all, args.steps, args.warmup)
-    for ctx in ctxs:
-        ctx.sync()
-        ctx.close()
     eng = binding.Engine(stream=stream.cuda_stream)
     planes = [eng.add_plane(w, h, args.engine_count_bits) for w, h, _ in reqs]
     ops = [eng.op(p, src) for p, src in zip(planes, hosts)]
@@ -960,15 +957,28 @@ def sweep_batched_streamed(args, torch, binding, device, stream, reqs, data, mem
         eng.submit(ops)
         eng.render(rops)
 
-    ms_batch = _timed(torch, stream, batched, args.steps, args.warmup)
+    # The two forms alternate pass by pass, so that a dip of the host link
+    # (these shared machines have them) falls on both alike; medians reported.
+    plain_ms, batch_ms = [], []
+    for i in range(args.warmup + args.steps):
+        a = _timed(torch, stream, plain_all, 1, 0)
+        b = _timed(torch, stream, batched, 1, 0)
+        if i >= args.warmup:
+            plain_ms.append(a)
+            batch_ms.append(b)
+    ms_plain, ms_batch = float(np.median(plain_ms)), float(np.median(batch_ms))
     eng.sync()
     eng.close()
+    for ctx in ctxs:
+        ctx.sync()
+        ctx.close()
     same = all(torch.equal(a, b) and torch.equal(c, d) for (a, c), (b, d) in zip(out_plain, out_batch))
     peak = link_peak_gbs(torch, device)
     gbs = lambda ms: member_px / (ms * 1e-3) / 1e9
     print(json.dumps({
         "sweep": "batched_streamed", "requests": len(reqs), "member_px": member_px,
         "plain_sequential_ms": ms_plain, "batched_ms": ms_batch, "speedup": ms_plain / ms_batch,
+        "plain_ms_each": plain_ms, "batched_ms_each": batch_ms,
         "plain_composites_per_s": len(reqs) / (ms_plain * 1e-3),
         "batched_composites_per_s": len(reqs) / (ms_batch * 1e-3),
         "plain_h2d_gbs": gbs(ms_plain), "batched_h2d_gbs": gbs(ms_batch), "link_peak_gbs": peak,
@@ -993,10 +1003,11 @@ def sweep_ingest(args, torch, binding, device, stream):
     del dev
     torch.cuda.empty_cache()
     peak = link_peak_gbs(torch, device)
-    for kind, data, threads in (("pinned", pinned, 0), ("pageable", pageable, 1), ("pageable", pageable, 4),
-                                ("pageable", pageable, 8), ("pageable", pageable, 0)):
+    for kind, data, threads, mode in (("pinned", pinned, 0, "auto"), ("pageable", pageable, 1, "ring"),
+                                      ("pageable", pageable, 4, "ring"), ("pageable", pageable, 8, "ring"),
+                                      ("pageable", pageable, 0, "ring"), ("pageable", pageable, 0, "auto")):
         with binding.Composite(W, H, chunk_members=args.chunk, staging_buffers=args.staging,
-                               stream=stream.cuda_stream, ingest_threads=threads) as comp:
+                               stream=stream.cuda_stream, ingest_threads=threads, pageable_ingest=mode) as comp:
             def step():
                 comp.clear()
                 comp.add(data)
@@ -1010,6 +1021,7 @@ def sweep_ingest(args, torch, binding, device, stream):
             exact = identity_rows_exact(comp, ens.terrain, ens.levels)
         gbs = N * W * H / (ms * 1e-3) / 1e9
         print(json.dumps({"sweep": "ingest", "input": kind, "ingest_threads": threads or "default",
+                          "pageable_ingest": mode if kind == "pageable" else None,
                           "width": W, "height": H, "members": N,
                           "chunk_members": args.chunk, "staging_buffers": args.staging, "ms_per_pass": ms,
                           "member_px_per_s": N * W * H / (ms * 1e-3), "gbs": gbs, "link_peak_gbs": peak,
@@ -1038,9 +1050,9 @@ def sweep_ingest(args, torch, binding, device, stream):
                           "piece_bytes": piece, "bytes": total, "ms_per_pass": ms,
                           "gbs": total / (ms * 1e-3) / 1e9}), flush=True)
 
-    # Alternative to the ring: register the pageable batch with the driver for
-    # the call (page-locking it in place), upload it as pinned memory, and
-    # unregister it afterwards.
+    # The same by hand, outside the library: register the pageable batch with
+    # the driver for the call (page-locking it in place), upload it as pinned
+    # memory, and unregister it afterwards.
     cudart = torch.cuda.cudart()
     with binding.Composite(W, H, chunk_members=args.chunk, staging_buffers=args.staging,
                            stream=stream.cuda_stream) as comp:

@@ -545,14 +545,15 @@ Lut make_lut(const uint8_t *rgba) {
 // that small uploads follow the caller's own uploads in order instead of
 // waiting behind them on a copy engine); returns the slot.  The caller
 // records slot->consumed on the engine stream after the launch that reads it.
-int upload(composite_engine *e, Upload *ring, int *idx, const void *src, size_t bytes, Upload **slot) {
+int upload(composite_engine *e, Upload *ring, int *idx, const void *src, size_t bytes, Upload **slot,
+           cudaStream_t on = nullptr) {
     Upload &u = ring[*idx];
     *idx = (*idx + 1) % kUploadRing;
     if (u.used) {
         int rc = ewait(e, u.done);
         if (rc) return rc;
     }
-    cudaStream_t us = e->cfg.upload_stream ? static_cast<cudaStream_t>(e->cfg.upload_stream) : e->stream;
+    cudaStream_t us = on ? on : e->cfg.upload_stream ? static_cast<cudaStream_t>(e->cfg.upload_stream) : e->stream;
     if (u.cap < bytes) {
         if (u.d) cudaFree(u.d);
         if (u.h) cudaFreeHost(u.h);
@@ -795,14 +796,17 @@ int ensure_stage(composite_engine *e) {
 }
 
 // Launches the accumulate kernel over ops (already validated as a whole).
-int launch_ops(composite_engine *e, const composite_op *ops, int32_t n_ops, bool *launched) {
+// desc_stream: where the descriptors are uploaded (NULL = the usual upload
+// stream); the launch waits for them either way.
+int launch_ops(composite_engine *e, const composite_op *ops, int32_t n_ops, bool *launched,
+               cudaStream_t desc_stream = nullptr) {
     std::vector<OpDesc> descs;
     std::vector<std::pair<int32_t, int64_t>> n_after;
     int64_t items = 0;
     int rc = plan_ops(e, ops, n_ops, &descs, &items, &n_after, false, false);
     if (rc || items == 0) return rc;
     Upload *u = nullptr;
-    rc = upload(e, e->up_ops, &e->up_i, descs.data(), descs.size() * sizeof(OpDesc), &u);
+    rc = upload(e, e->up_ops, &e->up_i, descs.data(), descs.size() * sizeof(OpDesc), &u, desc_stream);
     if (rc) return rc;
     if (cpt::fault_injected("engine_submit")) return efail(e, CPT_ECUDA, "submit refused before its launch (injected)");
     *launched = true;   // from here on the launch may have begun
@@ -858,7 +862,10 @@ int stream_host_ops(composite_engine *e, const std::vector<composite_op> &hops, 
         }
         ECK(e, cudaEventRecord(slot.ready, e->copy));
         ECK(e, cudaStreamWaitEvent(e->stream, slot.ready, 0));
-        int r = launch_ops(e, cops.data(), (int32_t)cops.size(), launched);
+        // the chunk's descriptors follow its rasters on the copy stream: on the
+        // engine stream they would queue on a copy engine behind the next
+        // chunk's rasters, and the fold would wait one upload longer
+        int r = launch_ops(e, cops.data(), (int32_t)cops.size(), launched, e->copy);
         if (r) return r;
         ECK(e, cudaEventRecord(slot.consumed, e->stream));
         slot.used = true;

@@ -157,3 +157,25 @@ def test_bench_identity_check_accepts_exact_and_rejects_off_by_one():
     assert not bench.identity_rows_exact(Fake(off), ens.terrain, ens.levels)
     cycled = oracle.count(np.concatenate([masks, masks[:4]]))
     assert bench.identity_rows_exact(Fake(cycled), ens.terrain, [ens.levels[m % 9] for m in range(13)])
+
+
+def test_ncu_traffic_record_scales_member_bytes_only(tmp_path):
+    # the summariser reads ncu's CSV log (one row per metric) and scales a
+    # small capture to the full workload: member bytes grow with the members,
+    # the plane's bytes do not
+    from paper_2104_14667_gb300 import ncu_traffic
+    head = '"ID","Process ID","Process Name","Host Name","Kernel Name","Context","Stream",' \
+           '"Block Size","Grid Size","Device","CC","Section Name","Metric Name","Metric Unit","Metric Value"\n'
+    rows = [("dram__bytes_read.sum", "byte", "1,000,000"), ("dram__bytes_write.sum", "Kbyte", "20"),
+            ("gpu__time_duration.sum", "ns", "5000")]
+    body = "".join(f'"0","1","p","h","void count_linear_kernel<unsigned short>(X)","1","13","(256, 1, 1)",'
+                   f'"(64, 1, 1)","0","10.3","Command line profiler metrics","{m}","{u}","{v}"\n' for m, u, v in rows)
+    other = '"1","1","p","h","render_counts_vec_kernel","1","13","(256, 1, 1)","(64, 1, 1)","0","10.3",' \
+            '"Command line profiler metrics","dram__bytes_read.sum","byte","7"\n'
+    path = tmp_path / "m.csv"
+    path.write_text("==PROF== Connected\n" + head + body + other)
+    rec = ncu_traffic.summarize(str(path), "count_linear", 100, 10, captured_members=4, members=64, command="c")
+    assert rec["captured_dram_bytes"] == 1_000_000 + 20_000
+    assert rec["captured_duration_us"] == 5.0
+    assert rec["dram_bytes_per_launch"] == 1_020_000 - 4 * 1000 + 64 * 1000
+    assert rec["workload"] == "100x10x64" and len(rec["kernel_source_sha256_16"]) == 16

@@ -885,8 +885,7 @@ def sweep_batched(args, torch, binding, device, stream):
     same = all(torch.equal(a, b) and torch.equal(c, d) for (a, c), (b, d) in zip(out_plain, out_batch))
 
     def direct():
-        for p in planes:
-            eng.clear(p)
+        eng.clear_many(planes)
         eng.submit(ops)
         eng.render(rops)
 
@@ -952,8 +951,7 @@ def sweep_batched_streamed(args, torch, binding, device, stream, reqs, data, mem
     cfg = eng.config()
 
     def batched():
-        for p in planes:
-            eng.clear(p)
+        eng.clear_many(planes)
         eng.submit(ops)
         eng.render(rops)
 

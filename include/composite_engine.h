@@ -119,6 +119,11 @@ int composite_engine_free_plane(composite_engine *eng, int32_t plane);
  * failed submit's mark cleared). */
 int composite_engine_clear(composite_engine *eng, int32_t plane);
 
+/* Queues a clear of every listed plane (ids may repeat) in ONE launch, as
+ * composite_engine_clear does for one: counts 0, N = 0, underflow state and
+ * failure marks cleared.  CPT_EINVAL, nothing queued, for an unknown plane. */
+int composite_engine_clear_many(composite_engine *eng, const int32_t *planes, int32_t n_planes);
+
 /* Queues every op in one persistent accumulate launch.  Validates all ops on
  * the host first (CPT_EINVAL and nothing queued if one is bad: unknown plane,
  * sign not +-1, N of a plane would go negative or above its count type's
@@ -146,8 +151,9 @@ int composite_engine_member_count(const composite_engine *eng, int32_t plane, in
 int composite_engine_sync(composite_engine *eng, int32_t *bad_plane_out);
 
 /* Captures "clear every target plane, submit ops, render rops" as a CUDA
- * graph held by the engine (replacing any earlier one); the ops' member
- * sets, index lists and outputs are fixed by the capture.  Does not run it.
+ * graph held by the engine (replacing any earlier one): three kernel nodes,
+ * the clear of all target planes in one of them.  The ops' member sets,
+ * index lists and outputs are fixed by the capture.  Does not run it.
  * Device members only (CPT_EINVAL for an op on host memory). */
 int composite_engine_capture(composite_engine *eng, const composite_op *ops, int32_t n_ops,
                              const composite_render_op *rops, int32_t n_rops, const uint8_t *lut_rgba);

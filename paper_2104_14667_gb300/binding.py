@@ -512,6 +512,7 @@ def _engine_lib():
             "composite_engine_add_plane_bits": (ctypes.c_int, [vp, i32, i32, i32, p32]),
             "composite_engine_free_plane": (ctypes.c_int, [vp, i32]),
             "composite_engine_clear": (ctypes.c_int, [vp, i32]),
+            "composite_engine_clear_many": (ctypes.c_int, [vp, p32, i32]),
             "composite_engine_submit": (ctypes.c_int, [vp, ctypes.POINTER(Op), i32]),
             "composite_engine_render": (ctypes.c_int, [vp, ctypes.POINTER(RenderOp), i32, vp]),
             "composite_engine_member_count": (ctypes.c_int, [vp, i32, p64]),
@@ -582,6 +583,11 @@ class Engine:
 
     def clear(self, plane: int):
         _echeck(self.lib, self.h, self.lib.composite_engine_clear(self.h, plane))
+
+    def clear_many(self, planes):
+        """Clears every listed plane in one launch."""
+        arr = (ctypes.c_int32 * len(planes))(*planes)
+        _echeck(self.lib, self.h, self.lib.composite_engine_clear_many(self.h, arr, len(planes)))
 
     def op(self, plane: int, members, sign: int = 1, index=None, mask_format: str = "bytes") -> Op:
         """An op from a tensor of masks [n, H, W] (bit-packed: [n, H,

@@ -79,7 +79,19 @@ struct RenderDesc {
     cpt::ClassDivisor div; // floor(255 c / n_members) by multiplication
 };
 
+// One plane of a batched clear: its bytes as 16-byte words, in items of
+// 32 lanes x kClearWords words.
+struct ClearDesc {
+    uint4 *data;
+    int64_t words;
+    int64_t item_start;
+    int32_t plane_id;
+    int32_t pad;
+};
+
 constexpr int kSmemStarts = 2048;      // ops whose first items fit in shared memory
+constexpr int kClearWords = 8;         // 16-byte words per lane per clear item
+constexpr int kClearCtasPerSm = 4;
 constexpr int kRenderGroups = 2;       // 16-pixel groups per lane per render item
 constexpr int kRenderCtasPerSm = 3;    // render launch: CTAs per SM, grid-stride over items
 
@@ -312,6 +324,31 @@ engine_accumulate_grid_kernel(const OpDesc *ops, int n_ops, uint32_t n_items, in
     run_item(ops[find_desc(ops, n_ops, item)], item, lane, s_index[threadIdx.x >> 5], flags);
 }
 
+// Clear of many planes in one launch (counts to zero, the planes' underflow
+// flags too): warp-level items (plane, 32 x kClearWords words) dealt round
+// robin.  A CUDA graph that clears its planes this way has one node for all
+// of them instead of two memset nodes per plane, which run one after another.
+__global__ void __launch_bounds__(kThreads)
+engine_clear_kernel(const ClearDesc *ops, int n_ops, uint32_t n_items, int *flags) {
+    __shared__ uint32_t s_starts[kSmemStarts];
+    load_starts(ops, n_ops, s_starts);
+    __syncthreads();
+    if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i < n_ops; i += blockDim.x) flags[ops[i].plane_id] = 0;
+    const int lane = threadIdx.x & 31;
+    const uint32_t warps = gridDim.x * (kThreads / 32);
+    const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+    for (uint32_t item = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5); item < n_items; item += warps) {
+        const ClearDesc &op = ops[find_op(ops, n_ops, s_starts, item)];
+        const int64_t w0 = (int64_t)(item - (uint32_t)op.item_start) * (32 * kClearWords) + lane;
+#pragma unroll
+        for (int k = 0; k < kClearWords; ++k) {
+            const int64_t wi = w0 + 32 * k;
+            if (wi < op.words) op.data[wi] = zero;
+        }
+    }
+}
+
 // Render: warp-level items (render op, chunk of 32 x kRenderGroups 16-pixel
 // groups) dealt round robin to every warp of the launch -- items are all the
 // same size, so no counter is needed -- and a lane loads all its groups
@@ -469,6 +506,7 @@ struct composite_engine {
     cudaGraphExec_t graph_exec = nullptr;
     void *graph_ops = nullptr;
     void *graph_rops = nullptr;
+    void *graph_clears = nullptr;
     uint32_t *graph_counters = nullptr;
     std::vector<std::pair<int32_t, int64_t>> graph_n;   // plane -> N after a replay
     std::vector<int32_t> graph_planes;                  // every plane the graph touches
@@ -747,6 +785,61 @@ int clear_plane(composite_engine *e, int32_t p) {
     return CPT_OK;
 }
 
+// Descriptors of one clear launch over the listed planes (each once).
+int plan_clears(composite_engine *e, const int32_t *planes, int32_t n, std::vector<ClearDesc> *descs,
+                int64_t *n_items) {
+    if (n < 0 || (n > 0 && !planes)) return efail(e, CPT_EINVAL, "bad plane list");
+    descs->clear();
+    std::vector<char> seen(e->planes.size(), 0);
+    int64_t items = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        const int32_t p = planes[i];
+        if (!plane_ok(e, p)) return efail(e, CPT_EINVAL, "clear %d: no plane %d", i, p);
+        if (seen[p]) continue;
+        seen[p] = 1;
+        const PlaneRec &r = e->planes[p];
+        ClearDesc d{};
+        d.data = reinterpret_cast<uint4 *>(r.data);
+        d.words = (int64_t)(r.bytes() / 16);   // plane rows are whole 16-pixel groups
+        d.item_start = items;
+        d.plane_id = p;
+        items += (d.words + 32 * kClearWords - 1) / (32 * kClearWords);
+        descs->push_back(d);
+    }
+    if (items >= (int64_t)1 << 31) return efail(e, CPT_EINVAL, "too many clear items");
+    *n_items = items;
+    return CPT_OK;
+}
+
+int launch_clear(composite_engine *e, const void *d_ops, int n_ops, int64_t n_items) {
+    const int64_t ctas = std::min<int64_t>((int64_t)e->caps.num_sms * kClearCtasPerSm,
+                                           (n_items + kThreads / 32 - 1) / (kThreads / 32));
+    engine_clear_kernel<<<(unsigned)std::max<int64_t>(1, ctas), kThreads, 0, e->stream>>>(
+        static_cast<const ClearDesc *>(d_ops), n_ops, (uint32_t)n_items, e->d_flags);
+    ECK(e, cudaGetLastError());
+    return CPT_OK;
+}
+
+// Clears the listed planes in one launch (their counts, N and underflow and
+// failure marks).
+int clear_many(composite_engine *e, const int32_t *planes, int32_t n) {
+    std::vector<ClearDesc> descs;
+    int64_t items = 0;
+    int rc = plan_clears(e, planes, n, &descs, &items);
+    if (rc || descs.empty()) return rc;
+    Upload *u = nullptr;
+    rc = upload(e, e->up_render, &e->rup_i, descs.data(), descs.size() * sizeof(ClearDesc), &u);
+    if (rc) return rc;
+    rc = launch_clear(e, u->d, (int)descs.size(), items);
+    if (rc) return rc;
+    ECK(e, cudaEventRecord(u->consumed, e->stream));
+    for (const ClearDesc &d : descs) {
+        e->planes[d.plane_id].n = 0;
+        e->planes[d.plane_id].poisoned = false;
+    }
+    return CPT_OK;
+}
+
 // Memory kind of an op's members: 1 = pinned host, 0 = device, -1 = neither.
 int member_kind(const void *p) {
     cudaPointerAttributes a;
@@ -953,10 +1046,11 @@ void destroy_graph(composite_engine *e) {
     if (e->graph) cudaGraphDestroy(e->graph);
     if (e->graph_ops) cudaFree(e->graph_ops);
     if (e->graph_rops) cudaFree(e->graph_rops);
+    if (e->graph_clears) cudaFree(e->graph_clears);
     if (e->graph_counters) cudaFree(e->graph_counters);
     e->graph_exec = nullptr;
     e->graph = nullptr;
-    e->graph_ops = e->graph_rops = nullptr;
+    e->graph_ops = e->graph_rops = e->graph_clears = nullptr;
     e->graph_counters = nullptr;
     e->graph_n.clear();
     e->graph_planes.clear();
@@ -1112,6 +1206,14 @@ int composite_engine_clear(composite_engine *e, int32_t plane) try {
     return cpt::abi_exception_status();
 }
 
+int composite_engine_clear_many(composite_engine *e, const int32_t *planes, int32_t n_planes) try {
+    if (!e) return CPT_EINVAL;
+    e->err.clear();
+    return clear_many(e, planes, n_planes);
+} catch (...) {
+    return cpt::abi_exception_status();
+}
+
 int composite_engine_submit(composite_engine *e, const composite_op *ops, int32_t n_ops) try {
     if (!e) return CPT_EINVAL;
     e->err.clear();
@@ -1180,10 +1282,20 @@ int composite_engine_capture(composite_engine *e, const composite_op *ops, int32
             return efail(e, CPT_EINVAL, "op %d: a captured graph reads device members only", i);
     rc = plan_render(e, rops, n_rops, &rdescs, &ritems, &n_after);
     if (rc) return rc;
+    std::vector<int32_t> cleared;
+    for (const auto &pn : n_after) cleared.push_back(pn.first);
+    std::vector<ClearDesc> cdescs;
+    int64_t citems = 0;
+    rc = plan_clears(e, cleared.data(), (int32_t)cleared.size(), &cdescs, &citems);
+    if (rc) return rc;
     rc = drain(e);
     if (rc) return rc;
     destroy_graph(e);
     ECK(e, cudaMalloc(&e->graph_counters, 2 * sizeof(uint32_t)));
+    if (!cdescs.empty()) {
+        ECK(e, cudaMalloc(&e->graph_clears, cdescs.size() * sizeof(ClearDesc)));
+        ECK(e, cudaMemcpy(e->graph_clears, cdescs.data(), cdescs.size() * sizeof(ClearDesc), cudaMemcpyHostToDevice));
+    }
     if (!descs.empty()) {
         ECK(e, cudaMalloc(&e->graph_ops, descs.size() * sizeof(OpDesc)));
         ECK(e, cudaMemcpy(e->graph_ops, descs.data(), descs.size() * sizeof(OpDesc), cudaMemcpyHostToDevice));
@@ -1205,10 +1317,9 @@ int composite_engine_capture(composite_engine *e, const composite_op *ops, int32
     } restore{e, engine_stream};
     ECK(e, cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal));
     auto body = [&]() -> int {
-        for (const auto &pn : n_after) {
-            PlaneRec &r = e->planes[pn.first];
-            ECK(e, cudaMemsetAsync(r.data, 0, r.bytes(), e->stream));
-            ECK(e, cudaMemsetAsync(e->d_flags + pn.first, 0, sizeof(int), e->stream));
+        if (citems > 0) {   // every target plane and its flag in one node
+            int r = launch_clear(e, e->graph_clears, (int)cdescs.size(), citems);
+            if (r) return r;
         }
         if (items > 0) {
             int r = launch_accumulate(e, e->graph_ops, (int)descs.size(), items, e->graph_counters);
@@ -1275,12 +1386,11 @@ int composite_engine_tune(composite_engine *e, const composite_op *ops, int32_t 
         cudaEventDestroy(a);
         return ecuda(e, ce, "cudaEventCreate");
     }
+    std::vector<int32_t> cleared;
+    for (const auto &pn : n_after) cleared.push_back(pn.first);
     auto run = [&]() -> int {
-        for (const auto &pn : n_after) {
-            int r = clear_plane(e, pn.first);
-            if (r) return r;
-        }
-        return submit_internal(e, ops, n_ops);
+        const int r = clear_many(e, cleared.data(), (int32_t)cleared.size());
+        return r ? r : submit_internal(e, ops, n_ops);
     };
     // Best of `repeats` timed runs (each after an untimed one) of the current
     // configuration, in ms; < 0 on error (rc set).

@@ -336,12 +336,15 @@ int build_cycle(composite_server *s, Cycle *cyc, std::vector<Request> &batch) {
     if (rc) return rc;
     std::vector<composite_op> ops;
     size_t off = 0;
+    std::vector<int32_t> cleared;   // planes recomputed from scratch: one clear launch for all
+    for (size_t r = 0; r < batch.size(); ++r)
+        if (recompute[r]) cleared.push_back(s->sessions[batch[r].session].plane);
+    if (!cleared.empty()) {
+        rc = engine_rc(s, composite_engine_clear_many(s->eng, cleared.data(), (int32_t)cleared.size()));
+        if (rc) return rc;
+    }
     for (size_t r = 0; r < batch.size(); ++r) {
         const int32_t plane = s->sessions[batch[r].session].plane;
-        if (recompute[r]) {
-            rc = engine_rc(s, composite_engine_clear(s->eng, plane));
-            if (rc) return rc;
-        }
         for (int sign = 1; sign >= -1; sign -= 2) {
             const std::vector<int32_t> &ids = sign > 0 ? res_add[r] : res_rem[r];
             if (ids.empty()) continue;

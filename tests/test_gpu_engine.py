@@ -325,3 +325,30 @@ def test_host_chunk_failure_poisons_the_submit_planes(monkeypatch):
         eng.sync()
     check(o, m)
     check(oq, other)
+
+
+@pytest.mark.parametrize("count_bits", [32, 16])
+def test_clear_many_in_one_launch(count_bits):
+    shapes = [(1024, 1024, 12), (13, 7, 5), (257, 131, 40), (4096, 3, 9)]
+    with binding.Engine() as eng:
+        planes, data = [], []
+        for i, (w, h, n) in enumerate(shapes):
+            m = synth.random_masks(300 + i, n, h, w)
+            p = eng.add_plane(w, h, count_bits)
+            dev = padded(m)
+            eng.submit([eng.op(p, dev), eng.op(p, dev)])
+            planes.append(p)
+            data.append((m, dev))
+        eng.clear_many(planes[:3] + [planes[0]])        # a repeated id is cleared once
+        assert [eng.member_count(p) for p in planes] == [0, 0, 0, 2 * shapes[3][2]]
+        eng.submit([eng.op(p, dev) for p, (_, dev) in zip(planes[:3], data[:3])])
+        outs = [outputs(w, h, count_bits) for w, h, _ in shapes]
+        eng.render([eng.render_op(p, *o) for p, o in zip(planes, outs)])
+        eng.sync()
+        for (m, _), o in zip(data[:3], outs[:3]):
+            check(o, m)
+        np.testing.assert_array_equal(outs[3][0].cpu().numpy().astype(np.int64) & 0xFFFF,
+                                      2 * oracle.count(data[3][0]))
+        with pytest.raises(binding.CompositeError) as e:
+            eng.clear_many([planes[0], 999])
+        assert e.value.code == binding.CPT_EINVAL

@@ -70,6 +70,8 @@ def parse_args():
     p.add_argument("--requests", type=int, default=200, help="serving: requests per offered rate")
     p.add_argument("--max-batch", type=int, default=64, help="serving: requests per cycle")
     p.add_argument("--poll-us", type=float, default=100.0, help="serving: host back-off between idle polls")
+    p.add_argument("--batch-requests", type=int, default=64,
+                   help="batched: requests in the mix (64 is the workload; fewer make a small profiling case)")
     p.add_argument("--batched-streamed", type=int, default=1,
                    help="batched: 1 = also run the 64 requests streamed from pinned host memory")
     p.add_argument("--plain-arm", type=int, default=1,
@@ -839,7 +841,7 @@ def sweep_batched(args, torch, binding, device, stream):
     persistent accumulate launch, one persistent render launch), after the
     engine's autotuner picked slab depth and CTAs per SM."""
     import synth
-    reqs = synth.batched_requests(4, 64)
+    reqs = synth.batched_requests(4, args.batch_requests)
     terrains, data = {}, []
     for r, (w, h, n) in enumerate(reqs):
         if (w, h) not in terrains:
@@ -1347,6 +1349,52 @@ def sweep_render(args, torch, binding, device, stream):
                                   "gbs": bpp * P / (ms * 1e-3) / 1e9}), flush=True)
             comp.sync()
         del m
+        torch.cuda.empty_cache()
+    sweep_render_engine(args, torch, binding, device, stream)
+
+
+def sweep_render_engine(args, torch, binding, device, stream):
+    """The engine's render launch alone over the batched mix's 64 plane shapes
+    (two random members folded into each 16-bit plane; bucket + RGBA device
+    outputs), against 64 plain renders of the same planes: 2 + 1 + 4 bytes
+    per pixel."""
+    import synth
+    reqs = synth.batched_requests(4, args.batch_requests)
+    px = sum(w * h for w, h, _ in reqs)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(8)
+    eng = binding.Engine(stream=stream.cuda_stream)
+    planes, outs, ctxs, masks = [], [], [], []
+    for w, h, _ in reqs:
+        m = torch.randint(0, 2, (2, h, w), dtype=torch.uint8, device=device, generator=gen)
+        p = eng.add_plane(w, h, 16)
+        eng.submit([eng.op(p, m)])
+        ctx = binding.Composite(w, h, stream=stream.cuda_stream, staging_buffers=1, chunk_members=1)
+        ctx.add(m)                    # device masks are read in place: no staging used
+        planes.append(p)
+        ctxs.append(ctx)
+        masks.append(m)
+        outs.append((torch.empty((h, w), dtype=torch.uint8, device=device),
+                     torch.empty((h, w, 4), dtype=torch.uint8, device=device)))
+    rops = [eng.render_op(p, None, b, c) for p, (b, c) in zip(planes, outs)]
+    ms_engine = _timed(torch, stream, lambda: eng.render(rops), 50, 5)
+
+    def plain():
+        for ctx, (b, c) in zip(ctxs, outs):
+            ctx.render(bucket_out=b, rgba_out=c)
+
+    ms_plain = _timed(torch, stream, plain, 50, 5)
+    eng.sync()
+    for ctx in ctxs:
+        ctx.sync()
+        ctx.close()
+    eng.close()
+    peaks, _ = measured_peaks()
+    gbs = lambda ms: 7 * px / (ms * 1e-3) / 1e9
+    print(json.dumps({"sweep": "render_engine", "planes": len(reqs), "pixels": px,
+                      "engine_us": 1e3 * ms_engine, "engine_gbs": gbs(ms_engine),
+                      "engine_frac_of_hbm": gbs(ms_engine) / peaks["hbm_gbs"],
+                      "plain_us": 1e3 * ms_plain, "plain_gbs": gbs(ms_plain)}), flush=True)
 
 
 def run_sweep(args):

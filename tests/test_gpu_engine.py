@@ -352,3 +352,18 @@ def test_clear_many_in_one_launch(count_bits):
         with pytest.raises(binding.CompositeError) as e:
             eng.clear_many([planes[0], 999])
         assert e.value.code == binding.CPT_EINVAL
+
+
+def test_host_ops_bit_packed_through_staging():
+    w, h, n = 512, 96, 30
+    m = synth.scramble_nonzero(synth.random_masks(310, n, h, w, density=0.4), 310)
+    packed = synth.pack_masks(m)                    # rows of 64 bytes: 16-byte aligned
+    host = torch.from_numpy(packed).pin_memory()
+    with binding.Engine(staging_bytes=1 << 20) as eng:
+        p = eng.add_plane(w, h)
+        eng.submit([eng.op(p, host, mask_format="bits"), eng.op(p, padded(m[:10]))])
+        eng.submit([eng.op(p, host[:10], sign=-1, mask_format="bits")])
+        o = outputs(w, h)
+        eng.render([eng.render_op(p, *o)])
+        eng.sync()
+    check(o, np.concatenate([m[10:], m[:10]]))

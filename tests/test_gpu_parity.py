@@ -555,3 +555,22 @@ def test_automatic_chunk_depth(w, h, n, path):
         rec = comp.trace()
         check_counts(comp, m)
     assert int((rec[:, 0] == 0).sum()) == -(-n // c)
+
+
+@pytest.mark.parametrize("what", ["mean_depth", "bits"])
+def test_registered_ingest_depths_and_bit_packed(what):
+    # page-locked in place for the call: float32 depths and bit-packed masks
+    w, h, n = 1024, 512, 40
+    if what == "mean_depth":
+        d = synth.random_depths(172, n, h, w)            # 84 MB: above the 64 MiB threshold
+        with binding.Composite(w, h, mode="mean_depth", pageable_ingest="register") as comp:
+            comp.add(d)
+            comp.remove(d[:5])
+            got = comp.render_host()["mean"]
+        assert np.abs(got.astype(np.float64) - oracle.mean_depth(d[5:])).max() <= 1e-5 * n
+    else:
+        m = synth.random_masks(173, n, h, w)
+        packed = synth.pack_masks(m)
+        with binding.Composite(w, h, mask_format="bits", pageable_ingest="register") as comp:
+            comp.add(packed)
+            check_counts(comp, m)

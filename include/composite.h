@@ -92,7 +92,10 @@ enum {
                                  (cudaHostRegister), upload straight from it, wait for the
                                  uploads and unregister it before returning; a batch the
                                  driver will not register (already registered, say) goes
-                                 through the ring                                        */
+                                 through the ring.  While the call runs the batch is
+                                 pinned memory to every other caller too: it must not be
+                                 handed to another call (another context, another
+                                 thread) at the same time                                */
 };
 
 enum {

@@ -162,7 +162,7 @@ int composite_engine_capture(composite_engine *eng, const composite_op *ops, int
 int composite_engine_replay(composite_engine *eng);
 
 /* Autotuner: times "clear the ops' planes + submit ops", `repeats` runs per
- * candidate, in three rounds, each keeping the fastest: (1) slab_members in
+ * candidate, in three passes, each keeping the fastest: (1) slab_members in
  * {32, 64, 128, 255} x schedule {grid, persistent with ctas_per_sm 3, 4, 5};
  * (2) item_member_groups in {256, 512, 1024, 2048} (the work item's tile of
  * groups); (3) when some op reads pinned host members, staging_buffers in

@@ -1419,7 +1419,7 @@ int composite_engine_tune(composite_engine *e, const composite_op *ops, int32_t 
         }
         return true;
     };
-    // round 1: slab depth x schedule (ctas_per_sm 0 stands for the grid schedule)
+    // pass 1: slab depth x schedule (ctas_per_sm 0 stands for the grid schedule)
     static const int slabs[] = {32, 64, 128, 255};
     static const int ctas[] = {0, 3, 4, 5};
     const int ctas_before = e->cfg.ctas_per_sm;
@@ -1431,7 +1431,7 @@ int composite_engine_tune(composite_engine *e, const composite_op *ops, int32_t 
             e->cfg.ctas_per_sm = c ? c : ctas_before;
             if (!consider()) break;
         }
-    // round 2: the work item's tile of groups
+    // pass 2: the work item's tile of groups
     static const int item_groups[] = {256, 512, 1024, 2048};
     if (!rc) {
         e->cfg = best;
@@ -1440,7 +1440,7 @@ int composite_engine_tune(composite_engine *e, const composite_op *ops, int32_t 
             if (!consider()) break;
         }
     }
-    // round 3: staging buffers for host members
+    // pass 3: staging buffers for host members
     static const int stage_counts[] = {2, 3, 4};
     static const int stage_mib[] = {64, 128, 256, 512};
     if (!rc && any_host) {

@@ -179,3 +179,29 @@ def test_ncu_traffic_record_scales_member_bytes_only(tmp_path):
     assert rec["captured_duration_us"] == 5.0
     assert rec["dram_bytes_per_launch"] == 1_020_000 - 4 * 1000 + 64 * 1000
     assert rec["workload"] == "100x10x64" and len(rec["kernel_source_sha256_16"]) == 16
+
+
+class _OracleComposite:
+    """Stands in for a GPU composite in the bench's check helpers: renders the
+    oracle's counts and mean depth of the members given."""
+
+    def __init__(self, masks=None, depths=None):
+        self.masks, self.depths = masks, depths
+
+    def render_host(self):
+        import oracle
+        if self.depths is not None:
+            return {"mean": oracle.mean_depth(self.depths).astype(np.float32)}
+        return {"counts": oracle.count(self.masks)}
+
+
+def test_bench_identity_checks_accept_the_oracle_and_reject_a_mistake():
+    import bench
+    ens = synth.ensemble(41, 96, 40, 12)
+    masks, depths = synth.masks(ens), synth.depths(ens)
+    assert bench.identity_rows_exact(_OracleComposite(masks=masks), ens.terrain, ens.levels)
+    assert not bench.identity_rows_exact(_OracleComposite(masks=masks[1:]), ens.terrain, ens.levels)
+    err = bench.depth_identity_max_error(_OracleComposite(depths=depths), ens.terrain, ens.levels)
+    assert err <= 1e-5
+    bad = bench.depth_identity_max_error(_OracleComposite(depths=depths[1:]), ens.terrain, ens.levels)
+    assert bad > 1e-3

@@ -23,7 +23,8 @@
  *     CPT_MODE_COUNT (or one bit per pixel with CPT_MASK_BITS), float32 in
  *     CPT_MODE_MEAN_DEPTH.  Row y of member m starts at members +
  *     m * member_stride_bytes + y * row_pitch_bytes.
- *   - Memory kind of `members` is detected (cudaPointerGetAttributes):
+ *   - Memory kind of `members` is detected (cudaPointerGetAttributes); device
+ *     memory of another GPU than the context's is rejected (CPT_EINVAL):
  *       pageable host  -> copied through the library's pinned ring; the
  *                         caller may reuse the memory as soon as the call
  *                         returns;
@@ -211,7 +212,9 @@ int composite_remove_members(composite_ctx *ctx, const void *members, int32_t n_
  *   mean_out    float32 mean depth per pixel                 MEAN_DEPTH mode
  * lut_rgba: 256 x 4 bytes in host memory, or NULL for the default ramp
  * b -> (255-b, 255-b, 255, 255).
- * out_on_device = 1: the outputs are device pointers; the render is queued on
+ * out_on_device = 1: the outputs are device pointers (device memory of the
+ * context's device, or mapped pinned host memory; anything else is rejected
+ * with CPT_EINVAL before anything is queued); the render is queued on
  * the compute stream and the call returns without waiting (an underflow is
  * then reported by composite_sync).  out_on_device = 0: host pointers; the
  * call waits (bounded) until they are written and reports an underflow.

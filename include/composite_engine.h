@@ -20,8 +20,10 @@
  *
  * Conventions: every call returns CPT_OK (0) or a negative composite_status
  * (composite.h); the message is in composite_engine_last_error.  Members are
- * device memory or pinned host memory; index lists and outputs are device
- * memory; rasters need 16-byte aligned base, row pitch and member stride.
+ * device memory of the engine's device or pinned host memory; index lists and
+ * outputs are device memory of that device (outputs may also be mapped pinned
+ * host memory); anything else is rejected with CPT_EINVAL before anything is
+ * queued.  Rasters need 16-byte aligned base, row pitch and member stride.
  * Ops on pinned host members stream through the engine's own staging
  * buffers (the dual-buffer pipeline of Section 4, Figs. 3-4): rasters of
  * consecutive host ops are packed into a buffer of staging_bytes, uploaded on

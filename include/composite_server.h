@@ -106,8 +106,9 @@ int composite_server_close_session(composite_server *srv, int32_t session);
 /* Queues a request: toggle the n member ids in `toggle` (host array, ids in
  * [0, n_resident + n_overflow), duplicates toggle twice) in the session, then
  * render its composite into the device outputs (each may be NULL; width x
- * height, dense; counts uint32 4-byte aligned, rgba 4-byte aligned).  The
- * outputs are written when the request completes.  *request_id_out gets an
+ * height, dense; counts uint32 4-byte aligned, rgba 4-byte aligned; device
+ * memory of the server's device or mapped pinned host memory, else
+ * CPT_EINVAL).  The outputs are written when the request completes.  *request_id_out gets an
  * id that increases with every request. */
 int composite_server_request(composite_server *srv, int32_t session, const int32_t *toggle, int32_t n,
                              uint32_t *counts_out, uint8_t *bucket_out, uint8_t *rgba_out,

@@ -37,7 +37,7 @@ namespace {
 
 thread_local std::string g_begin_error;
 
-enum MemKind { kPageable = 0, kPinned = 1, kDevice = 2 };
+enum MemKind { kPageable = 0, kPinned = 1, kDevice = 2, kForeignDevice = 3 };
 constexpr int kDefaultTmaBoxBytes = 256;
 enum TraceKind { kTraceUpload = 0, kTraceConvert = 1, kTraceKernel = 2 };
 
@@ -218,7 +218,9 @@ int begin_chunk(composite_ctx *ctx) {
     return CPT_OK;
 }
 
-MemKind memory_kind(const void *p) {
+// Memory kind of p as seen from `device`: device memory of another GPU is
+// kForeignDevice (a kernel here cannot be assumed to reach it).
+MemKind memory_kind(const void *p, int device) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
@@ -226,6 +228,7 @@ MemKind memory_kind(const void *p) {
     }
     switch (a.type) {
         case cudaMemoryTypeDevice:
+            return a.device == device ? kDevice : kForeignDevice;
         case cudaMemoryTypeManaged:
             return kDevice;
         case cudaMemoryTypeHost:
@@ -233,6 +236,20 @@ MemKind memory_kind(const void *p) {
         default:
             return kPageable;
     }
+}
+
+// Whether a kernel on `device` may write p: device memory of that device,
+// managed memory, or pinned host memory mapped for the device.  Pageable
+// host memory or another GPU's memory is turned away before any launch.
+bool device_writable(const void *p, int device) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type == cudaMemoryTypeManaged) return true;
+    if (a.type == cudaMemoryTypeDevice) return a.device == device;
+    return a.type == cudaMemoryTypeHost && a.devicePointer != nullptr;
 }
 
 Lut pack_lut(const uint8_t *rgba) {
@@ -656,7 +673,9 @@ int apply(composite_ctx *ctx, const void *members, int32_t n, int64_t stride, in
         return fail(ctx, CPT_EINVAL, "32-bit counts hold at most 2^32-1 members");
 
     const uint8_t *src = static_cast<const uint8_t *>(members);
-    const MemKind kind = memory_kind(members);
+    const MemKind kind = memory_kind(members, ctx->device);
+    if (kind == kForeignDevice)
+        return fail(ctx, CPT_EINVAL, "members are device memory of another GPU (the context runs on device %d)", ctx->device);
     ctx->call_chunks = 0;
     ctx->call_chunk = chunk_for_call(ctx, n);
     // uploads on the copy stream start after the caller's earlier work on the
@@ -860,7 +879,9 @@ int composite_load_counts(composite_ctx *ctx, const void *counts, int64_t n_memb
         return fail(ctx, CPT_EINVAL, "n_members %lld outside 0..%lld", (long long)n_members, (long long)limit);
     const size_t elem = (size_t)ctx->cfg.count_bits / 8;
     if (reinterpret_cast<uintptr_t>(counts) % elem) return fail(ctx, CPT_EINVAL, "counts not aligned to its element");
-    const MemKind kind = memory_kind(counts);
+    const MemKind kind = memory_kind(counts, ctx->device);
+    if (kind == kForeignDevice)
+        return fail(ctx, CPT_EINVAL, "counts are device memory of another GPU (the context runs on device %d)", ctx->device);
     const int64_t px = (int64_t)ctx->width * ctx->height;
     if (kind != kDevice) {
         // host counts are checked against N before anything changes
@@ -942,6 +963,12 @@ int render(composite_ctx *ctx, void *counts_out, uint8_t *bucket_out, uint8_t *r
         if ((reinterpret_cast<uintptr_t>(counts_out) % cbytes) || (reinterpret_cast<uintptr_t>(rgba_out) % 4) ||
             (reinterpret_cast<uintptr_t>(mean_out) % 4) || (reinterpret_cast<uintptr_t>(hist_out) % 8))
             return fail(ctx, CPT_EINVAL, "device outputs must be aligned to their element size");
+        // the render kernel writes them directly
+        const void *outs[5] = {counts_out, bucket_out, rgba_out, mean_out, hist_out};
+        for (const void *o : outs)
+            if (o && !device_writable(o, ctx->device))
+                return fail(ctx, CPT_EINVAL, "out_on_device = 1 needs device memory of device %d (or mapped pinned "
+                                             "host memory) for every output", ctx->device);
     }
     const Lut lut = lut_rgba ? pack_lut(lut_rgba) : ctx->default_lut;
     const int64_t px = (int64_t)ctx->width * ctx->height;

@@ -612,6 +612,33 @@ int upload(composite_engine *e, Upload *ring, int *idx, const void *src, size_t 
     return CPT_OK;
 }
 
+// Memory kind of an op's members as seen from `device`: 1 = pinned host,
+// 0 = device (this device's, or managed), -1 = neither (pageable host, or
+// another GPU's memory, which a kernel here cannot be assumed to reach).
+int member_kind(const void *p, int device) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    if (a.type == cudaMemoryTypeManaged) return 0;
+    if (a.type == cudaMemoryTypeDevice) return a.device == device ? 0 : -1;
+    return a.type == cudaMemoryTypeHost ? 1 : -1;
+}
+
+// Whether a kernel on `device` may read or write p in place: this device's
+// memory, managed memory, or pinned host memory mapped for the device.
+bool device_reachable(const void *p, int device) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type == cudaMemoryTypeManaged) return true;
+    if (a.type == cudaMemoryTypeDevice) return a.device == device;
+    return a.type == cudaMemoryTypeHost && a.devicePointer != nullptr;
+}
+
 bool plane_ok(const composite_engine *e, int32_t p) {
     return p >= 0 && p < (int32_t)e->planes.size() && e->planes[p].alive;
 }
@@ -704,6 +731,11 @@ int plan_render(composite_engine *e, const composite_render_op *ops, int32_t n_o
         const PlaneRec &p = e->planes[o.plane];
         if ((reinterpret_cast<uintptr_t>(o.counts_out) % (p.count_bits / 8)) || (reinterpret_cast<uintptr_t>(o.rgba_out) % 4))
             return efail(e, CPT_EINVAL, "render %d: counts_out must be aligned to its count type, rgba_out to 4 bytes", i);
+        const void *outs[3] = {o.counts_out, o.bucket_out, o.rgba_out};
+        for (const void *q : outs)
+            if (q && !device_reachable(q, e->device))
+                return efail(e, CPT_EINVAL, "render %d: outputs must be device memory of device %d (or mapped pinned "
+                                            "host memory)", i, e->device);
         int64_t n = p.n;
         bool refolded = false;   // a captured graph clears and refolds the plane first
         if (n_override)
@@ -838,17 +870,6 @@ int clear_many(composite_engine *e, const int32_t *planes, int32_t n) {
         e->planes[d.plane_id].poisoned = false;
     }
     return CPT_OK;
-}
-
-// Memory kind of an op's members: 1 = pinned host, 0 = device, -1 = neither.
-int member_kind(const void *p) {
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return -1;
-    }
-    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return 0;
-    return a.type == cudaMemoryTypeHost ? 1 : -1;
 }
 
 void free_stage(composite_engine *e) {
@@ -999,9 +1020,13 @@ int submit_internal(composite_engine *e, const composite_op *ops, int32_t n_ops)
     for (int32_t i = 0; i < n_ops; ++i) {
         const composite_op &o = ops[i];
         if (o.n_members == 0) continue;
-        const int kind = member_kind(o.members);
-        if (kind < 0) return efail(e, CPT_EINVAL, "op %d: members must be device or pinned host memory", i);
+        const int kind = member_kind(o.members, e->device);
+        if (kind < 0)
+            return efail(e, CPT_EINVAL, "op %d: members must be device memory of device %d or pinned host memory", i,
+                         e->device);
         if (kind == 0) {
+            if (o.member_index && !device_reachable(o.member_index, e->device))
+                return efail(e, CPT_EINVAL, "op %d: member_index must be device memory of device %d", i, e->device);
             dev_ops.push_back(o);
             continue;
         }
@@ -1277,9 +1302,13 @@ int composite_engine_capture(composite_engine *e, const composite_op *ops, int32
     int64_t items = 0, ritems = 0;
     int rc = plan_ops(e, ops, n_ops, &descs, &items, &n_after, true);
     if (rc) return rc;
-    for (int32_t i = 0; i < n_ops; ++i)
-        if (ops[i].n_members > 0 && member_kind(ops[i].members) != 0)
-            return efail(e, CPT_EINVAL, "op %d: a captured graph reads device members only", i);
+    for (int32_t i = 0; i < n_ops; ++i) {
+        if (ops[i].n_members == 0) continue;
+        if (member_kind(ops[i].members, e->device) != 0)
+            return efail(e, CPT_EINVAL, "op %d: a captured graph reads members of device %d only", i, e->device);
+        if (ops[i].member_index && !device_reachable(ops[i].member_index, e->device))
+            return efail(e, CPT_EINVAL, "op %d: member_index must be device memory of device %d", i, e->device);
+    }
     rc = plan_render(e, rops, n_rops, &rdescs, &ritems, &n_after);
     if (rc) return rc;
     std::vector<int32_t> cleared;
@@ -1378,7 +1407,7 @@ int composite_engine_tune(composite_engine *e, const composite_op *ops, int32_t 
     if (rc) return rc;
     bool any_host = false;
     for (int32_t i = 0; i < n_ops; ++i)
-        if (ops[i].n_members > 0 && member_kind(ops[i].members) == 1) any_host = true;
+        if (ops[i].n_members > 0 && member_kind(ops[i].members, e->device) == 1) any_host = true;
     cudaEvent_t a = nullptr, b = nullptr;
     ECK(e, cudaEventCreate(&a));
     cudaError_t ce = cudaEventCreate(&b);

@@ -86,6 +86,7 @@ struct composite_server {
     const void *overflow_dev = nullptr;   // the overflow part as the device reads it
     std::vector<int32_t> pos_of;          // overflow id -> staging position, per cycle
     cpt::DeviceCaps caps{};
+    int device = 0;                // the device current at begin
     cudaEvent_t stage_ready[2] = {nullptr, nullptr}, stage_free[2] = {nullptr, nullptr};
     int stage_half = 0;
     int64_t next_id = 0;
@@ -518,23 +519,31 @@ int composite_server_begin(composite_server **out, const composite_server_config
     if (c.staging_members < 1 || c.staging_members > 4096) return sfail(nullptr, CPT_EINVAL, "staging_members not in 1..4096");
     if (c.max_cycles_in_flight < 1 || c.max_cycles_in_flight > 16) return sfail(nullptr, CPT_EINVAL, "max_cycles_in_flight not in 1..16");
     if (c.hbm_budget_bytes < 0 || c.wait_timeout_ms < 0) return sfail(nullptr, CPT_EINVAL, "negative budget or timeout");
+    int device = 0;
+    if (cudaGetDevice(&device) != cudaSuccess) {
+        cudaGetLastError();
+        return sfail(nullptr, CPT_ECUDA, "no CUDA device");
+    }
     if (c.n_resident > 0) {
         cudaPointerAttributes a;
         if (cudaPointerGetAttributes(&a, c.resident) != cudaSuccess ||
-            (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)) {
+            !(a.type == cudaMemoryTypeManaged || (a.type == cudaMemoryTypeDevice && a.device == device))) {
             cudaGetLastError();
-            return sfail(nullptr, CPT_EINVAL, "resident members must be device memory");
+            return sfail(nullptr, CPT_EINVAL, "resident members must be device memory of the current device");
         }
     }
     if (c.n_overflow > 0) {
         cudaPointerAttributes a;
-        if (cudaPointerGetAttributes(&a, c.overflow) != cudaSuccess || a.type == cudaMemoryTypeUnregistered) {
+        if (cudaPointerGetAttributes(&a, c.overflow) != cudaSuccess || a.type == cudaMemoryTypeUnregistered ||
+            (a.type == cudaMemoryTypeDevice && a.device != device)) {
             cudaGetLastError();
-            return sfail(nullptr, CPT_EINVAL, "overflow members must be pinned host (or device) memory");
+            return sfail(nullptr, CPT_EINVAL, "overflow members must be pinned host memory (or device memory of "
+                                              "the current device)");
         }
     }
     composite_server *s = new composite_server();
     s->cfg = c;
+    s->device = device;
     s->n_total = c.n_resident + c.n_overflow;
     s->raster_bytes = (int64_t)c.row_pitch_bytes * c.height;
     s->plane_bytes = ((int64_t)c.width + 15) / 16 * 16 * c.height * 4;
@@ -660,6 +669,21 @@ int composite_server_request(composite_server *s, int32_t session, const int32_t
             return sfail(s, CPT_EINVAL, "member id %d out of range [0, %d)", toggle[i], s->n_total);
     if ((reinterpret_cast<uintptr_t>(counts_out) % 4) || (reinterpret_cast<uintptr_t>(rgba_out) % 4))
         return sfail(s, CPT_EINVAL, "counts_out and rgba_out must be 4-byte aligned");
+    // the render kernel writes the outputs directly: device memory of the
+    // server's device, or mapped pinned host memory
+    const void *outs[3] = {counts_out, bucket_out, rgba_out};
+    for (const void *o : outs) {
+        if (!o) continue;
+        cudaPointerAttributes a;
+        const bool ok = cudaPointerGetAttributes(&a, o) == cudaSuccess &&
+                        (a.type == cudaMemoryTypeManaged || (a.type == cudaMemoryTypeDevice && a.device == s->device) ||
+                         (a.type == cudaMemoryTypeHost && a.devicePointer != nullptr));
+        if (!ok) {
+            cudaGetLastError();
+            return sfail(s, CPT_EINVAL, "outputs must be device memory of device %d (or mapped pinned host memory)",
+                         s->device);
+        }
+    }
     Request q;
     q.id = s->next_id++;
     q.session = session;

@@ -540,9 +540,11 @@ def test_resume_rejects_counts_above_n():
         assert (comp.render_host()["bucket"] == 255).all()
 
 
-@pytest.mark.parametrize("w,h,n,path", [(1024, 1024, 100, "linear"), (64, 48, 300, "linear"),
-                                        (1024, 1024, 40, "texture"), (2048, 512, 70, "tma")])
-def test_automatic_chunk_depth(w, h, n, path):
+@pytest.mark.parametrize("w,h,n,path,kind", [(1024, 1024, 100, "linear", "pinned"), (64, 48, 300, "linear", "pinned"),
+                                             (1024, 1024, 40, "texture", "pinned"),
+                                             (1024, 1024, 40, "texture", "device"),
+                                             (2048, 512, 70, "tma", "pinned"), (512, 256, 600, "linear", "pageable")])
+def test_automatic_chunk_depth(w, h, n, path, kind):
     # chunk_members 0: a staging buffer holds up to 256 MiB of rasters, and
     # a call of n rasters goes in chunks of max(16 MiB, min(cap, ceil(n/32)))
     m = synth.scramble_nonzero(synth.random_masks(60 + n, n, h, w, density=0.3), 60)
@@ -550,11 +552,15 @@ def test_automatic_chunk_depth(w, h, n, path):
     member = row * h
     cap = max(1, min(255, (256 << 20) // member))
     c = max(min(cap, -(-(16 << 20) // member)), min(cap, -(-n // 32)))
-    with binding.Composite(w, h, read_path=path, chunk_members=0, trace=True) as comp:
-        comp.add(as_kind(m, "pinned"))
+    with binding.Composite(w, h, read_path=path, chunk_members=0, trace=True, pageable_ingest="ring") as comp:
+        comp.add(as_kind(m, kind))
         rec = comp.trace()
         check_counts(comp, m)
-    assert int((rec[:, 0] == 0).sum()) == -(-n // c)
+    # one upload per chunk (the texture path's direct conversion from device
+    # memory uploads nothing: one conversion per chunk instead)
+    kinds = rec[:, 0].astype(int)
+    per_chunk = (kinds == 1).sum() if kind == "device" else (kinds == 0).sum()
+    assert int(per_chunk) == -(-n // c)
 
 
 @pytest.mark.parametrize("what", ["mean_depth", "bits"])

@@ -92,8 +92,8 @@ struct ClearDesc {
 constexpr int kSmemStarts = 2048;      // ops whose first items fit in shared memory
 constexpr int kClearWords = 8;         // 16-byte words per lane per clear item
 constexpr int kClearCtasPerSm = 4;
-constexpr int kRenderGroups = 2;       // 16-pixel groups per lane per render item
-constexpr int kRenderCtasPerSm = 3;    // render launch: CTAs per SM, grid-stride over items
+constexpr int kRenderGroups = 1;       // 16-pixel groups per lane per render item
+constexpr int kRenderCtasPerSm = 4;    // render launch: CTAs per SM, grid-stride over items
 
 template <typename Desc>
 __device__ __forceinline__ int find_desc(const Desc *d, int n, int64_t item) {
@@ -339,7 +339,7 @@ engine_clear_kernel(const ClearDesc *ops, int n_ops, uint32_t n_items, int *flag
     const uint32_t warps = gridDim.x * (kThreads / 32);
     const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
     for (uint32_t item = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5); item < n_items; item += warps) {
-        const ClearDesc &op = ops[find_op(ops, n_ops, s_starts, item)];
+        const ClearDesc op = ops[find_op(ops, n_ops, s_starts, item)];   // by value: the stores may alias
         const int64_t w0 = (int64_t)(item - (uint32_t)op.item_start) * (32 * kClearWords) + lane;
 #pragma unroll
         for (int k = 0; k < kClearWords; ++k) {
@@ -363,7 +363,10 @@ engine_render_kernel(const RenderDesc *ops, int n_ops, uint32_t n_items, Lut lut
     const int lane = threadIdx.x & 31;
     const uint32_t warps = gridDim.x * (kThreads / 32);
     for (uint32_t item = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5); item < n_items; item += warps) {
-        const RenderDesc &op = ops[find_op(ops, n_ops, s_starts, item)];
+        // a copy in registers: the outputs this item stores to are global
+        // memory too, and through a reference the compiler would have to
+        // reload the descriptor's fields after every store
+        const RenderDesc op = ops[find_op(ops, n_ops, s_starts, item)];
         const int64_t groups = (int64_t)op.groups_per_row * op.height;
         const int64_t g0 = (int64_t)(item - (uint32_t)op.item_start) * (32 * kRenderGroups) + lane;
         uint32_t c[kRenderGroups][16];

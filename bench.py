@@ -1355,46 +1355,75 @@ def sweep_render(args, torch, binding, device, stream):
 
 def sweep_render_engine(args, torch, binding, device, stream):
     """The engine's render launch alone over the batched mix's 64 plane shapes
-    (two random members folded into each 16-bit plane; bucket + RGBA device
-    outputs), against 64 plain renders of the same planes: 2 + 1 + 4 bytes
-    per pixel."""
+    (bucket + RGBA device outputs into 16-bit planes), against 64 plain
+    renders of the same planes: 2 + 1 + 4 bytes per pixel.  Then both again
+    with a class histogram per plane (the engine zeroes the 64 histograms in
+    one clear launch before its render).  Two inputs: two random members per
+    plane (salt-and-pepper classes 0 / 127 / 255, the worst case for counting
+    runs of equal classes) and 32 members of one terrain ensemble, each plane
+    a crop of one 4096 x 4096 terrain (smooth class fields, noisy edges)."""
     import synth
     reqs = synth.batched_requests(4, args.batch_requests)
     px = sum(w * h for w, h, _ in reqs)
-    gen = torch.Generator(device=device)
-    gen.manual_seed(8)
-    eng = binding.Engine(stream=stream.cuda_stream)
-    planes, outs, ctxs, masks = [], [], [], []
-    for w, h, _ in reqs:
-        m = torch.randint(0, 2, (2, h, w), dtype=torch.uint8, device=device, generator=gen)
-        p = eng.add_plane(w, h, 16)
-        eng.submit([eng.op(p, m)])
-        ctx = binding.Composite(w, h, stream=stream.cuda_stream, staging_buffers=1, chunk_members=1)
-        ctx.add(m)                    # device masks are read in place: no staging used
-        planes.append(p)
-        ctxs.append(ctx)
-        masks.append(m)
-        outs.append((torch.empty((h, w), dtype=torch.uint8, device=device),
-                     torch.empty((h, w, 4), dtype=torch.uint8, device=device)))
-    rops = [eng.render_op(p, None, b, c) for p, (b, c) in zip(planes, outs)]
-    ms_engine = _timed(torch, stream, lambda: eng.render(rops), 50, 5)
-
-    def plain():
-        for ctx, (b, c) in zip(ctxs, outs):
-            ctx.render(bucket_out=b, rgba_out=c)
-
-    ms_plain = _timed(torch, stream, plain, 50, 5)
-    eng.sync()
-    for ctx in ctxs:
-        ctx.sync()
-        ctx.close()
-    eng.close()
+    side = max(max(w, h) for w, h, _ in reqs)
+    ens = synth.ensemble(4, side, side, 32)
+    terrain = torch.from_numpy(ens.terrain).to(device)
     peaks, _ = measured_peaks()
     gbs = lambda ms: 7 * px / (ms * 1e-3) / 1e9
-    print(json.dumps({"sweep": "render_engine", "planes": len(reqs), "pixels": px,
-                      "engine_us": 1e3 * ms_engine, "engine_gbs": gbs(ms_engine),
-                      "engine_frac_of_hbm": gbs(ms_engine) / peaks["hbm_gbs"],
-                      "plain_us": 1e3 * ms_plain, "plain_gbs": gbs(ms_plain)}), flush=True)
+    for kind in ("random2", "terrain32"):
+        gen = torch.Generator(device=device)
+        gen.manual_seed(8)
+        eng = binding.Engine(stream=stream.cuda_stream)
+        planes, outs, ctxs = [], [], []
+        for w, h, _ in reqs:
+            if kind == "random2":
+                m = torch.randint(0, 2, (2, h, w), dtype=torch.uint8, device=device, generator=gen)
+            else:
+                crop = terrain[:h, :w]
+                m = torch.stack([(crop < float(lv)).to(torch.uint8) for lv in ens.levels])
+            p = eng.add_plane(w, h, 16)
+            eng.submit([eng.op(p, m)])
+            ctx = binding.Composite(w, h, stream=stream.cuda_stream, staging_buffers=1, chunk_members=1)
+            ctx.add(m)                    # device masks are read in place: no staging used
+            planes.append(p)
+            ctxs.append(ctx)
+            outs.append((torch.empty((h, w), dtype=torch.uint8, device=device),
+                         torch.empty((h, w, 4), dtype=torch.uint8, device=device)))
+            eng.sync()
+            del m
+        rops = [eng.render_op(p, None, b, c) for p, (b, c) in zip(planes, outs)]
+        ms_engine = _timed(torch, stream, lambda: eng.render(rops), 50, 5)
+
+        def plain():
+            for ctx, (b, c) in zip(ctxs, outs):
+                ctx.render(bucket_out=b, rgba_out=c)
+
+        ms_plain = _timed(torch, stream, plain, 50, 5)
+        hists = [torch.empty(256, dtype=torch.int64, device=device) for _ in planes]
+        hrops = [eng.render_op(p, None, b, c, hg) for p, (b, c), hg in zip(planes, outs, hists)]
+        ms_engine_hist = _timed(torch, stream, lambda: eng.render(hrops), 50, 5)
+
+        def plain_hist():
+            for ctx, (b, c), hg in zip(ctxs, outs, hists):
+                ctx.render_histogram(hg, bucket_out=b, rgba_out=c)
+
+        ms_plain_hist = _timed(torch, stream, plain_hist, 50, 5)
+        eng.render(hrops)
+        eng.sync()
+        # every histogram against a count of the bucket image rendered with it
+        hist_ok = all(torch.equal(hg, torch.bincount(b.flatten(), minlength=256)) for hg, (b, _) in zip(hists, outs))
+        classes = int(sum((hg > 0).sum() for hg in hists)) / len(hists)
+        for ctx in ctxs:
+            ctx.sync()
+            ctx.close()
+        eng.close()
+        print(json.dumps({"sweep": "render_engine", "input": kind, "planes": len(reqs), "pixels": px,
+                          "mean_classes_per_plane": classes,
+                          "engine_us": 1e3 * ms_engine, "engine_gbs": gbs(ms_engine),
+                          "engine_frac_of_hbm": gbs(ms_engine) / peaks["hbm_gbs"],
+                          "plain_us": 1e3 * ms_plain, "plain_gbs": gbs(ms_plain),
+                          "engine_hist_us": 1e3 * ms_engine_hist, "engine_hist_gbs": gbs(ms_engine_hist),
+                          "plain_hist_us": 1e3 * ms_plain_hist, "hist_equals_bucket_count": hist_ok}), flush=True)
 
 
 def run_sweep(args):

@@ -97,6 +97,10 @@ typedef struct composite_render_op {
                                uint16 for a 16-bit plane), aligned to it */
     uint8_t *bucket_out;    /* width x height */
     uint8_t *rgba_out;      /* width x height x 4, 4-byte aligned */
+    uint64_t *histogram_out; /* 256 x uint64, 16-byte aligned, or NULL: the number of
+                               pixels of the plane in every overlap class (Fig. 1
+                               caption: the frequency of the overlap classes),
+                               counted in the same launch */
 } composite_render_op;
 
 int composite_engine_default_config(composite_engine_config *cfg);
@@ -140,7 +144,12 @@ int composite_engine_clear_many(composite_engine *eng, const int32_t *planes, in
 int composite_engine_submit(composite_engine *eng, const composite_op *ops, int32_t n_ops);
 
 /* Queues the render of every listed plane in one persistent launch.
- * lut_rgba: 256 x 4 host bytes or NULL for the default white-to-blue ramp. */
+ * lut_rgba: 256 x 4 host bytes or NULL for the default white-to-blue ramp.
+ * An op's histogram_out (if not NULL) is zeroed and then filled in the same
+ * call: bin k = the number of the plane's width x height pixels whose
+ * overlap class is k; it must not overlap another output of the call unless
+ * it is the same histogram, in which case the ops' pixels add up in it.
+ * CPT_EINVAL, nothing queued, for an unaligned or unreachable output. */
 int composite_engine_render(composite_engine *eng, const composite_render_op *ops, int32_t n_ops,
                             const uint8_t *lut_rgba);
 

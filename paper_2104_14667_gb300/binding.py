@@ -493,6 +493,7 @@ class RenderOp(ctypes.Structure):
         ("counts_out", ctypes.c_void_p),
         ("bucket_out", ctypes.c_void_p),
         ("rgba_out", ctypes.c_void_p),
+        ("histogram_out", ctypes.c_void_p),
     ]
 
 
@@ -609,10 +610,11 @@ class Engine:
         return o
 
     @staticmethod
-    def render_op(plane: int, counts_out=None, bucket_out=None, rgba_out=None) -> RenderOp:
+    def render_op(plane: int, counts_out=None, bucket_out=None, rgba_out=None, histogram_out=None) -> RenderOp:
         r = RenderOp()
         r.plane = plane
         r.counts_out, r.bucket_out, r.rgba_out = _ptr(counts_out), _ptr(bucket_out), _ptr(rgba_out)
+        r.histogram_out = _ptr(histogram_out)
         return r
 
     def submit(self, ops, keep=()):

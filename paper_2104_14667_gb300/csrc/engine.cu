@@ -77,6 +77,7 @@ struct RenderDesc {
     int32_t vec;           // 16-byte stores allowed
     int32_t u16;           // the plane holds uint16 counts (else uint32)
     cpt::ClassDivisor div; // floor(255 c / n_members) by multiplication
+    unsigned long long *hist;   // 256 class counts, zeroed before the launch, or NULL
 };
 
 // One plane of a batched clear: its bytes as 16-byte words, in items of
@@ -94,6 +95,7 @@ constexpr int kClearWords = 8;         // 16-byte words per lane per clear item
 constexpr int kClearCtasPerSm = 4;
 constexpr int kRenderGroups = 1;       // 16-pixel groups per lane per render item
 constexpr int kRenderCtasPerSm = 4;    // render launch: CTAs per SM, grid-stride over items
+constexpr int kRenderHistCtasPerSm = 3;   // with histograms: 64 KB of counters per CTA
 
 template <typename Desc>
 __device__ __forceinline__ int find_desc(const Desc *d, int n, int64_t item) {
@@ -334,7 +336,8 @@ engine_clear_kernel(const ClearDesc *ops, int n_ops, uint32_t n_items, int *flag
     load_starts(ops, n_ops, s_starts);
     __syncthreads();
     if (blockIdx.x == 0)
-        for (int i = threadIdx.x; i < n_ops; i += blockDim.x) flags[ops[i].plane_id] = 0;
+        for (int i = threadIdx.x; i < n_ops; i += blockDim.x)
+            if (ops[i].plane_id >= 0) flags[ops[i].plane_id] = 0;   // -1: a histogram, no flag
     const int lane = threadIdx.x & 31;
     const uint32_t warps = gridDim.x * (kThreads / 32);
     const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
@@ -349,24 +352,129 @@ engine_clear_kernel(const ClearDesc *ops, int n_ops, uint32_t n_items, int *flag
     }
 }
 
+// Class histogram of the render (Fig. 1 caption: the frequency of the
+// overlap classes).  Every lane of a warp owns a byte counter per class in
+// shared memory (8 KB per warp), four to a 32-bit word, and adds to it with
+// shared atomics whose result it never waits for; no two lanes touch one
+// word, so the adds never conflict.  A lane whose 16 pixels share one class
+// adds 16 at once.  A lane's row of 64 words is stored with the word index
+// XORed with the lane, so that one class of all 32 lanes lies in 32 different
+// banks.  Every kHistFoldItems items (at most 16 per item, so a byte stays
+// below 256) the warp folds the bytes into per-lane 32-bit totals in
+// registers -- lane L owns classes 4L..4L+3 and 128+4L..128+4L+3 -- and when
+// its items move on to another op, and at the end, it adds the totals to the
+// op's 64-bit histogram in global memory.
+constexpr int kHistWarpBytes = 32 * 256;
+constexpr int kHistFoldItems = 15;
+
+// row: the lane's 256 counter bytes; key: lane << 2, which XORs the word
+// index (class >> 2) with the lane
+__device__ __forceinline__ void hist_add(uint8_t *row, uint32_t key, uint32_t cls, uint32_t n) {
+    atomicAdd(reinterpret_cast<uint32_t *>(row + ((cls ^ key) & 0xFCu)), n << ((cls & 3u) << 3));
+}
+
+__device__ __forceinline__ void hist_count_group(uint8_t *row, uint32_t key, const uint32_t (&b)[16], int valid) {
+    bool same = valid == 16;
+#pragma unroll
+    for (int j = 1; j < 16; ++j) same &= b[j] == b[0];
+    if (same) {
+        hist_add(row, key, b[0], 16u);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            if (j < valid) hist_add(row, key, b[j], 1u);
+    }
+}
+
+__device__ __forceinline__ void hist_fold(uint8_t *cnt, uint32_t (&tot)[8], int lane) {
+    __syncwarp();
+    uint32_t *w = reinterpret_cast<uint32_t *>(cnt);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const uint32_t k = (uint32_t)lane + 32u * h;   // the word of classes 4k..4k+3
+        uint32_t lo = 0, hi = 0;                      // bytes 0, 2 and 1, 3 as 16-bit sums
+#pragma unroll 8
+        for (int r = 0; r < 32; ++r) {
+            uint32_t *at = w + r * 64 + (k ^ (uint32_t)r);
+            const uint32_t v = *at;
+            *at = 0u;
+            lo += v & 0x00FF00FFu;
+            hi += (v >> 8) & 0x00FF00FFu;
+        }
+        tot[4 * h + 0] += lo & 0xFFFFu;
+        tot[4 * h + 1] += hi & 0xFFFFu;
+        tot[4 * h + 2] += lo >> 16;
+        tot[4 * h + 3] += hi >> 16;
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ void hist_emit(uint32_t (&tot)[8], unsigned long long *hist, int lane) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t t = tot[4 * h + j];
+            if (t) atomicAdd(hist + 4 * lane + 128 * h + j, (unsigned long long)t);
+            tot[4 * h + j] = 0u;
+        }
+}
+
 // Render: warp-level items (render op, chunk of 32 x kRenderGroups 16-pixel
 // groups) dealt round robin to every warp of the launch -- items are all the
 // same size, so no counter is needed -- and a lane loads all its groups
-// before it classifies and stores any.
-__global__ void __launch_bounds__(kThreads, kRenderCtasPerSm)
+// before it classifies and stores any.  With histograms (kHist; 8 KB of
+// dynamic shared memory per warp) every CTA takes one contiguous range of
+// items instead, so that a warp's items span one or two ops and its totals
+// go to global memory once or twice.
+template <bool kHist>
+__global__ void __launch_bounds__(kThreads, kHist ? kRenderHistCtasPerSm : kRenderCtasPerSm)
 engine_render_kernel(const RenderDesc *ops, int n_ops, uint32_t n_items, Lut lut) {
     __shared__ uint32_t table[256];
     __shared__ uint32_t s_starts[kSmemStarts];
+    extern __shared__ __align__(16) uint8_t s_hist[];
+    const int lane = threadIdx.x & 31;
+    uint8_t *cnt = s_hist + (kHist ? (threadIdx.x >> 5) * kHistWarpBytes : 0);
+    uint8_t *row = cnt + (kHist ? lane * 256 : 0);
+    const uint32_t key = (uint32_t)lane << 2;
     for (int i = threadIdx.x; i < 256; i += kThreads) table[i] = lut.rgba[i];
+    if (kHist)
+        for (int i = lane; i < kHistWarpBytes / 16; i += 32) reinterpret_cast<uint4 *>(cnt)[i] = make_uint4(0, 0, 0, 0);
     load_starts(ops, n_ops, s_starts);
     __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const uint32_t warps = gridDim.x * (kThreads / 32);
-    for (uint32_t item = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5); item < n_items; item += warps) {
+    unsigned long long *hist_at = nullptr;   // the histogram the warp's counts belong to
+    uint32_t tot[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int since_fold = 0;
+    uint32_t first, last, stride;
+    if (kHist) {
+        const uint32_t per = (n_items + gridDim.x - 1) / gridDim.x;
+        first = blockIdx.x * per + (threadIdx.x >> 5);
+        last = min(n_items, (blockIdx.x + 1) * per);
+        stride = kThreads / 32;
+    } else {
+        first = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+        last = n_items;
+        stride = gridDim.x * (kThreads / 32);
+    }
+    for (uint32_t item = first; item < last; item += stride) {
         // a copy in registers: the outputs this item stores to are global
         // memory too, and through a reference the compiler would have to
         // reload the descriptor's fields after every store
         const RenderDesc op = ops[find_op(ops, n_ops, s_starts, item)];
+        if (kHist) {
+            if (op.hist != hist_at) {
+                if (hist_at) {
+                    hist_fold(cnt, tot, lane);
+                    hist_emit(tot, hist_at, lane);
+                }
+                hist_at = op.hist;
+                since_fold = 0;
+            } else if (hist_at && since_fold == kHistFoldItems) {
+                hist_fold(cnt, tot, lane);
+                since_fold = 0;
+            }
+            ++since_fold;
+        }
         const int64_t groups = (int64_t)op.groups_per_row * op.height;
         const int64_t g0 = (int64_t)(item - (uint32_t)op.item_start) * (32 * kRenderGroups) + lane;
         uint32_t c[kRenderGroups][16];
@@ -405,6 +513,7 @@ engine_render_kernel(const RenderDesc *ops, int n_ops, uint32_t n_items, Lut lut
             uint32_t b[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) b[j] = cpt::overlap_class(c[k][j], op.div);
+            if (kHist && hist_at) hist_count_group(row, key, b, valid);
             const int64_t out = (int64_t)y * op.width + x0;
             if (op.vec && valid == 16) {
                 if (op.counts_out) {
@@ -450,6 +559,10 @@ engine_render_kernel(const RenderDesc *ops, int n_ops, uint32_t n_items, Lut lut
                 }
             }
         }
+    }
+    if (kHist && hist_at) {
+        hist_fold(cnt, tot, lane);
+        hist_emit(tot, hist_at, lane);
     }
 }
 
@@ -734,7 +847,9 @@ int plan_render(composite_engine *e, const composite_render_op *ops, int32_t n_o
         const PlaneRec &p = e->planes[o.plane];
         if ((reinterpret_cast<uintptr_t>(o.counts_out) % (p.count_bits / 8)) || (reinterpret_cast<uintptr_t>(o.rgba_out) % 4))
             return efail(e, CPT_EINVAL, "render %d: counts_out must be aligned to its count type, rgba_out to 4 bytes", i);
-        const void *outs[3] = {o.counts_out, o.bucket_out, o.rgba_out};
+        if (reinterpret_cast<uintptr_t>(o.histogram_out) % 16)
+            return efail(e, CPT_EINVAL, "render %d: histogram_out must be 16-byte aligned", i);
+        const void *outs[4] = {o.counts_out, o.bucket_out, o.rgba_out, o.histogram_out};
         for (const void *q : outs)
             if (q && !device_reachable(q, e->device))
                 return efail(e, CPT_EINVAL, "render %d: outputs must be device memory of device %d (or mapped pinned "
@@ -767,6 +882,7 @@ int plan_render(composite_engine *e, const composite_render_op *ops, int32_t n_o
                             reinterpret_cast<uintptr_t>(o.rgba_out);
         d.vec = (p.width % 16 == 0) && (a % 16 == 0);
         d.u16 = p.count_bits == 16 ? 1 : 0;
+        d.hist = reinterpret_cast<unsigned long long *>(o.histogram_out);
         items += d.tiles;
         descs->push_back(d);
     }
@@ -801,12 +917,50 @@ int launch_accumulate(composite_engine *e, const void *d_ops, int n_ops, int64_t
     return CPT_OK;
 }
 
-int launch_render(composite_engine *e, const void *d_ops, int n_ops, int64_t n_items, uint32_t *,
-                  const Lut &lut) {
-    const int64_t ctas = std::min<int64_t>((int64_t)e->caps.num_sms * kRenderCtasPerSm,
+// True when some render op asks for a class histogram.
+bool any_histogram(const std::vector<RenderDesc> &descs) {
+    for (const RenderDesc &d : descs)
+        if (d.hist) return true;
+    return false;
+}
+
+// Clear entries (plane_id -1, no flag) for the histograms of a render, each
+// 256 x uint64 = 128 16-byte words, one clear item.
+void plan_histogram_clears(const std::vector<RenderDesc> &rdescs, std::vector<ClearDesc> *cdescs, int64_t *citems) {
+    for (const RenderDesc &r : rdescs) {
+        if (!r.hist) continue;
+        ClearDesc d{};
+        d.data = reinterpret_cast<uint4 *>(r.hist);
+        d.words = 256 * sizeof(uint64_t) / 16;
+        d.item_start = *citems;
+        d.plane_id = -1;
+        *citems += (d.words + 32 * kClearWords - 1) / (32 * kClearWords);
+        cdescs->push_back(d);
+    }
+}
+
+constexpr int kRenderHistSmem = (kThreads / 32) * kHistWarpBytes;   // dynamic: the warps' counters
+
+// The histogram render's 64 KB of dynamic shared memory is above the default
+// limit; asking for the largest carveout keeps three such CTAs on an SM.
+int prepare_render_kernels(composite_engine *e) {
+    ECK(e, cudaFuncSetAttribute(engine_render_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kRenderHistSmem));
+    ECK(e, cudaFuncSetAttribute(engine_render_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared));
+    return CPT_OK;
+}
+
+int launch_render(composite_engine *e, const void *d_ops, int n_ops, int64_t n_items, bool hist, const Lut &lut) {
+    const int64_t ctas = std::min<int64_t>((int64_t)e->caps.num_sms * (hist ? kRenderHistCtasPerSm : kRenderCtasPerSm),
                                            (n_items + kThreads / 32 - 1) / (kThreads / 32));
-    engine_render_kernel<<<(unsigned)std::max<int64_t>(1, ctas), kThreads, 0, e->stream>>>(
-        static_cast<const RenderDesc *>(d_ops), n_ops, (uint32_t)n_items, lut);
+    const unsigned grid = (unsigned)std::max<int64_t>(1, ctas);
+    if (hist)
+        engine_render_kernel<true><<<grid, kThreads, kRenderHistSmem, e->stream>>>(
+            static_cast<const RenderDesc *>(d_ops), n_ops, (uint32_t)n_items, lut);
+    else
+        engine_render_kernel<false><<<grid, kThreads, 0, e->stream>>>(static_cast<const RenderDesc *>(d_ops), n_ops,
+                                                                       (uint32_t)n_items, lut);
     ECK(e, cudaGetLastError());
     return CPT_OK;
 }
@@ -1167,7 +1321,7 @@ int composite_engine_begin(composite_engine **out, const composite_engine_config
                 ECK(e, cudaEventCreateWithFlags(&ring[i].consumed, cudaEventDisableTiming));
             }
         e->default_lut = make_lut(nullptr);
-        return CPT_OK;
+        return prepare_render_kernels(e);
     };
     const int rc = setup();
     if (rc) {
@@ -1258,10 +1412,23 @@ int composite_engine_render(composite_engine *e, const composite_render_op *ops,
     int64_t items = 0;
     int rc = plan_render(e, ops, n_ops, &descs, &items, nullptr);
     if (rc || items == 0) return rc;
+    const bool hist = any_histogram(descs);
+    std::vector<ClearDesc> cdescs;
+    int64_t citems = 0;
+    if (hist) plan_histogram_clears(descs, &cdescs, &citems);
+    // one upload: the histograms' clear entries, then the render descriptors
+    std::vector<unsigned char> blob(cdescs.size() * sizeof(ClearDesc) + descs.size() * sizeof(RenderDesc));
+    if (!cdescs.empty()) memcpy(blob.data(), cdescs.data(), cdescs.size() * sizeof(ClearDesc));
+    memcpy(blob.data() + cdescs.size() * sizeof(ClearDesc), descs.data(), descs.size() * sizeof(RenderDesc));
     Upload *u = nullptr;
-    rc = upload(e, e->up_render, &e->rup_i, descs.data(), descs.size() * sizeof(RenderDesc), &u);
+    rc = upload(e, e->up_render, &e->rup_i, blob.data(), blob.size(), &u);
     if (rc) return rc;
-    rc = launch_render(e, u->d, (int)descs.size(), items, e->d_counter, lut_rgba ? make_lut(lut_rgba) : e->default_lut);
+    if (citems > 0) {
+        rc = launch_clear(e, u->d, (int)cdescs.size(), citems);
+        if (rc) return rc;
+    }
+    rc = launch_render(e, static_cast<unsigned char *>(u->d) + cdescs.size() * sizeof(ClearDesc), (int)descs.size(),
+                       items, hist, lut_rgba ? make_lut(lut_rgba) : e->default_lut);
     if (rc) return rc;
     ECK(e, cudaEventRecord(u->consumed, e->stream));
     return CPT_OK;
@@ -1320,6 +1487,8 @@ int composite_engine_capture(composite_engine *e, const composite_op *ops, int32
     int64_t citems = 0;
     rc = plan_clears(e, cleared.data(), (int32_t)cleared.size(), &cdescs, &citems);
     if (rc) return rc;
+    const bool hist = any_histogram(rdescs);
+    plan_histogram_clears(rdescs, &cdescs, &citems);   // zeroed in the same clear node
     rc = drain(e);
     if (rc) return rc;
     destroy_graph(e);
@@ -1358,7 +1527,7 @@ int composite_engine_capture(composite_engine *e, const composite_op *ops, int32
             if (r) return r;
         }
         if (ritems > 0) {
-            int r = launch_render(e, e->graph_rops, (int)rdescs.size(), ritems, e->graph_counters + 1, lut);
+            int r = launch_render(e, e->graph_rops, (int)rdescs.size(), ritems, hist, lut);
             if (r) return r;
         }
         return CPT_OK;

@@ -81,7 +81,7 @@ def test_engine_defaults_and_no_gpu(lib):
     cfg = binding.EngineConfig()
     assert eng_lib.composite_engine_default_config(ctypes.byref(cfg)) == binding.CPT_OK
     assert (cfg.slab_members, cfg.ctas_per_sm) == (128, 5)
-    assert ctypes.sizeof(binding.Op) == 48 and ctypes.sizeof(binding.RenderOp) == 32
+    assert ctypes.sizeof(binding.Op) == 48 and ctypes.sizeof(binding.RenderOp) == 40
     assert ctypes.sizeof(binding.EngineConfig) == 56 and cfg.schedule == binding.CPT_SCHEDULE_PERSISTENT
     assert (cfg.item_member_groups, cfg.staging_buffers, cfg.staging_bytes) == (512, 2, 256 << 20)
     assert eng_lib.composite_engine_end(None) == binding.CPT_OK

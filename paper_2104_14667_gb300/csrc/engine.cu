@@ -62,20 +62,20 @@ struct OpDesc {
     int32_t pad;
 };
 
+// One render op.  The plane's pitch is groups_per_row x 16 pixels, so group g of the plane holds
+// the counts of pixels 16 g .. 16 g + 15 in memory order.
 struct RenderDesc {
     const uint32_t *plane;
     void *counts_out;
     uint8_t *bucket_out;
     uint32_t *rgba_out;
-    int64_t plane_pitch;
     int64_t item_start;
-    uint64_t n_members;
     int32_t width;
     int32_t height;
     int32_t groups_per_row;
-    int32_t tiles;
     int32_t vec;           // 16-byte stores allowed
     int32_t u16;           // the plane holds uint16 counts (else uint32)
+    int32_t dense;         // width == plane pitch: group g's outputs start at 16 g
     cpt::ClassDivisor div; // floor(255 c / n_members) by multiplication
     unsigned long long *hist;   // 256 class counts, zeroed before the launch, or NULL
 };
@@ -93,9 +93,8 @@ struct ClearDesc {
 constexpr int kSmemStarts = 2048;      // ops whose first items fit in shared memory
 constexpr int kClearWords = 8;         // 16-byte words per lane per clear item
 constexpr int kClearCtasPerSm = 4;
-constexpr int kRenderGroups = 1;       // 16-pixel groups per lane per render item
 constexpr int kRenderCtasPerSm = 4;    // render launch: CTAs per SM, grid-stride over items
-constexpr int kRenderHistCtasPerSm = 3;   // with histograms: 64 KB of counters per CTA
+constexpr int kRenderHistCtasPerSm = 4;   // with histograms: 32 KB of counters per CTA
 
 template <typename Desc>
 __device__ __forceinline__ int find_desc(const Desc *d, int n, int64_t item) {
@@ -353,40 +352,44 @@ engine_clear_kernel(const ClearDesc *ops, int n_ops, uint32_t n_items, int *flag
 }
 
 // Class histogram of the render (Fig. 1 caption: the frequency of the
-// overlap classes).  Every lane of a warp owns a byte counter per class in
-// shared memory (8 KB per warp), four to a 32-bit word, and adds to it with
-// shared atomics whose result it never waits for; no two lanes touch one
-// word, so the adds never conflict.  A lane whose 16 pixels share one class
-// adds 16 at once.  A lane's row of 64 words is stored with the word index
-// XORed with the lane, so that one class of all 32 lanes lies in 32 different
-// banks.  Every kHistFoldItems items (at most 16 per item, so a byte stays
-// below 256) the warp folds the bytes into per-lane 32-bit totals in
-// registers -- lane L owns classes 4L..4L+3 and 128+4L..128+4L+3 -- and when
-// its items move on to another op, and at the end, it adds the totals to the
-// op's 64-bit histogram in global memory.
-constexpr int kHistWarpBytes = 32 * 256;
-constexpr int kHistFoldItems = 15;
+// overlap classes).  Every kHistLanesPerRow lanes of a warp share a row of
+// byte counters in shared memory, one per class, four to a 32-bit word, and
+// add to them with shared atomics whose result they never wait for; lanes
+// of different rows never touch one word.  Four neighbouring pixels of one
+// class are added at once.  Row r's 64 words are stored with the word index
+// XORed with r, so that one class of all rows lies in different banks.  Every
+// kHistFoldItems items (at most 16 per lane and item, so a byte stays below
+// 256) the warp folds the bytes into 32-bit totals, also in shared memory
+// (lane L owns classes 4L..4L+3 and 128+4L..128+4L+3, stored at
+// [class slot][lane] so that the lanes' accesses never share a bank), and
+// when its items move on to another op, and at the end, it adds the totals
+// to the op's 64-bit histogram in global memory.
+constexpr int kHistLanesPerRow = 2;
+constexpr int kHistRows = 32 / kHistLanesPerRow;
+constexpr int kHistCounterBytes = kHistRows * 256;
+constexpr int kHistWarpBytes = kHistCounterBytes + 256 * 4;   // counters, then the totals
+constexpr int kHistFoldItems = 255 / (16 * kHistLanesPerRow);
 
-// row: the lane's 256 counter bytes; key: lane << 2, which XORs the word
-// index (class >> 2) with the lane
+// row: the lane's row of 256 counter bytes; key: the row index << 2, which
+// XORs the word index (class >> 2) with the row index
 __device__ __forceinline__ void hist_add(uint8_t *row, uint32_t key, uint32_t cls, uint32_t n) {
     atomicAdd(reinterpret_cast<uint32_t *>(row + ((cls ^ key) & 0xFCu)), n << ((cls & 3u) << 3));
 }
 
-__device__ __forceinline__ void hist_count_group(uint8_t *row, uint32_t key, const uint32_t (&b)[16], int valid) {
-    bool same = valid == 16;
-#pragma unroll
-    for (int j = 1; j < 16; ++j) same &= b[j] == b[0];
-    if (same) {
-        hist_add(row, key, b[0], 16u);
+// Four pixels' classes: one add when they agree.
+__device__ __forceinline__ void hist_count_quarter(uint8_t *row, uint32_t key, uint32_t b0, uint32_t b1, uint32_t b2,
+                                                   uint32_t b3) {
+    if (b0 == b1 && b1 == b2 && b2 == b3) {
+        hist_add(row, key, b0, 4u);
     } else {
-#pragma unroll
-        for (int j = 0; j < 16; ++j)
-            if (j < valid) hist_add(row, key, b[j], 1u);
+        hist_add(row, key, b0, 1u);
+        hist_add(row, key, b1, 1u);
+        hist_add(row, key, b2, 1u);
+        hist_add(row, key, b3, 1u);
     }
 }
 
-__device__ __forceinline__ void hist_fold(uint8_t *cnt, uint32_t (&tot)[8], int lane) {
+__device__ __forceinline__ void hist_fold(uint8_t *cnt, uint32_t *tot, int lane) {
     __syncwarp();
     uint32_t *w = reinterpret_cast<uint32_t *>(cnt);
 #pragma unroll
@@ -394,56 +397,105 @@ __device__ __forceinline__ void hist_fold(uint8_t *cnt, uint32_t (&tot)[8], int 
         const uint32_t k = (uint32_t)lane + 32u * h;   // the word of classes 4k..4k+3
         uint32_t lo = 0, hi = 0;                      // bytes 0, 2 and 1, 3 as 16-bit sums
 #pragma unroll 8
-        for (int r = 0; r < 32; ++r) {
+        for (int r = 0; r < kHistRows; ++r) {
             uint32_t *at = w + r * 64 + (k ^ (uint32_t)r);
             const uint32_t v = *at;
             *at = 0u;
             lo += v & 0x00FF00FFu;
             hi += (v >> 8) & 0x00FF00FFu;
         }
-        tot[4 * h + 0] += lo & 0xFFFFu;
-        tot[4 * h + 1] += hi & 0xFFFFu;
-        tot[4 * h + 2] += lo >> 16;
-        tot[4 * h + 3] += hi >> 16;
+        tot[(4 * h + 0) * 32 + lane] += lo & 0xFFFFu;
+        tot[(4 * h + 1) * 32 + lane] += hi & 0xFFFFu;
+        tot[(4 * h + 2) * 32 + lane] += lo >> 16;
+        tot[(4 * h + 3) * 32 + lane] += hi >> 16;
     }
     __syncwarp();
 }
 
-__device__ __forceinline__ void hist_emit(uint32_t (&tot)[8], unsigned long long *hist, int lane) {
+__device__ __forceinline__ void hist_emit(uint32_t *tot, unsigned long long *hist, int lane) {
 #pragma unroll
     for (int h = 0; h < 2; ++h)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const uint32_t t = tot[4 * h + j];
+            uint32_t &t = tot[(4 * h + j) * 32 + lane];
             if (t) atomicAdd(hist + 4 * lane + 128 * h + j, (unsigned long long)t);
-            tot[4 * h + j] = 0u;
+            t = 0u;
         }
 }
 
-// Render: warp-level items (render op, chunk of 32 x kRenderGroups 16-pixel
-// groups) dealt round robin to every warp of the launch -- items are all the
-// same size, so no counter is needed -- and a lane loads all its groups
-// before it classifies and stores any.  With histograms (kHist; 8 KB of
+// Classify and store one lane's group of 16 pixels (counts c, as loaded in
+// v); row: the lane's histogram counters, or NULL.
+template <bool kHist, bool kNarrow>
+__device__ __forceinline__ void render_group(const RenderDesc &op, const uint4 (&v)[4], const uint32_t (&c)[16], int valid,
+                                             int64_t out, int pieces, const uint32_t *table, uint8_t *row,
+                                             uint32_t key) {
+    auto cls = [&](uint32_t x) {
+        return kNarrow ? cpt::overlap_class_narrow(x, op.div) : cpt::overlap_class(x, op.div);
+    };
+    if (op.vec && valid == 16) {
+        if (op.counts_out) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (q < pieces)   // 'pieces' bytes per count
+                    reinterpret_cast<uint4 *>(static_cast<uint8_t *>(op.counts_out) + out * pieces)[q] = v[q];
+        }
+        // a quarter of the group at a time: classes, their colours, the packed classes
+        uint32_t w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t b0 = cls(c[4 * q]), b1 = cls(c[4 * q + 1]);
+            const uint32_t b2 = cls(c[4 * q + 2]), b3 = cls(c[4 * q + 3]);
+            w[q] = b0 | (b1 << 8) | (b2 << 16) | (b3 << 24);
+            if (kHist && row) hist_count_quarter(row, key, b0, b1, b2, b3);
+            if (op.rgba_out)
+                reinterpret_cast<uint4 *>(op.rgba_out + out)[q] = make_uint4(table[b0], table[b1], table[b2], table[b3]);
+        }
+        if (op.bucket_out) *reinterpret_cast<uint4 *>(op.bucket_out + out) = make_uint4(w[0], w[1], w[2], w[3]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            if (j < valid) {
+                const uint32_t b = cls(c[j]);
+                if (op.counts_out) {
+                    if (op.u16)
+                        reinterpret_cast<uint16_t *>(op.counts_out)[out + j] = (uint16_t)c[j];
+                    else
+                        reinterpret_cast<uint32_t *>(op.counts_out)[out + j] = c[j];
+                }
+                if (op.bucket_out) op.bucket_out[out + j] = (uint8_t)b;
+                if (op.rgba_out) op.rgba_out[out + j] = table[b];
+                if (kHist && row) hist_add(row, key, b, 1u);
+            }
+        }
+    }
+}
+
+// Render: warp-level items (render op, 32 16-pixel groups of its plane, one
+// per lane) dealt round robin to every warp of the launch -- items are all
+// the same size, so no counter is needed.  With histograms (kHist; 8 KB of
 // dynamic shared memory per warp) every CTA takes one contiguous range of
 // items instead, so that a warp's items span one or two ops and its totals
-// go to global memory once or twice.
+// go to global memory once or twice.  A plane's pitch is a whole number of
+// groups, so group g holds the counts of pixels 16 g .. 16 g + 15 in memory
+// order; when the outputs are dense at that pitch too (width a multiple of
+// 16) they start at 16 g as well and no row division is needed.
 template <bool kHist>
 __global__ void __launch_bounds__(kThreads, kHist ? kRenderHistCtasPerSm : kRenderCtasPerSm)
-engine_render_kernel(const RenderDesc *ops, int n_ops, uint32_t n_items, Lut lut) {
+engine_render_kernel(const RenderDesc *__restrict__ ops, int n_ops, uint32_t n_items, Lut lut) {
     __shared__ uint32_t table[256];
     __shared__ uint32_t s_starts[kSmemStarts];
     extern __shared__ __align__(16) uint8_t s_hist[];
     const int lane = threadIdx.x & 31;
     uint8_t *cnt = s_hist + (kHist ? (threadIdx.x >> 5) * kHistWarpBytes : 0);
-    uint8_t *row = cnt + (kHist ? lane * 256 : 0);
-    const uint32_t key = (uint32_t)lane << 2;
+    uint8_t *row = cnt + (kHist ? (lane / kHistLanesPerRow) * 256 : 0);
+    const uint32_t key = (uint32_t)(lane / kHistLanesPerRow) << 2;
     for (int i = threadIdx.x; i < 256; i += kThreads) table[i] = lut.rgba[i];
     if (kHist)
         for (int i = lane; i < kHistWarpBytes / 16; i += 32) reinterpret_cast<uint4 *>(cnt)[i] = make_uint4(0, 0, 0, 0);
     load_starts(ops, n_ops, s_starts);
     __syncthreads();
     unsigned long long *hist_at = nullptr;   // the histogram the warp's counts belong to
-    uint32_t tot[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    uint32_t *tot = reinterpret_cast<uint32_t *>(cnt + kHistCounterBytes);
     int since_fold = 0;
     uint32_t first, last, stride;
     if (kHist) {
@@ -460,7 +512,7 @@ engine_render_kernel(const RenderDesc *ops, int n_ops, uint32_t n_items, Lut lut
         // a copy in registers: the outputs this item stores to are global
         // memory too, and through a reference the compiler would have to
         // reload the descriptor's fields after every store
-        const RenderDesc op = ops[find_op(ops, n_ops, s_starts, item)];
+        const RenderDesc &op = ops[find_op(ops, n_ops, s_starts, item)];
         if (kHist) {
             if (op.hist != hist_at) {
                 if (hist_at) {
@@ -476,89 +528,43 @@ engine_render_kernel(const RenderDesc *ops, int n_ops, uint32_t n_items, Lut lut
             ++since_fold;
         }
         const int64_t groups = (int64_t)op.groups_per_row * op.height;
-        const int64_t g0 = (int64_t)(item - (uint32_t)op.item_start) * (32 * kRenderGroups) + lane;
-        uint32_t c[kRenderGroups][16];
+        const int64_t g = (int64_t)(item - (uint32_t)op.item_start) * 32 + lane;
+        if (g >= groups) continue;
+        const int pieces = op.u16 ? 2 : 4;   // 16-byte pieces of a group's counts
+        const uint4 *src = reinterpret_cast<const uint4 *>(op.plane) + g * pieces;
+        uint4 v[4];
 #pragma unroll
-        for (int k = 0; k < kRenderGroups; ++k) {
-            const int64_t g = g0 + 32 * k;
-            if (g >= groups) break;
-            const int y = (int)(g / op.groups_per_row);
-            const int x0 = (int)(g - (int64_t)y * op.groups_per_row) * 16;
-            const int64_t at = (int64_t)y * op.plane_pitch + x0;
-            if (op.u16) {
-                const uint4 *src = reinterpret_cast<const uint4 *>(reinterpret_cast<const uint16_t *>(op.plane) + at);
-                const uint4 a = src[0], b = src[1];
-                const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+        for (int q = 0; q < 4; ++q)
+            if (q < pieces) v[q] = src[q];
+        uint32_t c[16];
+        if (op.u16) {
+            const uint32_t w[8] = {v[0].x, v[0].y, v[0].z, v[0].w, v[1].x, v[1].y, v[1].z, v[1].w};
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    c[k][2 * q] = w[q] & 0xFFFFu;
-                    c[k][2 * q + 1] = w[q] >> 16;
-                }
-            } else {
-                const uint4 *src = reinterpret_cast<const uint4 *>(op.plane + at);
+            for (int q = 0; q < 8; ++q) {
+                c[2 * q] = w[q] & 0xFFFFu;
+                c[2 * q + 1] = w[q] >> 16;
+            }
+        } else {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const uint4 v = src[q];
-                    c[k][4 * q] = v.x; c[k][4 * q + 1] = v.y; c[k][4 * q + 2] = v.z; c[k][4 * q + 3] = v.w;
-                }
+            for (int q = 0; q < 4; ++q) {
+                c[4 * q] = v[q].x; c[4 * q + 1] = v[q].y; c[4 * q + 2] = v[q].z; c[4 * q + 3] = v[q].w;
             }
         }
-#pragma unroll
-        for (int k = 0; k < kRenderGroups; ++k) {
-            const int64_t g = g0 + 32 * k;
-            if (g >= groups) break;
+        int valid = 16;
+        int64_t out = g * 16;
+        if (!op.dense) {
             const int y = (int)(g / op.groups_per_row);
             const int x0 = (int)(g - (int64_t)y * op.groups_per_row) * 16;
-            const int valid = min(16, op.width - x0);
-            uint32_t b[16];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) b[j] = cpt::overlap_class(c[k][j], op.div);
-            if (kHist && hist_at) hist_count_group(row, key, b, valid);
-            const int64_t out = (int64_t)y * op.width + x0;
-            if (op.vec && valid == 16) {
-                if (op.counts_out) {
-                    if (op.u16) {
-#pragma unroll
-                        for (int q = 0; q < 2; ++q)
-                            reinterpret_cast<uint4 *>(reinterpret_cast<uint16_t *>(op.counts_out) + out)[q] =
-                                make_uint4(c[k][8 * q] | (c[k][8 * q + 1] << 16), c[k][8 * q + 2] | (c[k][8 * q + 3] << 16),
-                                           c[k][8 * q + 4] | (c[k][8 * q + 5] << 16), c[k][8 * q + 6] | (c[k][8 * q + 7] << 16));
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < 4; ++q)
-                            reinterpret_cast<uint4 *>(reinterpret_cast<uint32_t *>(op.counts_out) + out)[q] =
-                                make_uint4(c[k][4 * q], c[k][4 * q + 1], c[k][4 * q + 2], c[k][4 * q + 3]);
-                    }
-                }
-                if (op.bucket_out) {
-                    uint32_t w[4];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        w[q] = b[4 * q] | (b[4 * q + 1] << 8) | (b[4 * q + 2] << 16) | (b[4 * q + 3] << 24);
-                    *reinterpret_cast<uint4 *>(op.bucket_out + out) = make_uint4(w[0], w[1], w[2], w[3]);
-                }
-                if (op.rgba_out) {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        reinterpret_cast<uint4 *>(op.rgba_out + out)[q] =
-                            make_uint4(table[b[4 * q]], table[b[4 * q + 1]], table[b[4 * q + 2]], table[b[4 * q + 3]]);
-                }
-            } else {
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    if (j < valid) {
-                        if (op.counts_out) {
-                            if (op.u16)
-                                reinterpret_cast<uint16_t *>(op.counts_out)[out + j] = (uint16_t)c[k][j];
-                            else
-                                reinterpret_cast<uint32_t *>(op.counts_out)[out + j] = c[k][j];
-                        }
-                        if (op.bucket_out) op.bucket_out[out + j] = (uint8_t)b[j];
-                        if (op.rgba_out) op.rgba_out[out + j] = table[b[j]];
-                    }
-                }
-            }
+            valid = min(16, op.width - x0);
+            out = (int64_t)y * op.width + x0;
         }
+        // one multiply-high per class for N < 2^16 (every 16-bit plane), the
+        // general division otherwise: a branch per item, so that each
+        // specialisation keeps only its own divisor fields live
+        if (op.div.narrow)
+            render_group<kHist, true>(op, v, c, valid, out, pieces, table, hist_at ? row : nullptr, key);
+        else
+            render_group<kHist, false>(op, v, c, valid, out, pieces, table, hist_at ? row : nullptr, key);
     }
     if (kHist && hist_at) {
         hist_fold(cnt, tot, lane);
@@ -869,21 +875,20 @@ int plan_render(composite_engine *e, const composite_render_op *ops, int32_t n_o
         d.counts_out = o.counts_out;
         d.bucket_out = o.bucket_out;
         d.rgba_out = reinterpret_cast<uint32_t *>(o.rgba_out);
-        d.plane_pitch = p.pitch_px;
         d.item_start = items;
-        d.n_members = (uint64_t)n;
         d.div = cpt::class_divisor((uint64_t)n);
         d.width = p.width;
         d.height = p.height;
         d.groups_per_row = (int32_t)(p.pitch_px / 16);
         const int64_t groups = (int64_t)d.groups_per_row * p.height;
-        d.tiles = (int32_t)((groups + 32 * kRenderGroups - 1) / (32 * kRenderGroups));
+        const int64_t tiles = (groups + 31) / 32;   // warp items: one 16-pixel group per lane
         const uintptr_t a = reinterpret_cast<uintptr_t>(o.counts_out) | reinterpret_cast<uintptr_t>(o.bucket_out) |
                             reinterpret_cast<uintptr_t>(o.rgba_out);
         d.vec = (p.width % 16 == 0) && (a % 16 == 0);
         d.u16 = p.count_bits == 16 ? 1 : 0;
+        d.dense = p.pitch_px == p.width ? 1 : 0;
         d.hist = reinterpret_cast<unsigned long long *>(o.histogram_out);
-        items += d.tiles;
+        items += tiles;
         descs->push_back(d);
     }
     if (items >= (int64_t)1 << 31) return efail(e, CPT_EINVAL, "too many render items");

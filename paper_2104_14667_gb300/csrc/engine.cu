@@ -27,6 +27,7 @@
 #include "bit_count.cuh"
 #include "internal.cuh"
 #include "overlap_class.cuh"
+#include "class_histogram.cuh"
 
 namespace {
 
@@ -351,78 +352,6 @@ engine_clear_kernel(const ClearDesc *ops, int n_ops, uint32_t n_items, int *flag
     }
 }
 
-// Class histogram of the render (Fig. 1 caption: the frequency of the
-// overlap classes).  Every kHistLanesPerRow lanes of a warp share a row of
-// byte counters in shared memory, one per class, four to a 32-bit word, and
-// add to them with shared atomics whose result they never wait for; lanes
-// of different rows never touch one word.  Four neighbouring pixels of one
-// class are added at once.  Row r's 64 words are stored with the word index
-// XORed with r, so that one class of all rows lies in different banks.  Every
-// kHistFoldItems items (at most 16 per lane and item, so a byte stays below
-// 256) the warp folds the bytes into 32-bit totals, also in shared memory
-// (lane L owns classes 4L..4L+3 and 128+4L..128+4L+3, stored at
-// [class slot][lane] so that the lanes' accesses never share a bank), and
-// when its items move on to another op, and at the end, it adds the totals
-// to the op's 64-bit histogram in global memory.
-constexpr int kHistLanesPerRow = 2;
-constexpr int kHistRows = 32 / kHistLanesPerRow;
-constexpr int kHistCounterBytes = kHistRows * 256;
-constexpr int kHistWarpBytes = kHistCounterBytes + 256 * 4;   // counters, then the totals
-constexpr int kHistFoldItems = 255 / (16 * kHistLanesPerRow);
-
-// row: the lane's row of 256 counter bytes; key: the row index << 2, which
-// XORs the word index (class >> 2) with the row index
-__device__ __forceinline__ void hist_add(uint8_t *row, uint32_t key, uint32_t cls, uint32_t n) {
-    atomicAdd(reinterpret_cast<uint32_t *>(row + ((cls ^ key) & 0xFCu)), n << ((cls & 3u) << 3));
-}
-
-// Four pixels' classes: one add when they agree.
-__device__ __forceinline__ void hist_count_quarter(uint8_t *row, uint32_t key, uint32_t b0, uint32_t b1, uint32_t b2,
-                                                   uint32_t b3) {
-    if (b0 == b1 && b1 == b2 && b2 == b3) {
-        hist_add(row, key, b0, 4u);
-    } else {
-        hist_add(row, key, b0, 1u);
-        hist_add(row, key, b1, 1u);
-        hist_add(row, key, b2, 1u);
-        hist_add(row, key, b3, 1u);
-    }
-}
-
-__device__ __forceinline__ void hist_fold(uint8_t *cnt, uint32_t *tot, int lane) {
-    __syncwarp();
-    uint32_t *w = reinterpret_cast<uint32_t *>(cnt);
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const uint32_t k = (uint32_t)lane + 32u * h;   // the word of classes 4k..4k+3
-        uint32_t lo = 0, hi = 0;                      // bytes 0, 2 and 1, 3 as 16-bit sums
-#pragma unroll 8
-        for (int r = 0; r < kHistRows; ++r) {
-            uint32_t *at = w + r * 64 + (k ^ (uint32_t)r);
-            const uint32_t v = *at;
-            *at = 0u;
-            lo += v & 0x00FF00FFu;
-            hi += (v >> 8) & 0x00FF00FFu;
-        }
-        tot[(4 * h + 0) * 32 + lane] += lo & 0xFFFFu;
-        tot[(4 * h + 1) * 32 + lane] += hi & 0xFFFFu;
-        tot[(4 * h + 2) * 32 + lane] += lo >> 16;
-        tot[(4 * h + 3) * 32 + lane] += hi >> 16;
-    }
-    __syncwarp();
-}
-
-__device__ __forceinline__ void hist_emit(uint32_t *tot, unsigned long long *hist, int lane) {
-#pragma unroll
-    for (int h = 0; h < 2; ++h)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            uint32_t &t = tot[(4 * h + j) * 32 + lane];
-            if (t) atomicAdd(hist + 4 * lane + 128 * h + j, (unsigned long long)t);
-            t = 0u;
-        }
-}
-
 // Classify and store one lane's group of 16 pixels (counts c, as loaded in
 // v); row: the lane's histogram counters, or NULL.
 template <bool kHist, bool kNarrow>
@@ -446,7 +375,7 @@ __device__ __forceinline__ void render_group(const RenderDesc &op, const uint4 (
             const uint32_t b0 = cls(c[4 * q]), b1 = cls(c[4 * q + 1]);
             const uint32_t b2 = cls(c[4 * q + 2]), b3 = cls(c[4 * q + 3]);
             w[q] = b0 | (b1 << 8) | (b2 << 16) | (b3 << 24);
-            if (kHist && row) hist_count_quarter(row, key, b0, b1, b2, b3);
+            if (kHist && row) cpt::hist_count_quarter(row, key, b0, b1, b2, b3);
             if (op.rgba_out)
                 reinterpret_cast<uint4 *>(op.rgba_out + out)[q] = make_uint4(table[b0], table[b1], table[b2], table[b3]);
         }
@@ -464,7 +393,7 @@ __device__ __forceinline__ void render_group(const RenderDesc &op, const uint4 (
                 }
                 if (op.bucket_out) op.bucket_out[out + j] = (uint8_t)b;
                 if (op.rgba_out) op.rgba_out[out + j] = table[b];
-                if (kHist && row) hist_add(row, key, b, 1u);
+                if (kHist && row) cpt::hist_add(row, key, b, 1u);
             }
         }
     }
@@ -486,16 +415,16 @@ engine_render_kernel(const RenderDesc *__restrict__ ops, int n_ops, uint32_t n_i
     __shared__ uint32_t s_starts[kSmemStarts];
     extern __shared__ __align__(16) uint8_t s_hist[];
     const int lane = threadIdx.x & 31;
-    uint8_t *cnt = s_hist + (kHist ? (threadIdx.x >> 5) * kHistWarpBytes : 0);
-    uint8_t *row = cnt + (kHist ? (lane / kHistLanesPerRow) * 256 : 0);
-    const uint32_t key = (uint32_t)(lane / kHistLanesPerRow) << 2;
+    uint8_t *cnt = s_hist + (kHist ? (threadIdx.x >> 5) * cpt::kHistWarpBytes : 0);
+    uint8_t *row = cnt + (kHist ? (lane / cpt::kHistLanesPerRow) * 256 : 0);
+    const uint32_t key = (uint32_t)(lane / cpt::kHistLanesPerRow) << 2;
     for (int i = threadIdx.x; i < 256; i += kThreads) table[i] = lut.rgba[i];
     if (kHist)
-        for (int i = lane; i < kHistWarpBytes / 16; i += 32) reinterpret_cast<uint4 *>(cnt)[i] = make_uint4(0, 0, 0, 0);
+        for (int i = lane; i < cpt::kHistWarpBytes / 16; i += 32) reinterpret_cast<uint4 *>(cnt)[i] = make_uint4(0, 0, 0, 0);
     load_starts(ops, n_ops, s_starts);
     __syncthreads();
     unsigned long long *hist_at = nullptr;   // the histogram the warp's counts belong to
-    uint32_t *tot = reinterpret_cast<uint32_t *>(cnt + kHistCounterBytes);
+    uint32_t *tot = reinterpret_cast<uint32_t *>(cnt + cpt::kHistCounterBytes);
     int since_fold = 0;
     uint32_t first, last, stride;
     if (kHist) {
@@ -516,13 +445,13 @@ engine_render_kernel(const RenderDesc *__restrict__ ops, int n_ops, uint32_t n_i
         if (kHist) {
             if (op.hist != hist_at) {
                 if (hist_at) {
-                    hist_fold(cnt, tot, lane);
-                    hist_emit(tot, hist_at, lane);
+                    cpt::hist_fold(cnt, tot, lane);
+                    cpt::hist_emit(tot, hist_at, lane);
                 }
                 hist_at = op.hist;
                 since_fold = 0;
-            } else if (hist_at && since_fold == kHistFoldItems) {
-                hist_fold(cnt, tot, lane);
+            } else if (hist_at && since_fold == cpt::kHistFoldItems) {
+                cpt::hist_fold(cnt, tot, lane);
                 since_fold = 0;
             }
             ++since_fold;
@@ -567,8 +496,8 @@ engine_render_kernel(const RenderDesc *__restrict__ ops, int n_ops, uint32_t n_i
             render_group<kHist, false>(op, v, c, valid, out, pieces, table, hist_at ? row : nullptr, key);
     }
     if (kHist && hist_at) {
-        hist_fold(cnt, tot, lane);
-        hist_emit(tot, hist_at, lane);
+        cpt::hist_fold(cnt, tot, lane);
+        cpt::hist_emit(tot, hist_at, lane);
     }
 }
 
@@ -944,7 +873,7 @@ void plan_histogram_clears(const std::vector<RenderDesc> &rdescs, std::vector<Cl
     }
 }
 
-constexpr int kRenderHistSmem = (kThreads / 32) * kHistWarpBytes;   // dynamic: the warps' counters
+constexpr int kRenderHistSmem = (kThreads / 32) * cpt::kHistWarpBytes;   // dynamic: the warps' counters
 
 // The histogram render's 64 KB of dynamic shared memory is above the default
 // limit; asking for the largest carveout keeps three such CTAs on an SM.

@@ -163,8 +163,9 @@ int composite_engine_sync(composite_engine *eng, int32_t *bad_plane_out);
 
 /* Captures "clear every target plane, submit ops, render rops" as a CUDA
  * graph held by the engine (replacing any earlier one): three kernel nodes,
- * the clear of all target planes in one of them.  The ops' member sets,
- * index lists and outputs are fixed by the capture.  Does not run it.
+ * the clear of all target planes (and of the render ops' histograms, so
+ * that every replay starts them from zero) in one of them.  The ops' member
+ * sets, index lists and outputs are fixed by the capture.  Does not run it.
  * Device members only (CPT_EINVAL for an op on host memory). */
 int composite_engine_capture(composite_engine *eng, const composite_op *ops, int32_t n_ops,
                              const composite_render_op *rops, int32_t n_rops, const uint8_t *lut_rgba);

@@ -126,6 +126,12 @@ __device__ __forceinline__ int find_op(const Desc *d, int n, const uint32_t *sta
     return lo;
 }
 
+// First item of op i (from shared memory when the list fits there).
+template <typename Desc>
+__device__ __forceinline__ uint32_t op_start(const Desc *d, int n, const uint32_t *starts, int i) {
+    return n <= kSmemStarts ? starts[i] : (uint32_t)d[i].item_start;
+}
+
 template <typename Desc>
 __device__ __forceinline__ void load_starts(const Desc *d, int n, uint32_t *starts) {
     if (n <= kSmemStarts)
@@ -437,11 +443,15 @@ engine_render_kernel(const RenderDesc *__restrict__ ops, int n_ops, uint32_t n_i
         last = n_items;
         stride = gridDim.x * (kThreads / 32);
     }
+    // the op of the warp's current item; without histograms the next item's
+    // op is looked up while the current item's counts are on their way (with
+    // them, the registers that takes would spill)
+    int idx = first < last ? find_op(ops, n_ops, s_starts, first) : 0;
     for (uint32_t item = first; item < last; item += stride) {
-        // a copy in registers: the outputs this item stores to are global
-        // memory too, and through a reference the compiler would have to
-        // reload the descriptor's fields after every store
-        const RenderDesc &op = ops[find_op(ops, n_ops, s_starts, item)];
+        if (kHist) idx = find_op(ops, n_ops, s_starts, item);
+        // restrict: the outputs are plain pointers, and without it every
+        // store would force the descriptor's fields to be reloaded
+        const RenderDesc &op = ops[idx];
         if (kHist) {
             if (op.hist != hist_at) {
                 if (hist_at) {
@@ -458,13 +468,18 @@ engine_render_kernel(const RenderDesc *__restrict__ ops, int n_ops, uint32_t n_i
         }
         const int64_t groups = (int64_t)op.groups_per_row * op.height;
         const int64_t g = (int64_t)(item - (uint32_t)op.item_start) * 32 + lane;
-        if (g >= groups) continue;
         const int pieces = op.u16 ? 2 : 4;   // 16-byte pieces of a group's counts
         const uint4 *src = reinterpret_cast<const uint4 *>(op.plane) + g * pieces;
         uint4 v[4];
+        if (g < groups) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-            if (q < pieces) v[q] = src[q];
+            for (int q = 0; q < 4; ++q)
+                if (q < pieces) v[q] = src[q];
+        }
+        const uint32_t next = item + stride;
+        if (!kHist && next < last && idx + 1 < n_ops && next >= op_start(ops, n_ops, s_starts, idx + 1))
+            idx = find_op(ops, n_ops, s_starts, next);
+        if (g >= groups) continue;
         uint32_t c[16];
         if (op.u16) {
             const uint32_t w[8] = {v[0].x, v[0].y, v[0].z, v[0].w, v[1].x, v[1].y, v[1].z, v[1].w};

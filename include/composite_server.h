@@ -114,6 +114,16 @@ int composite_server_request(composite_server *srv, int32_t session, const int32
                              uint32_t *counts_out, uint8_t *bucket_out, uint8_t *rgba_out,
                              int64_t *request_id_out);
 
+/* As composite_server_request, and also the class histogram of the request's
+ * composite (Fig. 1 caption: the frequency of the overlap classes) into
+ * histogram_out: 256 x uint64, bin k = the pixels whose overlap class is k,
+ * 16-byte aligned, device memory of the server's device or mapped pinned host
+ * memory (else CPT_EINVAL), zeroed and filled when the request completes.  A
+ * histogram must not be shared by two requests in flight.  NULL = none. */
+int composite_server_request_histogram(composite_server *srv, int32_t session, const int32_t *toggle, int32_t n,
+                                       uint32_t *counts_out, uint8_t *bucket_out, uint8_t *rgba_out,
+                                       uint64_t *histogram_out, int64_t *request_id_out);
+
 /* Makes progress without blocking: collects completed cycles (their request
  * ids go to `completed`, up to `capacity`; *n_completed = how many were
  * written) and queues new cycles for admissible requests.

@@ -735,6 +735,8 @@ def _server_lib():
             "composite_server_open_session": (ctypes.c_int, [vp, ctypes.POINTER(i32)]),
             "composite_server_close_session": (ctypes.c_int, [vp, i32]),
             "composite_server_request": (ctypes.c_int, [vp, i32, vp, i32, vp, vp, vp, ctypes.POINTER(i64)]),
+            "composite_server_request_histogram": (ctypes.c_int, [vp, i32, vp, i32, vp, vp, vp, vp,
+                                                                  ctypes.POINTER(i64)]),
             "composite_server_pump": (ctypes.c_int, [vp, vp, i32, ctypes.POINTER(i32)]),
             "composite_server_drain": (ctypes.c_int, [vp]),
             "composite_server_session_members": (ctypes.c_int, [vp, i32, ctypes.POINTER(i64)]),
@@ -800,13 +802,20 @@ class Server:
     def close_session(self, session: int):
         _scheck(self.lib, self.h, self.lib.composite_server_close_session(self.h, session))
 
-    def request(self, session: int, toggle, counts_out=None, bucket_out=None, rgba_out=None) -> int:
+    def request(self, session: int, toggle, counts_out=None, bucket_out=None, rgba_out=None,
+                histogram_out=None) -> int:
         ids = np.ascontiguousarray(np.asarray(toggle, dtype=np.int32))
         rid = ctypes.c_int64()
-        _scheck(self.lib, self.h, self.lib.composite_server_request(
-            self.h, session, ids.ctypes.data if ids.size else None, int(ids.size), _ptr(counts_out),
-            _ptr(bucket_out), _ptr(rgba_out), ctypes.byref(rid)))
-        self._pending[rid.value] = (counts_out, bucket_out, rgba_out)
+        if histogram_out is None:
+            rc = self.lib.composite_server_request(
+                self.h, session, ids.ctypes.data if ids.size else None, int(ids.size), _ptr(counts_out),
+                _ptr(bucket_out), _ptr(rgba_out), ctypes.byref(rid))
+        else:
+            rc = self.lib.composite_server_request_histogram(
+                self.h, session, ids.ctypes.data if ids.size else None, int(ids.size), _ptr(counts_out),
+                _ptr(bucket_out), _ptr(rgba_out), _ptr(histogram_out), ctypes.byref(rid))
+        _scheck(self.lib, self.h, rc)
+        self._pending[rid.value] = (counts_out, bucket_out, rgba_out, histogram_out)
         return rid.value
 
     def pump(self, capacity: int = 4096) -> list:

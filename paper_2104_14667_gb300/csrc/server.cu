@@ -38,6 +38,7 @@ struct Request {
     uint32_t *counts_out;
     uint8_t *bucket_out;
     uint8_t *rgba_out;
+    uint64_t *histogram_out;
 };
 
 struct Cycle {
@@ -442,7 +443,8 @@ int build_cycle(composite_server *s, Cycle *cyc, std::vector<Request> &batch) {
         ro.counts_out = q.counts_out;
         ro.bucket_out = q.bucket_out;
         ro.rgba_out = q.rgba_out;
-        if (ro.counts_out || ro.bucket_out || ro.rgba_out) rops.push_back(ro);
+        ro.histogram_out = q.histogram_out;
+        if (ro.counts_out || ro.bucket_out || ro.rgba_out || ro.histogram_out) rops.push_back(ro);
     }
     if (!rops.empty()) {
         rc = engine_rc(s, composite_engine_render(s->eng, rops.data(), (int32_t)rops.size(), nullptr));
@@ -655,8 +657,10 @@ int composite_server_close_session(composite_server *s, int32_t session) try {
     return cpt::abi_exception_status();
 }
 
-int composite_server_request(composite_server *s, int32_t session, const int32_t *toggle, int32_t n,
-                             uint32_t *counts_out, uint8_t *bucket_out, uint8_t *rgba_out, int64_t *request_id_out) try {
+namespace {
+
+int queue_request(composite_server *s, int32_t session, const int32_t *toggle, int32_t n, uint32_t *counts_out,
+                  uint8_t *bucket_out, uint8_t *rgba_out, uint64_t *histogram_out, int64_t *request_id_out) {
     if (!s) return CPT_EINVAL;
     s->err.clear();
     if (session < 0 || session >= (int32_t)s->sessions.size() || !s->sessions[session].open)
@@ -669,9 +673,11 @@ int composite_server_request(composite_server *s, int32_t session, const int32_t
             return sfail(s, CPT_EINVAL, "member id %d out of range [0, %d)", toggle[i], s->n_total);
     if ((reinterpret_cast<uintptr_t>(counts_out) % 4) || (reinterpret_cast<uintptr_t>(rgba_out) % 4))
         return sfail(s, CPT_EINVAL, "counts_out and rgba_out must be 4-byte aligned");
+    if (reinterpret_cast<uintptr_t>(histogram_out) % 16)
+        return sfail(s, CPT_EINVAL, "histogram_out must be 16-byte aligned");
     // the render kernel writes the outputs directly: device memory of the
     // server's device, or mapped pinned host memory
-    const void *outs[3] = {counts_out, bucket_out, rgba_out};
+    const void *outs[4] = {counts_out, bucket_out, rgba_out, histogram_out};
     for (const void *o : outs) {
         if (!o) continue;
         cudaPointerAttributes a;
@@ -691,6 +697,7 @@ int composite_server_request(composite_server *s, int32_t session, const int32_t
     q.counts_out = counts_out;
     q.bucket_out = bucket_out;
     q.rgba_out = rgba_out;
+    q.histogram_out = histogram_out;
     Session &ss = s->sessions[session];
     toggle_bits(ss.view, q.toggle);
     ss.n_view = popcount_words(ss.view);
@@ -699,6 +706,21 @@ int composite_server_request(composite_server *s, int32_t session, const int32_t
     ++s->stats.queued;
     if (request_id_out) *request_id_out = s->next_id - 1;
     return CPT_OK;
+}
+
+}  // namespace
+
+int composite_server_request(composite_server *s, int32_t session, const int32_t *toggle, int32_t n,
+                             uint32_t *counts_out, uint8_t *bucket_out, uint8_t *rgba_out, int64_t *request_id_out) try {
+    return queue_request(s, session, toggle, n, counts_out, bucket_out, rgba_out, nullptr, request_id_out);
+} catch (...) {
+    return cpt::abi_exception_status();
+}
+
+int composite_server_request_histogram(composite_server *s, int32_t session, const int32_t *toggle, int32_t n,
+                                       uint32_t *counts_out, uint8_t *bucket_out, uint8_t *rgba_out,
+                                       uint64_t *histogram_out, int64_t *request_id_out) try {
+    return queue_request(s, session, toggle, n, counts_out, bucket_out, rgba_out, histogram_out, request_id_out);
 } catch (...) {
     return cpt::abi_exception_status();
 }

@@ -139,3 +139,36 @@ def test_bit_packed_ensemble_matches_byte_ensemble():
     for (counts, _, _), members in zip(as_bits, expected_sets(reqs, 4)):
         c = oracle.count(m[members]) if len(members) else np.zeros((H, W), np.int64)
         np.testing.assert_array_equal(counts.astype(np.int64), c)
+
+
+def test_request_histograms_match_the_oracle():
+    # composite_server_request_histogram: the class histogram of every
+    # request's composite, with and without image outputs, in mixed cycles
+    m, res, ovf = ensemble()
+    reqs = trace(5, 4, 24)
+    hists, buckets = [], []
+    with binding.Server(res, ovf, max_batch=8, staging_members=7) as srv:
+        sessions = [srv.open_session() for _ in range(4)]
+        for i, (s, tog) in enumerate(reqs):
+            hist = torch.full((256,), -1, dtype=torch.int64, device="cuda")
+            bucket = torch.empty((H, W), dtype=torch.uint8, device="cuda") if i % 2 else None
+            srv.request(sessions[s], tog, None, bucket, None, histogram_out=hist)
+            hists.append(hist)
+            buckets.append(bucket)
+            if i % 3 == 0:
+                srv.pump()
+        srv.drain()
+        bad = torch.zeros(258, dtype=torch.int64, device="cuda")
+        with pytest.raises(binding.CompositeError) as ei:
+            srv.request(sessions[0], [1], histogram_out=bad[1:257])   # 8 bytes off a 16-byte boundary
+        assert ei.value.code == binding.CPT_EINVAL
+        with pytest.raises(binding.CompositeError) as ei:
+            srv.request(sessions[0], [1], histogram_out=np.zeros(256, np.int64))   # pageable host memory
+        assert ei.value.code == binding.CPT_EINVAL
+    torch.cuda.synchronize()
+    for hist, bucket, members in zip(hists, buckets, expected_sets(reqs, 4)):
+        c = oracle.count(m[members]) if len(members) else np.zeros((H, W), np.int64)
+        b = oracle.bucket(c, len(members))
+        np.testing.assert_array_equal(hist.cpu().numpy(), oracle.histogram(b).astype(np.int64))
+        if bucket is not None:
+            np.testing.assert_array_equal(bucket.cpu().numpy(), b)

@@ -407,7 +407,7 @@ __device__ __forceinline__ void render_group(const RenderDesc &op, const uint4 (
 
 // Render: warp-level items (render op, 32 16-pixel groups of its plane, one
 // per lane) dealt round robin to every warp of the launch -- items are all
-// the same size, so no counter is needed.  With histograms (kHist; 8 KB of
+// the same size, so no counter is needed.  With histograms (kHist; 5 KB of
 // dynamic shared memory per warp) every CTA takes one contiguous range of
 // items instead, so that a warp's items span one or two ops and its totals
 // go to global memory once or twice.  A plane's pitch is a whole number of
@@ -890,8 +890,9 @@ void plan_histogram_clears(const std::vector<RenderDesc> &rdescs, std::vector<Cl
 
 constexpr int kRenderHistSmem = (kThreads / 32) * cpt::kHistWarpBytes;   // dynamic: the warps' counters
 
-// The histogram render's 64 KB of dynamic shared memory is above the default
-// limit; asking for the largest carveout keeps three such CTAs on an SM.
+// The histogram render's dynamic shared memory (40 KB, beside 9 KB static):
+// allowed explicitly, and the largest carveout asked for, so that four such
+// CTAs fit on an SM.
 int prepare_render_kernels(composite_engine *e) {
     ECK(e, cudaFuncSetAttribute(engine_render_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 kRenderHistSmem));

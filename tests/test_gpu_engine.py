@@ -367,3 +367,30 @@ def test_host_ops_bit_packed_through_staging():
         eng.render([eng.render_op(p, *o)])
         eng.sync()
     check(o, np.concatenate([m[10:], m[:10]]))
+
+
+@pytest.mark.parametrize("hist", [False, True])
+def test_op_lists_longer_than_the_shared_memory_index(hist):
+    # 2500 planes, one op each, and 2500 render ops in one launch: more than
+    # the 2048 first items the kernels keep in shared memory, so the clear,
+    # accumulate and render launches look the ops up in global memory
+    n_planes, w, h = 2500, 24, 3
+    m = synth.scramble_nonzero(synth.random_masks(300, 5, h, w, density=0.4), 300)
+    dev = padded(m)
+    with binding.Engine() as eng:
+        planes = [eng.add_plane(w, h, 16 if i % 2 else 32) for i in range(n_planes)]
+        eng.clear_many(planes)
+        eng.submit([eng.op(p, dev[: 1 + i % 5]) for i, p in enumerate(planes)])
+        buckets = torch.empty((n_planes, h, w), dtype=torch.uint8, device="cuda")
+        hists = torch.empty((n_planes, 256), dtype=torch.int64, device="cuda") if hist else None
+        eng.render([eng.render_op(p, None, buckets[i], None, hists[i] if hist else None)
+                    for i, p in enumerate(planes)])
+        eng.sync()
+        got_b = buckets.cpu().numpy()
+        got_h = hists.cpu().numpy() if hist else None
+    for k in range(1, 6):
+        b = oracle.bucket(oracle.count(m[:k]), k)
+        for i in range(k - 1, n_planes, 5):
+            np.testing.assert_array_equal(got_b[i], b, err_msg=f"plane {i}")
+            if hist:
+                np.testing.assert_array_equal(got_h[i], oracle.histogram(b).astype(np.int64), err_msg=f"plane {i}")

@@ -121,7 +121,8 @@ typedef struct composite_config {
                                    default 2                                              */
     int32_t chunk_members;      /* C members per upload and per kernel launch, 1..255, or
                                    0 = automatic (the default): a staging buffer holds up
-                                   to 256 MiB of rasters (at most 255), and each add or
+                                   to 256 MiB of rasters (512 MiB on the texture path;
+                                   at most 255 rasters), and each add or
                                    remove of n rasters is cut into chunks of
                                    max(16 MiB of rasters, min(that cap, ceil(n / 32)))
                                    members, so that a call has about 32 chunks: the

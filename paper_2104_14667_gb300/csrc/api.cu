@@ -191,13 +191,19 @@ int refuse_poisoned(composite_ctx *ctx) {
 // chunks, no smaller than kAutoMinChunkBytes: the kernel of a call's last
 // chunk has no later upload to hide under, so the share of kernel time left
 // exposed is about one chunk in the number of chunks, while chunks too small
-// pay a fixed cost per copy and launch.
+// pay a fixed cost per copy and launch.  The texture path's slots hold twice
+// as much: each chunk is a conversion launch and a texture-fold launch over a
+// layered array, and device-resident masks go through the slots too (4096^2 x
+// 1024 resident: 2.09-2.10e12 member-px/s with 32 layers per chunk against
+// 1.97-2.00e12 with 16; streamed, both at 0.985-0.991 of the link).
 constexpr int64_t kAutoSlotBytes = 256ll << 20;
+constexpr int64_t kAutoSlotBytesTexture = 512ll << 20;
 constexpr int64_t kAutoMinChunkBytes = 16ll << 20;
 constexpr int kAutoChunksPerCall = 32;
 
-int auto_slot_members(int64_t member_bytes) {
-    return (int)std::max<int64_t>(1, std::min<int64_t>(255, kAutoSlotBytes / member_bytes));
+int auto_slot_members(int64_t member_bytes, int32_t read_path) {
+    const int64_t slot = read_path == CPT_READ_TEXTURE ? kAutoSlotBytesTexture : kAutoSlotBytes;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(255, slot / member_bytes));
 }
 
 int chunk_for_call(const composite_ctx *ctx, int n) {
@@ -856,7 +862,7 @@ int composite_begin(composite_ctx **out, int32_t width, int32_t height, const co
     ctx->row_bytes = ctx->bits ? ((int64_t)width + 7) / 8 : (int64_t)width * ctx->elem;
     ctx->stage_pitch = (ctx->row_bytes + 15) / 16 * 16;
     ctx->member_bytes = ctx->stage_pitch * height;
-    ctx->slot_members = c.chunk_members > 0 ? c.chunk_members : auto_slot_members(ctx->member_bytes);
+    ctx->slot_members = c.chunk_members > 0 ? c.chunk_members : auto_slot_members(ctx->member_bytes, c.read_path);
     rc = setup(ctx);
     if (rc) {
         g_begin_error = ctx->err;

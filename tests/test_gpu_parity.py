@@ -545,12 +545,13 @@ def test_resume_rejects_counts_above_n():
                                              (1024, 1024, 40, "texture", "device"),
                                              (2048, 512, 70, "tma", "pinned"), (512, 256, 600, "linear", "pageable")])
 def test_automatic_chunk_depth(w, h, n, path, kind):
-    # chunk_members 0: a staging buffer holds up to 256 MiB of rasters, and
-    # a call of n rasters goes in chunks of max(16 MiB, min(cap, ceil(n/32)))
+    # chunk_members 0: a staging buffer holds up to 256 MiB of rasters (512
+    # MiB on the texture path), and a call of n rasters goes in chunks of
+    # max(16 MiB, min(cap, ceil(n/32)))
     m = synth.scramble_nonzero(synth.random_masks(60 + n, n, h, w, density=0.3), 60)
     row = (w + 15) // 16 * 16
     member = row * h
-    cap = max(1, min(255, (256 << 20) // member))
+    cap = max(1, min(255, ((512 if path == "texture" else 256) << 20) // member))
     c = max(min(cap, -(-(16 << 20) // member)), min(cap, -(-n // 32)))
     with binding.Composite(w, h, read_path=path, chunk_members=0, trace=True, pageable_ingest="ring") as comp:
         comp.add(as_kind(m, kind))

@@ -159,6 +159,25 @@ def _ptr(a):
     return a.ctypes.data
 
 
+def _nbytes(a) -> int:
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            return a.numel() * a.element_size()
+    except ImportError:  # pragma: no cover
+        pass
+    return int(a.nbytes)
+
+
+def _check_room(**outs):
+    """Every output must hold what the library writes into it: the C ABI
+    takes plain pointers and cannot check sizes, and a short device output
+    would be overrun by a kernel."""
+    for name, (a, need) in outs.items():
+        if a is not None and _nbytes(a) < need:
+            raise ValueError(f"{name} holds {_nbytes(a)} bytes; the render writes {need}")
+
+
 def _on_device(*arrays) -> int:
     dev = None
     for a in arrays:
@@ -390,12 +409,20 @@ class Composite:
     def n(self) -> int:
         return composite_member_count(self.ctx)
 
+    def _check_outputs(self, counts_out, bucket_out, rgba_out, mean_out=None, histogram_out=None):
+        px = self.width * self.height
+        _check_room(counts_out=(counts_out, px * ((self.config.count_bits or 16) // 8)),
+                    bucket_out=(bucket_out, px), rgba_out=(rgba_out, 4 * px), mean_out=(mean_out, 4 * px),
+                    histogram_out=(histogram_out, 256 * 8))
+
     def render(self, counts_out=None, bucket_out=None, rgba_out=None, mean_out=None, lut=None):
+        self._check_outputs(counts_out, bucket_out, rgba_out, mean_out)
         composite_render(self.ctx, counts_out, bucket_out, rgba_out, mean_out, lut)
         if not _on_device(counts_out, bucket_out, rgba_out, mean_out):
             self._borrowed.clear()
 
     def render_histogram(self, histogram_out, counts_out=None, bucket_out=None, rgba_out=None, lut=None):
+        self._check_outputs(counts_out, bucket_out, rgba_out, histogram_out=histogram_out)
         composite_render_histogram(self.ctx, histogram_out, counts_out, bucket_out, rgba_out, lut)
         if not _on_device(histogram_out, counts_out, bucket_out, rgba_out):
             self._borrowed.clear()
@@ -569,7 +596,8 @@ class Engine:
         _echeck(self.lib, None, self.lib.composite_engine_begin(ctypes.byref(h), ctypes.byref(cfg)))
         self.h = h
         self._keep = []
-        self.shapes = {}
+        self.shapes = {}        # plane -> (width, height)
+        self.count_bytes = {}   # plane -> bytes per count
 
     def add_plane(self, width: int, height: int, count_bits: int = 32) -> int:
         """A zeroed plane of uint32 (or, count_bits=16, uint16) counts; its id."""
@@ -577,10 +605,13 @@ class Engine:
         _echeck(self.lib, self.h, self.lib.composite_engine_add_plane_bits(self.h, width, height, count_bits,
                                                                           ctypes.byref(pid)))
         self.shapes[pid.value] = (width, height)
+        self.count_bytes[pid.value] = count_bits // 8
         return pid.value
 
     def free_plane(self, plane: int):
         _echeck(self.lib, self.h, self.lib.composite_engine_free_plane(self.h, plane))
+        self.shapes.pop(plane, None)
+        self.count_bytes.pop(plane, None)
 
     def clear(self, plane: int):
         _echeck(self.lib, self.h, self.lib.composite_engine_clear(self.h, plane))
@@ -609,8 +640,11 @@ class Engine:
             o.n_members = n
         return o
 
-    @staticmethod
-    def render_op(plane: int, counts_out=None, bucket_out=None, rgba_out=None, histogram_out=None) -> RenderOp:
+    def render_op(self, plane: int, counts_out=None, bucket_out=None, rgba_out=None, histogram_out=None) -> RenderOp:
+        if plane in self.shapes:   # an unknown plane is the library's to reject
+            w, h = self.shapes[plane]
+            _check_room(counts_out=(counts_out, w * h * self.count_bytes[plane]), bucket_out=(bucket_out, w * h),
+                        rgba_out=(rgba_out, 4 * w * h), histogram_out=(histogram_out, 256 * 8))
         r = RenderOp()
         r.plane = plane
         r.counts_out, r.bucket_out, r.rgba_out = _ptr(counts_out), _ptr(bucket_out), _ptr(rgba_out)
@@ -804,6 +838,9 @@ class Server:
 
     def request(self, session: int, toggle, counts_out=None, bucket_out=None, rgba_out=None,
                 histogram_out=None) -> int:
+        px = self.width * self.height
+        _check_room(counts_out=(counts_out, 4 * px), bucket_out=(bucket_out, px), rgba_out=(rgba_out, 4 * px),
+                    histogram_out=(histogram_out, 256 * 8))
         ids = np.ascontiguousarray(np.asarray(toggle, dtype=np.int32))
         rid = ctypes.c_int64()
         if histogram_out is None:

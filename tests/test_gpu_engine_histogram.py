@@ -157,3 +157,32 @@ def test_full_size_terrain_histogram():
     got = np.bincount(bucket.cpu().numpy().ravel(), minlength=256)
     np.testing.assert_array_equal(got, want)
     assert (want > 0).sum() > 32   # the ensemble spans many classes
+
+
+def test_short_outputs_are_refused_before_any_launch():
+    # the binding checks that every output holds what the render writes: the
+    # C ABI takes plain pointers, and a kernel would overrun a short one
+    w, h = 64, 8
+    masks = padded(ensemble(98, 3, h, w, 0.5))
+    short = {"counts_out": torch.empty((h, w - 1), dtype=torch.int32, device="cuda"),
+             "bucket_out": torch.empty((h - 1, w), dtype=torch.uint8, device="cuda"),
+             "rgba_out": torch.empty((h, w, 3), dtype=torch.uint8, device="cuda"),
+             "histogram_out": torch.empty(255, dtype=torch.int64, device="cuda")}
+    with binding.Engine() as eng:
+        p = eng.add_plane(w, h)
+        eng.submit([eng.op(p, masks)])
+        for name, t in short.items():
+            with pytest.raises(ValueError, match=name):
+                eng.render_op(p, **{name: t})
+        eng.sync()
+    with binding.Composite(w, h, count_bits=32) as comp:
+        comp.add(masks)
+        for name, t in short.items():
+            with pytest.raises(ValueError, match=name):
+                if name == "histogram_out":
+                    comp.render_histogram(t)
+                else:
+                    comp.render(**{name: t})
+        with pytest.raises(ValueError, match="counts_out"):
+            comp.render(counts_out=np.empty((h, w), np.uint16))   # 16-bit host counts for 32-bit ones
+        comp.sync()

@@ -165,6 +165,8 @@ def test_request_histograms_match_the_oracle():
         with pytest.raises(binding.CompositeError) as ei:
             srv.request(sessions[0], [1], histogram_out=np.zeros(256, np.int64))   # pageable host memory
         assert ei.value.code == binding.CPT_EINVAL
+        with pytest.raises(ValueError, match="bucket_out"):   # refused by the binding: too short
+            srv.request(sessions[0], [1], bucket_out=torch.empty((H - 1, W), dtype=torch.uint8, device="cuda"))
     torch.cuda.synchronize()
     for hist, bucket, members in zip(hists, buckets, expected_sets(reqs, 4)):
         c = oracle.count(m[members]) if len(members) else np.zeros((H, W), np.int64)

@@ -633,6 +633,14 @@ class Engine:
         o.mask_format = {"bytes": CPT_MASK_BYTES, "bits": CPT_MASK_BITS}[mask_format]
         o.row_pitch_bytes, o.member_stride_bytes = pitch, stride
         if index is not None:
+            # the kernel reads members + index[i] * stride: every id must name
+            # a raster of `members` (checked here, on the device values)
+            import torch
+            if not (isinstance(index, torch.Tensor) and index.is_cuda and index.dtype == torch.int32
+                    and index.is_contiguous()):
+                raise ValueError("index must be a contiguous int32 CUDA tensor")
+            if index.numel() and (int(index.min()) < 0 or int(index.max()) >= n):
+                raise ValueError(f"index holds member ids outside [0, {n})")
             o.member_index = index.data_ptr()
             o.n_members = int(index.numel())
         else:

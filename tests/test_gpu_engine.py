@@ -394,3 +394,19 @@ def test_op_lists_longer_than_the_shared_memory_index(hist):
             np.testing.assert_array_equal(got_b[i], b, err_msg=f"plane {i}")
             if hist:
                 np.testing.assert_array_equal(got_h[i], oracle.histogram(b).astype(np.int64), err_msg=f"plane {i}")
+
+
+def test_index_lists_are_checked_by_the_binding():
+    w, h = 64, 8
+    dev = padded(synth.random_masks(92, 6, h, w))
+    with binding.Engine() as eng:
+        p = eng.add_plane(w, h)
+        for bad in (torch.tensor([0, 6], dtype=torch.int32, device="cuda"),     # past the last member
+                    torch.tensor([-1], dtype=torch.int32, device="cuda"),
+                    torch.tensor([0, 1], dtype=torch.int64, device="cuda"),     # wrong type
+                    torch.tensor([0, 1], dtype=torch.int32)):                   # host memory
+            with pytest.raises(ValueError):
+                eng.op(p, dev, index=bad)
+        eng.submit([eng.op(p, dev, index=torch.tensor([5, 0, 5], dtype=torch.int32, device="cuda"))])
+        eng.sync()
+        assert eng.member_count(p) == 3

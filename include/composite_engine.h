@@ -77,7 +77,10 @@ typedef struct composite_engine_config {
  * the raster at members + idx(i) * member_stride_bytes, idx(i) =
  * member_index[i] (a device int32 array) or i when member_index is NULL.
  * The raster's width and height are the plane's.  members is device memory,
- * or pinned host memory (then member_index must be NULL). */
+ * or pinned host memory (then member_index must be NULL).  The library does
+ * not know how many rasters the allocation holds: every member_index entry
+ * must name one of them (the Python binding checks this on the device
+ * values). */
 typedef struct composite_op {
     int32_t plane;
     int32_t sign;                 /* +1 add, -1 remove */

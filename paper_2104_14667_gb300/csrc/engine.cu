@@ -443,12 +443,17 @@ engine_render_kernel(const RenderDesc *__restrict__ ops, int n_ops, uint32_t n_i
         last = n_items;
         stride = gridDim.x * (kThreads / 32);
     }
-    // the op of the warp's current item; without histograms the next item's
-    // op is looked up while the current item's counts are on their way (with
-    // them, the registers that takes would spill)
+    // the op of the warp's current item: without histograms the next item's
+    // op is looked up while the current item's counts are on their way; with
+    // them (contiguous items, few op changes) only when an item passes the
+    // current op's end
     int idx = first < last ? find_op(ops, n_ops, s_starts, first) : 0;
+    uint32_t op_end = kHist && first < last && idx + 1 < n_ops ? op_start(ops, n_ops, s_starts, idx + 1) : n_items;
     for (uint32_t item = first; item < last; item += stride) {
-        if (kHist) idx = find_op(ops, n_ops, s_starts, item);
+        if (kHist && item >= op_end) {
+            idx = find_op(ops, n_ops, s_starts, item);
+            op_end = idx + 1 < n_ops ? op_start(ops, n_ops, s_starts, idx + 1) : n_items;
+        }
         // restrict: the outputs are plain pointers, and without it every
         // store would force the descriptor's fields to be reloaded
         const RenderDesc &op = ops[idx];

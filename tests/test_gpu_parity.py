@@ -409,8 +409,11 @@ def test_overlap_class_for_every_count(count_bits):
         with binding.Composite(len(targets), 1, count_bits=count_bits) as comp:
             comp.add(masks)
             got = comp.render_host()
+            hist = np.empty(256, np.uint64)
+            comp.render_histogram(hist)   # host output: synchronous
         c = np.asarray(targets, np.int64)[None, :]
         b = oracle.bucket(c, n)
+        np.testing.assert_array_equal(hist, oracle.histogram(b), err_msg=f"N={n}")
         np.testing.assert_array_equal(got["counts"].astype(np.int64), c, err_msg=f"N={n}")
         np.testing.assert_array_equal(got["bucket"], b, err_msg=f"N={n}")
         np.testing.assert_array_equal(got["rgba"], oracle.rgba(b), err_msg=f"N={n}")
@@ -428,8 +431,10 @@ def test_engine_overlap_class_for_every_count(count_bits):
             p = eng.add_plane(w, 1, count_bits)
             counts = torch.empty((1, w), dtype=torch.int32 if count_bits == 32 else torch.int16, device="cuda")
             bucket = torch.empty((1, w), dtype=torch.uint8, device="cuda")
+            hist = torch.empty(256, dtype=torch.int64, device="cuda")
             eng.submit([eng.op(p, buf[:, :, :w])])
             eng.render([eng.render_op(p, counts, bucket, None)])
+            eng.render([eng.render_op(p, histogram_out=hist)])   # the histogram launch's class path too
             eng.sync()
             got = counts.cpu().numpy()
             if got.dtype == np.int16:
@@ -437,6 +442,8 @@ def test_engine_overlap_class_for_every_count(count_bits):
             c = np.asarray(targets, np.int64)[None, :]
             np.testing.assert_array_equal(got.astype(np.int64), c, err_msg=f"N={n}")
             np.testing.assert_array_equal(bucket.cpu().numpy(), oracle.bucket(c, n), err_msg=f"N={n}")
+            np.testing.assert_array_equal(hist.cpu().numpy(), oracle.histogram(oracle.bucket(c, n)).astype(np.int64),
+                                          err_msg=f"N={n}")
             eng.free_plane(p)
 
 

@@ -636,9 +636,10 @@ int run_ring(composite_ctx *ctx, const uint8_t *src, int n, int64_t stride, int6
 // the call returns -- the call waits for its uploads and unregisters the
 // batch.  A wait that fails leaves the batch registered until the copy
 // stream is known idle (the next successful sync, render to host or end).
-// On this class of host the driver page-locks a batch faster than host
-// threads can copy it (109 GB/s end to end against 78 through the ring for
-// 4.3 GB; the host's own pageable-to-pinned copy tops out at 88 GB/s).
+// On a 16-core Grace host with a GB300, page-locking a batch in place was
+// faster than any number of host threads copying it (109-145 GB/s end to end
+// for 4.3 GB, against 78-100 through the ring; the host's own pageable-to-
+// pinned copy tops out at 88-106 GB/s).
 constexpr int64_t kRegisterMinBytes = 64ll << 20;
 
 int run_registered(composite_ctx *ctx, const uint8_t *src, int n, int64_t stride, int64_t pitch, int sign) {

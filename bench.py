@@ -795,9 +795,9 @@ def sweep_streaming(args, torch, binding, device, stream, sides=None, counts=Non
                 add_all(comp)
                 comp.sync()
                 passes.append(1e3 * (time.perf_counter() - t0))
-            # the median pass: the host link of these shared machines dips now
-            # and then for one pass (copies at a fraction of the rate the same
-            # buffer reaches in the next); min and max are reported beside it
+            # the median pass: a host link shared with other GPUs' jobs can dip
+            # for one pass (copies at a fraction of the rate the same buffer
+            # reaches in the next); min and max are reported beside it
             ms = float(np.median(passes))
         with binding.Composite(side, side, trace=True, **cfg) as comp:
             add_all(comp)
@@ -958,7 +958,8 @@ def sweep_batched_streamed(args, torch, binding, device, stream, reqs, data, mem
         eng.render(rops)
 
     # The two forms alternate pass by pass, so that a dip of the host link
-    # (these shared machines have them) falls on both alike; medians reported.
+    # (a link shared with other jobs has them) falls on both alike; medians
+    # reported.
     plain_ms, batch_ms = [], []
     for i in range(args.warmup + args.steps):
         a = _timed(torch, stream, plain_all, 1, 0)

@@ -186,3 +186,23 @@ def test_short_outputs_are_refused_before_any_launch():
         with pytest.raises(ValueError, match="counts_out"):
             comp.render(counts_out=np.empty((h, w), np.uint16))   # 16-bit host counts for 32-bit ones
         comp.sync()
+
+
+@pytest.mark.parametrize("count_bits", [32, 16])
+def test_empty_plane_is_all_class_zero(count_bits):
+    # N = 0: every pixel is class 0 (the divisor's empty case), in the same
+    # launch as a plane with members
+    w, h = 40, 9
+    m = ensemble(99, 3, h, w, 0.5)
+    with binding.Engine() as eng:
+        empty, full = eng.add_plane(w, h, count_bits), eng.add_plane(w, h, count_bits)
+        eng.submit([eng.op(full, padded(m))])
+        he, hf = new_hist(), new_hist()
+        bucket = torch.full((h, w), 7, dtype=torch.uint8, device="cuda")
+        eng.render([eng.render_op(empty, None, bucket, None, he), eng.render_op(full, histogram_out=hf)])
+        eng.sync()
+    want = np.zeros(256, np.int64)
+    want[0] = w * h
+    np.testing.assert_array_equal(he.cpu().numpy(), want)
+    assert not bucket.any()
+    np.testing.assert_array_equal(hf.cpu().numpy(), expected_hist(m))

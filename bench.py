@@ -359,16 +359,43 @@ def workload_config(args):
             "seed": args.seed, "l2": "inputs larger than L2 (no flush needed)"}
 
 
+# How the last pinned_host_buffer was made, for the bench line.
+HOST_BUFFER_NOTE = {}
+
+
+def _h2d_rate(torch, flat, nbytes, reps=2):
+    """Best host -> device cudaMemcpyAsync rate (GB/s) of flat[:nbytes]."""
+    dst = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.Stream()
+    best = 0.0
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(s):
+            a.record()
+            dst.copy_(flat[:nbytes], non_blocking=True)
+            b.record()
+        b.synchronize()
+        best = max(best, nbytes / (a.elapsed_time(b) * 1e-3) / 1e9)
+    del dst
+    return best
+
+
 def pinned_host_buffer(torch, shape):
     """A page-locked host buffer for the e2e leg: anonymous memory advised to
     use transparent huge pages, faulted in, then registered with the driver
     (mapped, so the in-place read path can use it too).  Copy engines read
     buffers of fragmented small pages more slowly: on one box successive
     processes that pinned 17 GB each saw the staged rate fall from 209 to 132
-    GB/s while the kernel's own loads held 210.  Falls back to torch's pinned
-    allocator.  Returns (tensor, handle for release_host_buffer)."""
+    GB/s while the kernel's own loads held 210, and on another the copy
+    engines read a registered 17 GB buffer at 27 GB/s while a 1 GiB buffer of
+    torch's pinned allocator went at 210.  So the registered buffer's copy
+    rate is probed on its first GiB against such a buffer's, and below 0.9 of
+    it the registered buffer is replaced by one from torch's pinned allocator
+    (also the fall-back when registering fails).  Returns (tensor, handle for
+    release_host_buffer); HOST_BUFFER_NOTE says which buffer it is."""
     import mmap
     n = int(np.prod(shape))
+    HOST_BUFFER_NOTE.clear()
     try:
         m = mmap.mmap(-1, n, flags=mmap.MAP_PRIVATE | mmap.MAP_ANONYMOUS)
         if hasattr(mmap, "MADV_HUGEPAGE"):
@@ -378,11 +405,23 @@ def pinned_host_buffer(torch, shape):
         t = torch.from_numpy(arr)
         rc = torch.cuda.cudart().cudaHostRegister(t.data_ptr(), n, 3)   # portable | mapped
         if int(rc) == 0:
-            return t, (m, t.data_ptr())
+            nb = min(n, 1 << 30)
+            probe = _h2d_rate(torch, t.view(-1), nb)
+            ref_buf = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
+            ref = _h2d_rate(torch, ref_buf, nb)
+            del ref_buf
+            HOST_BUFFER_NOTE.update(registered_probe_gbs=probe, pinned_probe_gbs=ref)
+            if probe >= 0.9 * ref:
+                HOST_BUFFER_NOTE["kind"] = "huge-page advised, registered"
+                return t, (m, t.data_ptr())
+            torch.cuda.synchronize()
+            torch.cuda.cudart().cudaHostUnregister(t.data_ptr())
+            HOST_BUFFER_NOTE["kind"] = "cudaHostAlloc (the registered buffer copied below 0.9 of it)"
         del t, arr
-        m.close()
+        m.close()   # before the replacement is pinned
     except Exception:
         pass
+    HOST_BUFFER_NOTE.setdefault("kind", "cudaHostAlloc")
     return torch.empty(shape, dtype=torch.uint8, pin_memory=True), None
 
 
@@ -504,6 +543,7 @@ def run_ours(args):
     e2e_launches = 0
     if not args.no_e2e:
         host, host_handle = pinned_host_buffer(torch, (N, H, W))
+        host_note = dict(HOST_BUFFER_NOTE)
         host.copy_(dev_masks)
         del dev_masks
         torch.cuda.empty_cache()
@@ -564,7 +604,7 @@ def run_ours(args):
                 "staged_h2d_gbs": N * P / (staged_ms * 1e-3 / args.steps) / 1e9,
                 "host_read_h2d_gbs": (N * P / (direct_ms * 1e-3 / args.steps) / 1e9) if direct_ms else None,
                 "overlap_fraction": overlap, "upload_busy_ms": copy_busy, "chunks": len(copies),
-                "host_buffer": "huge-page advised, registered" if host_handle is not None else "cudaHostAlloc"}
+                "host_buffer": dict(host_note)}
         release_host_buffer(torch, host, host_handle)
         del host
 

@@ -793,6 +793,7 @@ def sweep_streaming(args, torch, binding, device, stream, sides=None, counts=Non
     plan = [tuple(e) + ("linear",) * (5 - len(e)) for e in plan]
     counts = sorted({e[1] for e in plan})
     pools = {}
+    pool_notes = {}   # side -> how its pinned pool was made
     for side, n, chunk, k, path in plan:
         P = side * side
         if side not in pools:
@@ -804,9 +805,10 @@ def sweep_streaming(args, torch, binding, device, stream, sides=None, counts=Non
             ens = synth.ensemble(2, side, side, pool_n)
             dev = torch.empty((pool_n, side, side), dtype=torch.uint8, device=device)
             synth.fill_masks_torch(ens, dev)
-            # huge-page advised and registered, like the e2e leg's buffer:
-            # repeated 16 GB cudaHostAlloc pools slowed the copy engines
+            # huge-page advised and registered, like the e2e leg's buffer
+            # (and replaced the same way when its copies are slow)
             host, handle = pinned_host_buffer(torch, (pool_n, side, side))
+            pool_notes[side] = dict(HOST_BUFFER_NOTE)
             host.copy_(dev)
             del dev
             pools[side] = (host, ens, handle)
@@ -868,7 +870,8 @@ def sweep_streaming(args, torch, binding, device, stream, sides=None, counts=Non
                           "member_px_per_s": n * P / (ms * 1e-3), "h2d_gbs": gbs,
                           "link_peak_gbs": peak, "link_frac": gbs / peak,
                           "overlap_fraction": metrics.overlap_fraction(copies, kernels),
-                          "mb_per_100ms": gbs * 100.0, **model, **busy, "exact_sampled_rows": exact}), flush=True)
+                          "mb_per_100ms": gbs * 100.0, **model, **busy, "exact_sampled_rows": exact,
+                          "host_buffer": pool_notes.get(side)}), flush=True)
     for old_host, _, old_handle in pools.values():
         release_host_buffer(torch, old_host, old_handle)
     pools.clear()

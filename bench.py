@@ -406,12 +406,15 @@ def pinned_host_buffer(torch, shape):
         rc = torch.cuda.cudart().cudaHostRegister(t.data_ptr(), n, 3)   # portable | mapped
         if int(rc) == 0:
             nb = min(n, 1 << 30)
-            probe = _h2d_rate(torch, t.view(-1), nb)
-            ref_buf = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
-            ref = _h2d_rate(torch, ref_buf, nb)
-            del ref_buf
+            try:
+                probe = _h2d_rate(torch, t.view(-1), nb)
+                ref_buf = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
+                ref = _h2d_rate(torch, ref_buf, nb)
+                del ref_buf
+            except Exception:   # no room for the probe: keep the registered buffer
+                probe = ref = None
             HOST_BUFFER_NOTE.update(registered_probe_gbs=probe, pinned_probe_gbs=ref)
-            if probe >= 0.9 * ref:
+            if probe is None or probe >= 0.9 * ref:
                 HOST_BUFFER_NOTE["kind"] = "huge-page advised, registered"
                 return t, (m, t.data_ptr())
             torch.cuda.synchronize()

@@ -14,8 +14,9 @@ namespace cpt {
 // result they never wait for; lanes of different rows never touch one word.
 // Four neighbouring pixels of one class are added at once.  Row r's 64 words
 // are stored with the word index XORed with r, so that one class of all rows
-// lies in different banks.  A lane adds at most 16 per item (one group of 16
-// pixels), so after kHistFoldItems items a byte is still below 256: the warp
+// lies in different banks.  A byte gains at most 16 per item from each of the
+// kHistLanesPerRow lanes of its row (one group of 16 pixels per lane), so
+// after kHistFoldItems items it is still below 256: the warp
 // then folds the bytes into the totals (hist_fold; lane L owns classes
 // 4L..4L+3 and 128+4L..128+4L+3, stored at [class slot][lane] so that the
 // lanes' accesses never share a bank).  The totals go to the 64-bit
